@@ -1,0 +1,717 @@
+/*
+ * lbm_oracle.c -- plain FP64 CPU oracle (TEST INFRASTRUCTURE ONLY; see
+ * lbm_oracle.h).  Slow on purpose: dense matrices, a generic set-partition
+ * cumulant formula and per-cell Gauss-Jordan inverses, so that each step can
+ * be checked against the paper by eye.  Shares nothing with the CUDA path.
+ */
+#include "lbm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define QMAX 27
+#define MAXPART 203 /* Bell(6): set partitions of the largest monomial */
+
+typedef struct {
+  int nblocks;
+  unsigned char e[6][3]; /* exponent of each block */
+} partition_t;
+
+typedef struct {
+  int ready;
+  int q, d;
+  int xi[QMAX][3];
+  int expo[QMAX][3];
+  int deg[QMAX];
+  int mono[3][3][3]; /* exponent -> monomial index, -1 if not in the set */
+  double w[QMAX];
+  double M[QMAX][QMAX], Minv[QMAX][QMAX];
+  double Praw[QMAX][QMAX], Prawinv[QMAX][QMAX];
+  double Pcm[QMAX][QMAX], Pcminv[QMAX][QMAX];
+  int group[QMAX];
+  int npart[QMAX];
+  partition_t part[QMAX][MAXPART];
+} lattice_t;
+
+static lattice_t g_lat[3];
+
+/* ------------------------------------------------------------------ */
+/* velocity sets (Sec. 2.1), documented order                          */
+/* ------------------------------------------------------------------ */
+static const int V2[9][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0},
+                             {0, 1, 0},  {0, -1, 0}, {1, 1, 0},
+                             {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+static const int V3[27][3] = {
+    {0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},
+    {0, 0, 1},   {0, 0, -1},  {1, 1, 0},   {-1, -1, 0}, {1, -1, 0},
+    {-1, 1, 0},  {1, 0, 1},   {-1, 0, -1}, {1, 0, -1},  {-1, 0, 1},
+    {0, 1, 1},   {0, -1, -1}, {0, 1, -1},  {0, -1, 1},  {1, 1, 1},
+    {-1, -1, -1}, {1, 1, -1}, {-1, -1, 1}, {1, -1, 1},  {-1, 1, -1},
+    {1, -1, -1}, {-1, 1, 1}};
+
+static double ipow(double x, int e) {
+  double r = 1.0;
+  for (int k = 0; k < e; ++k) r *= x;
+  return r;
+}
+
+/* Moments of the 1-D normal distribution with variance c_s^2 = 1/3
+ * (the rest-state Maxwellian, Eq. 2.12): E[X^n]. */
+static double gauss_moment(int n) {
+  if (n % 2) return 0.0;
+  double r = 1.0;
+  for (int k = n - 1; k > 0; k -= 2) r *= (double)k; /* (n-1)!! */
+  return r * ipow(1.0 / 3.0, n / 2);
+}
+
+static double binom(int n, int k) {
+  double r = 1.0;
+  for (int j = 1; j <= k; ++j) r = r * (double)(n - k + j) / (double)j;
+  return r;
+}
+
+/* Gauss-Jordan inverse with partial pivoting of the leading n x n block of
+ * a QMAX x QMAX array.  Returns 0 on success, -1 if singular. */
+static int invert(int n, const double A[QMAX][QMAX], double Ainv[QMAX][QMAX]) {
+  double a[QMAX][2 * QMAX];
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < 2 * n; ++c)
+      a[r][c] = c < n ? A[r][c] : (c - n == r ? 1.0 : 0.0);
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+    if (fabs(a[piv][col]) < 1e-300) return -1;
+    if (piv != col)
+      for (int c = 0; c < 2 * n; ++c) {
+        double t = a[col][c];
+        a[col][c] = a[piv][c];
+        a[piv][c] = t;
+      }
+    double inv = 1.0 / a[col][col];
+    for (int c = 0; c < 2 * n; ++c) a[col][c] *= inv;
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      double f = a[r][col];
+      if (f == 0.0) continue;
+      for (int c = 0; c < 2 * n; ++c) a[r][c] -= f * a[col][c];
+    }
+  }
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) Ainv[r][c] = a[r][c + n];
+  return 0;
+}
+
+static void matvec(int n, const double A[QMAX][QMAX], const double* x,
+                   double* y) {
+  for (int r = 0; r < n; ++r) {
+    double s = 0.0;
+    for (int c = 0; c < n; ++c) s += A[r][c] * x[c];
+    y[r] = s;
+  }
+}
+
+/* Enumerate the set partitions of the multiset of axis labels given by
+ * exponent (a,b,c): positions 0..n-1 carry labels x..x y..y z..z; every
+ * partition of the positions is a restricted growth string. */
+static void enumerate_partitions(lattice_t* L, int k) {
+  int lab[6], n = 0;
+  for (int d = 0; d < 3; ++d)
+    for (int t = 0; t < L->expo[k][d]; ++t) lab[n++] = d;
+  L->npart[k] = 0;
+  if (n == 0) return;
+  int rgs[6] = {0};
+  for (;;) {
+    partition_t* p = &L->part[k][L->npart[k]++];
+    int nb = 0;
+    for (int j = 0; j < n; ++j)
+      if (rgs[j] + 1 > nb) nb = rgs[j] + 1;
+    p->nblocks = nb;
+    memset(p->e, 0, sizeof(p->e));
+    for (int j = 0; j < n; ++j) p->e[rgs[j]][lab[j]]++;
+    /* next restricted growth string */
+    int j = n - 1;
+    for (; j > 0; --j) {
+      int mx = 0;
+      for (int t = 0; t < j; ++t)
+        if (rgs[t] > mx) mx = rgs[t];
+      if (rgs[j] <= mx) {
+        rgs[j]++;
+        for (int t = j + 1; t < n; ++t) rgs[t] = 0;
+        break;
+      }
+    }
+    if (j == 0) break;
+  }
+}
+
+static int in_set(int stencil, int a, int b, int c) {
+  if (stencil == LBM_ORACLE_D2Q9) return c == 0;
+  if (stencil == LBM_ORACLE_D3Q19) return (a > 0) + (b > 0) + (c > 0) <= 2;
+  return 1;
+}
+
+/* Gram-Schmidt of the rows of B (polynomials in monomial coordinates) under
+ * the unweighted inner product <p,q> = sum_i p(xi_i) q(xi_i). */
+static void gram_schmidt(lattice_t* L, double B[QMAX][QMAX]) {
+  int q = L->q;
+  double V[QMAX][QMAX]; /* V[r][i] = p_r(xi_i) */
+  for (int r = 0; r < q; ++r)
+    for (int i = 0; i < q; ++i) {
+      double s = 0.0;
+      for (int k = 0; k < q; ++k) s += B[r][k] * L->M[k][i];
+      V[r][i] = s;
+    }
+  for (int r = 0; r < q; ++r)
+    for (int j = 0; j < r; ++j) {
+      double num = 0.0, den = 0.0;
+      for (int i = 0; i < q; ++i) {
+        num += V[r][i] * V[j][i];
+        den += V[j][i] * V[j][i];
+      }
+      double c = num / den;
+      for (int i = 0; i < q; ++i) V[r][i] -= c * V[j][i];
+      for (int k = 0; k < q; ++k) B[r][k] -= c * B[j][k];
+    }
+}
+
+static void add_row(lattice_t* L, double B[QMAX][QMAX], int* r, int grp,
+                    const int e[][3], const double* coef, int nterms) {
+  for (int k = 0; k < L->q; ++k) B[*r][k] = 0.0;
+  for (int t = 0; t < nterms; ++t)
+    B[*r][L->mono[e[t][0]][e[t][1]][e[t][2]]] += coef[t];
+  L->group[*r] = grp;
+  (*r)++;
+}
+
+static int build_lattice(int stencil) {
+  if (stencil < 0 || stencil > 2) return -1;
+  lattice_t* L = &g_lat[stencil];
+  if (L->ready) return 0;
+  memset(L, 0, sizeof(*L));
+  L->q = stencil == LBM_ORACLE_D2Q9 ? 9 : (stencil == LBM_ORACLE_D3Q19 ? 19 : 27);
+  L->d = stencil == LBM_ORACLE_D2Q9 ? 2 : 3;
+  for (int i = 0; i < L->q; ++i)
+    for (int d = 0; d < 3; ++d)
+      L->xi[i][d] = stencil == LBM_ORACLE_D2Q9 ? V2[i][d] : V3[i][d];
+  /* monomial exponent set, ordered by total degree then lexicographically */
+  int n = 0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c) L->mono[a][b][c] = -1;
+  for (int deg = 0; deg <= 6; ++deg)
+    for (int a = 2; a >= 0; --a)
+      for (int b = 2; b >= 0; --b)
+        for (int c = 2; c >= 0; --c) {
+          if (a + b + c != deg || !in_set(stencil, a, b, c)) continue;
+          L->expo[n][0] = a;
+          L->expo[n][1] = b;
+          L->expo[n][2] = c;
+          L->deg[n] = deg;
+          L->mono[a][b][c] = n++;
+        }
+  if (n != L->q) return -1;
+  /* M[k][i] = prod_d xi_{i,d}^{e_{k,d}}  (Eq. 2.8) */
+  for (int k = 0; k < L->q; ++k)
+    for (int i = 0; i < L->q; ++i)
+      L->M[k][i] = ipow(L->xi[i][0], L->expo[k][0]) *
+                   ipow(L->xi[i][1], L->expo[k][1]) *
+                   ipow(L->xi[i][2], L->expo[k][2]);
+  if (invert(L->q, L->M, L->Minv)) return -1;
+  /* background f0 = M^-1 m0 with m0 the moments of Psi(1, 0) (Sec. 2.4) */
+  double m0[QMAX];
+  for (int k = 0; k < L->q; ++k)
+    m0[k] = gauss_moment(L->expo[k][0]) * gauss_moment(L->expo[k][1]) *
+            gauss_moment(L->expo[k][2]);
+  matvec(L->q, L->Minv, m0, L->w);
+
+  /* homogeneous basis: 1 | x y z | shear (traceless 2nd order) | bulk
+   * (trace) | every monomial of order 3, 4, 5, 6 */
+  int r = 0;
+  {
+    static const int e0[1][3] = {{0, 0, 0}};
+    static const double one[1] = {1.0};
+    add_row(L, L->Pcm, &r, LBM_ORACLE_GROUP_CONSERVED, e0, one, 1);
+    for (int d = 0; d < L->d; ++d) {
+      int e1[1][3] = {{d == 0, d == 1, d == 2}};
+      add_row(L, L->Pcm, &r, LBM_ORACLE_GROUP_CONSERVED, e1, one, 1);
+    }
+    static const double pm[2] = {1.0, -1.0}, pp[3] = {1.0, 1.0, 1.0};
+    if (L->d == 2) {
+      static const int xx_yy[2][3] = {{2, 0, 0}, {0, 2, 0}};
+      static const int xy[1][3] = {{1, 1, 0}};
+      add_row(L, L->Pcm, &r, LBM_ORACLE_GROUP_SHEAR, xx_yy, pm, 2);
+      add_row(L, L->Pcm, &r, LBM_ORACLE_GROUP_SHEAR, xy, one, 1);
+      add_row(L, L->Pcm, &r, LBM_ORACLE_GROUP_BULK, xx_yy, pp, 2);
+    } else {
+      static const int xx_yy[2][3] = {{2, 0, 0}, {0, 2, 0}};
+      static const int xx_zz[2][3] = {{2, 0, 0}, {0, 0, 2}};
+      static const int xy[1][3] = {{1, 1, 0}}, xz[1][3] = {{1, 0, 1}},
+                       yz[1][3] = {{0, 1, 1}};
+      static const int tr[3][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}};
+      add_row(L, L->Pcm, &r, LBM_ORACLE_GROUP_SHEAR, xx_yy, pm, 2);
+      add_row(L, L->Pcm, &r, LBM_ORACLE_GROUP_SHEAR, xx_zz, pm, 2);
+      add_row(L, L->Pcm, &r, LBM_ORACLE_GROUP_SHEAR, xy, one, 1);
+      add_row(L, L->Pcm, &r, LBM_ORACLE_GROUP_SHEAR, xz, one, 1);
+      add_row(L, L->Pcm, &r, LBM_ORACLE_GROUP_SHEAR, yz, one, 1);
+      add_row(L, L->Pcm, &r, LBM_ORACLE_GROUP_BULK, tr, pp, 3);
+    }
+    for (int k = 0; k < L->q; ++k) {
+      if (L->deg[k] < 3) continue;
+      int ek[1][3] = {{L->expo[k][0], L->expo[k][1], L->expo[k][2]}};
+      add_row(L, L->Pcm, &r, LBM_ORACLE_GROUP_ORDER3 + L->deg[k] - 3, ek, one,
+              1);
+    }
+  }
+  if (r != L->q) return -1;
+  if (invert(L->q, L->Pcm, L->Pcminv)) return -1;
+  /* orthogonal raw-moment basis (O-MRT, Sec. 4.2): same rows, unweighted
+   * Gram-Schmidt in degree order */
+  memcpy(L->Praw, L->Pcm, sizeof(L->Praw));
+  gram_schmidt(L, L->Praw);
+  if (invert(L->q, L->Praw, L->Prawinv)) return -1;
+  for (int k = 0; k < L->q; ++k) enumerate_partitions(L, k);
+  L->ready = 1;
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* equilibria (Sec. 2.4, Eq. 2.12)                                      */
+/* ------------------------------------------------------------------ */
+
+/* Raw moment of Psi(rho, u) for exponent e:  rho prod_d E[(u_d + X)^e_d]
+ * with X ~ N(0, 1/3).  truncate != 0 drops every term of total degree > 2
+ * in u (the default second-order equilibrium, Sec. 4.2). */
+static double maxwell_raw_moment(const int* e, double rho, const double* u,
+                                 int truncate) {
+  double s = 0.0;
+  for (int ka = 0; ka <= e[0]; ++ka)
+    for (int kb = 0; kb <= e[1]; ++kb)
+      for (int kc = 0; kc <= e[2]; ++kc) {
+        int udeg = (e[0] - ka) + (e[1] - kb) + (e[2] - kc);
+        if (truncate && udeg > 2) continue;
+        s += binom(e[0], ka) * ipow(u[0], e[0] - ka) * gauss_moment(ka) *
+             binom(e[1], kb) * ipow(u[1], e[1] - kb) * gauss_moment(kb) *
+             binom(e[2], kc) * ipow(u[2], e[2] - kc) * gauss_moment(kc);
+      }
+  return rho * s;
+}
+
+/* Central moment of Psi(rho, u): rho prod_d E[X^e_d], velocity-free. */
+static double maxwell_central_moment(const int* e, double rho) {
+  return rho * gauss_moment(e[0]) * gauss_moment(e[1]) * gauss_moment(e[2]);
+}
+
+/* ------------------------------------------------------------------ */
+/* cumulants (Eq. 2.11): c(S) = sum over set partitions pi of S of      */
+/* (-1)^(|pi|-1) (|pi|-1)! prod_{B in pi} mu(B)  -- the coefficient     */
+/* extraction of log M; inverse mu(S) = sum_pi prod_B c(B).             */
+/* ------------------------------------------------------------------ */
+static double fact(int n) {
+  double r = 1.0;
+  for (int k = 2; k <= n; ++k) r *= k;
+  return r;
+}
+
+static double cumulant_from_mu(const partition_t* parts, int np,
+                               const double mu[3][3][3]) {
+  double s = 0.0;
+  for (int p = 0; p < np; ++p) {
+    int k = parts[p].nblocks;
+    double prod = ((k - 1) % 2 ? -1.0 : 1.0) * fact(k - 1);
+    for (int b = 0; b < k; ++b)
+      prod *= mu[parts[p].e[b][0]][parts[p].e[b][1]][parts[p].e[b][2]];
+    s += prod;
+  }
+  return s;
+}
+
+static double mu_from_cumulants(const partition_t* parts, int np,
+                                const double c[3][3][3]) {
+  double s = 0.0;
+  for (int p = 0; p < np; ++p) {
+    double prod = 1.0;
+    for (int b = 0; b < parts[p].nblocks; ++b)
+      prod *= c[parts[p].e[b][0]][parts[p].e[b][1]][parts[p].e[b][2]];
+    s += prod;
+  }
+  return s;
+}
+
+/* ------------------------------------------------------------------ */
+/* collision (Eq. 2.4-2.6)                                              */
+/* ------------------------------------------------------------------ */
+static double rate_of(const lbm_oracle_method* m, int grp) {
+  return grp < 0 ? 0.0 : m->rates[grp];
+}
+
+/* q* = q + S (q_eq - q) in the basis P, acting on monomial quantities v:
+ * v_out = P^-1 (P v + S P (v_eq - v)) */
+static void relax(const lattice_t* L, const lbm_oracle_method* m,
+                  const double P[QMAX][QMAX], const double Pinv[QMAX][QMAX],
+                  const double* v, const double* veq, double* vout) {
+  double qv[QMAX], qe[QMAX], qs[QMAX];
+  matvec(L->q, P, v, qv);
+  matvec(L->q, P, veq, qe);
+  for (int r = 0; r < L->q; ++r)
+    qs[r] = qv[r] + rate_of(m, L->group[r]) * (qe[r] - qv[r]);
+  matvec(L->q, Pinv, qs, vout);
+}
+
+static void central_matrix(const lattice_t* L, const double* u,
+                           double K[QMAX][QMAX]) {
+  for (int k = 0; k < L->q; ++k)
+    for (int i = 0; i < L->q; ++i)
+      K[k][i] = ipow(L->xi[i][0] - u[0], L->expo[k][0]) *
+                ipow(L->xi[i][1] - u[1], L->expo[k][1]) *
+                ipow(L->xi[i][2] - u[2], L->expo[k][2]);
+}
+
+static int collide_cell(const lattice_t* L, const lbm_oracle_method* m,
+                        const double* df, double* out) {
+  const int q = L->q;
+  /* conserved quantities from the deviations, Eq. 2.3, rho0 = 1 */
+  double drho = 0.0, j[3] = {0, 0, 0}, u[3];
+  for (int i = 0; i < q; ++i) {
+    drho += df[i];
+    for (int d = 0; d < 3; ++d) j[d] += L->xi[i][d] * df[i];
+  }
+  const double rho = 1.0 + drho;
+  for (int d = 0; d < 3; ++d) u[d] = j[d] / rho;
+  const int delta = m->equilibrium == LBM_ORACLE_EQ_DELTA;
+  double f[QMAX] = {0}, tmp[QMAX] = {0}, tmp2[QMAX] = {0}, veq[QMAX] = {0},
+         vout[QMAX] = {0};
+  static const double zero_u[3] = {0, 0, 0};
+
+  switch (m->space) {
+    case LBM_ORACLE_SPACE_NONE:
+      for (int i = 0; i < q; ++i) out[i] = df[i];
+      return 0;
+    case LBM_ORACLE_SPACE_POPULATIONS: {
+      /* SRT: f* = f + w (f_eq - f), f_eq = M^-1 m_eq (truncated) */
+      for (int k = 0; k < q; ++k)
+        veq[k] = maxwell_raw_moment(L->expo[k], rho, u, 1) -
+                 (delta ? maxwell_raw_moment(L->expo[k], 1.0, zero_u, 1) : 0.0);
+      matvec(q, L->Minv, veq, tmp); /* delta: df_eq ; absolute: f_eq */
+      const double om = m->rates[0];
+      for (int i = 0; i < q; ++i) {
+        if (delta)
+          out[i] = df[i] + om * (tmp[i] - df[i]);
+        else {
+          double fi = df[i] + L->w[i];
+          out[i] = fi + om * (tmp[i] - fi) - L->w[i];
+        }
+      }
+      return 0;
+    }
+    case LBM_ORACLE_SPACE_RAW: {
+      if (delta) { /* Eq. 2.5: dq = T(df), dq_eq = q_eq - q0 */
+        matvec(q, L->M, df, tmp);
+        for (int k = 0; k < q; ++k)
+          veq[k] = maxwell_raw_moment(L->expo[k], rho, u, 1) -
+                   maxwell_raw_moment(L->expo[k], 1.0, zero_u, 1);
+        relax(L, m, L->Praw, L->Prawinv, tmp, veq, vout);
+        matvec(q, L->Minv, vout, out);
+      } else { /* Eq. 2.6 */
+        for (int i = 0; i < q; ++i) f[i] = df[i] + L->w[i];
+        matvec(q, L->M, f, tmp);
+        for (int k = 0; k < q; ++k)
+          veq[k] = maxwell_raw_moment(L->expo[k], rho, u, 1);
+        relax(L, m, L->Praw, L->Prawinv, tmp, veq, vout);
+        matvec(q, L->Minv, vout, tmp2);
+        for (int i = 0; i < q; ++i) out[i] = tmp2[i] - L->w[i];
+      }
+      return 0;
+    }
+    case LBM_ORACLE_SPACE_CENTRAL: {
+      double K[QMAX][QMAX], Kinv[QMAX][QMAX];
+      central_matrix(L, u, K);
+      if (invert(q, K, Kinv)) return -1;
+      if (delta) { /* Eq. 2.5 with T = K(u): q0 = K(u) f0 */
+        double k0[QMAX];
+        matvec(q, K, df, tmp);
+        matvec(q, K, L->w, k0);
+        for (int k = 0; k < q; ++k)
+          veq[k] = maxwell_central_moment(L->expo[k], rho) - k0[k];
+        relax(L, m, L->Pcm, L->Pcminv, tmp, veq, vout);
+        matvec(q, Kinv, vout, out);
+      } else { /* Eq. 2.6 */
+        for (int i = 0; i < q; ++i) f[i] = df[i] + L->w[i];
+        matvec(q, K, f, tmp);
+        for (int k = 0; k < q; ++k)
+          veq[k] = maxwell_central_moment(L->expo[k], rho);
+        relax(L, m, L->Pcm, L->Pcminv, tmp, veq, vout);
+        matvec(q, Kinv, vout, tmp2);
+        for (int i = 0; i < q; ++i) out[i] = tmp2[i] - L->w[i];
+      }
+      return 0;
+    }
+    case LBM_ORACLE_SPACE_CUMULANT: {
+      if (delta) return -3; /* no zero-centered cumulants (Sec. 2.4, 3) */
+      double mu[3][3][3], c[3][3][3];
+      for (int a = 0; a < 27; ++a) (&mu[0][0][0])[a] = NAN, (&c[0][0][0])[a] = NAN;
+      for (int i = 0; i < q; ++i) f[i] = df[i] + L->w[i];
+      matvec(q, L->M, f, tmp);
+      const double rho_a = tmp[0]; /* = m_000 */
+      double v[QMAX] = {0};
+      for (int k = 0; k < q; ++k) {
+        const int* e = L->expo[k];
+        mu[e[0]][e[1]][e[2]] = tmp[k] / rho_a;
+      }
+      for (int k = 0; k < q; ++k) {
+        const int* e = L->expo[k];
+        if (L->deg[k] == 0)
+          v[k] = rho_a;
+        else if (L->deg[k] == 1)
+          v[k] = mu[e[0]][e[1]][e[2]];
+        else
+          v[k] = rho_a * cumulant_from_mu(L->part[k], L->npart[k], mu);
+        /* equilibrium cumulants of Psi: C_eq = rho c_s^2 on the diagonal
+         * of order 2, zero above; orders 0 and 1 are conserved */
+        if (L->deg[k] <= 1)
+          veq[k] = v[k];
+        else
+          veq[k] = (L->deg[k] == 2 && (e[0] == 2 || e[1] == 2 || e[2] == 2))
+                       ? rho_a / 3.0
+                       : 0.0;
+      }
+      relax(L, m, L->Pcm, L->Pcminv, v, veq, vout);
+      for (int k = 0; k < q; ++k) {
+        const int* e = L->expo[k];
+        c[e[0]][e[1]][e[2]] =
+            L->deg[k] >= 2 ? vout[k] / rho_a : (L->deg[k] == 1 ? v[k] : 1.0);
+      }
+      for (int k = 0; k < q; ++k) {
+        tmp2[k] = L->deg[k] == 0
+                      ? rho_a
+                      : rho_a * mu_from_cumulants(L->part[k], L->npart[k], c);
+      }
+      matvec(q, L->Minv, tmp2, f);
+      for (int i = 0; i < q; ++i) out[i] = f[i] - L->w[i];
+      return 0;
+    }
+  }
+  return -1;
+}
+
+static int check_method(const lbm_oracle_method* m) {
+  if (!m || build_lattice(m->stencil)) return -1;
+  if (m->space < 0 || m->space > 4) return -1;
+  if (m->equilibrium != LBM_ORACLE_EQ_DELTA &&
+      m->equilibrium != LBM_ORACLE_EQ_ABSOLUTE)
+    return -1;
+  if (m->space == LBM_ORACLE_SPACE_CUMULANT &&
+      m->equilibrium == LBM_ORACLE_EQ_DELTA)
+    return -3;
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* exported API                                                         */
+/* ------------------------------------------------------------------ */
+int lbm_oracle_lattice(int stencil, int* q, int* d, int* xi, double* w,
+                       int* expo) {
+  if (build_lattice(stencil)) return -1;
+  const lattice_t* L = &g_lat[stencil];
+  if (q) *q = L->q;
+  if (d) *d = L->d;
+  for (int i = 0; i < L->q; ++i)
+    for (int k = 0; k < 3; ++k) {
+      if (xi) xi[i * 3 + k] = L->xi[i][k];
+      if (expo) expo[i * 3 + k] = L->expo[i][k];
+    }
+  if (w)
+    for (int i = 0; i < L->q; ++i) w[i] = L->w[i];
+  return 0;
+}
+
+int lbm_oracle_matrices(int stencil, double* M, double* Minv, double* Praw,
+                        double* Pcm, int* group) {
+  if (build_lattice(stencil)) return -1;
+  const lattice_t* L = &g_lat[stencil];
+  int q = L->q;
+  for (int r = 0; r < q; ++r) {
+    for (int c = 0; c < q; ++c) {
+      if (M) M[r * q + c] = L->M[r][c];
+      if (Minv) Minv[r * q + c] = L->Minv[r][c];
+      if (Praw) Praw[r * q + c] = L->Praw[r][c];
+      if (Pcm) Pcm[r * q + c] = L->Pcm[r][c];
+    }
+    if (group) group[r] = L->group[r];
+  }
+  return 0;
+}
+
+int lbm_oracle_central_matrix(int stencil, const double* u, double* K) {
+  if (build_lattice(stencil) || !u || !K) return -1;
+  const lattice_t* L = &g_lat[stencil];
+  double Km[QMAX][QMAX];
+  central_matrix(L, u, Km);
+  for (int r = 0; r < L->q; ++r)
+    for (int c = 0; c < L->q; ++c) K[r * L->q + c] = Km[r][c];
+  return 0;
+}
+
+int lbm_oracle_cumulants(int stencil, const double* f, double* out) {
+  if (build_lattice(stencil) || !f || !out) return -1;
+  const lattice_t* L = &g_lat[stencil];
+  double m[QMAX], mu[3][3][3];
+  for (int a = 0; a < 27; ++a) (&mu[0][0][0])[a] = NAN;
+  matvec(L->q, L->M, f, m);
+  for (int k = 0; k < L->q; ++k)
+    mu[L->expo[k][0]][L->expo[k][1]][L->expo[k][2]] = m[k] / m[0];
+  for (int k = 0; k < L->q; ++k) {
+    const int* e = L->expo[k];
+    if (L->deg[k] == 0)
+      out[k] = m[0];
+    else if (L->deg[k] == 1)
+      out[k] = mu[e[0]][e[1]][e[2]];
+    else
+      out[k] = m[0] * cumulant_from_mu(L->part[k], L->npart[k], mu);
+  }
+  return 0;
+}
+
+int lbm_oracle_moments_from_cumulants(int stencil, const double* c_in,
+                                      double* m) {
+  if (build_lattice(stencil) || !c_in || !m) return -1;
+  const lattice_t* L = &g_lat[stencil];
+  double c[3][3][3];
+  for (int a = 0; a < 27; ++a) (&c[0][0][0])[a] = NAN;
+  const double rho = c_in[0];
+  for (int k = 0; k < L->q; ++k) {
+    const int* e = L->expo[k];
+    c[e[0]][e[1]][e[2]] = L->deg[k] >= 2 ? c_in[k] / rho : c_in[k];
+  }
+  c[0][0][0] = 1.0;
+  for (int k = 0; k < L->q; ++k)
+    m[k] = L->deg[k] == 0
+               ? rho
+               : rho * mu_from_cumulants(L->part[k], L->npart[k], c);
+  return 0;
+}
+
+double lbm_oracle_cumulant_of(const double* mu27, int a, int b, int c) {
+  if (build_lattice(LBM_ORACLE_D3Q27)) return NAN;
+  if (a < 0 || a > 2 || b < 0 || b > 2 || c < 0 || c > 2) return NAN;
+  const lattice_t* L = &g_lat[LBM_ORACLE_D3Q27];
+  double mu[3][3][3];
+  memcpy(mu, mu27, sizeof(mu));
+  int k = L->mono[a][b][c];
+  if (L->deg[k] == 0) return 0.0;
+  return cumulant_from_mu(L->part[k], L->npart[k], mu);
+}
+
+int lbm_oracle_collide(const lbm_oracle_method* m, int64_t ncells,
+                       const double* df_in, double* df_out) {
+  int rc = check_method(m);
+  if (rc) return rc;
+  const lattice_t* L = &g_lat[m->stencil];
+  for (int64_t c = 0; c < ncells; ++c) {
+    double tmp[QMAX];
+    rc = collide_cell(L, m, df_in + c * L->q, tmp);
+    if (rc) return rc;
+    memcpy(df_out + c * L->q, tmp, sizeof(double) * L->q);
+  }
+  return 0;
+}
+
+static void equilibrium_cell(const lattice_t* L, const lbm_oracle_method* m,
+                             double rho, const double* u, double* out) {
+  /* raw-moment methods relax to the truncated equilibrium; central-moment
+   * and cumulant methods to the full Maxwellian (velocity-free central
+   * moments), so each method's own equilibrium is a collision fixed point */
+  static const double zero_u[3] = {0, 0, 0};
+  const int trunc = m->space == LBM_ORACLE_SPACE_RAW ||
+                    m->space == LBM_ORACLE_SPACE_POPULATIONS ||
+                    m->space == LBM_ORACLE_SPACE_NONE;
+  double dm[QMAX];
+  for (int k = 0; k < L->q; ++k)
+    dm[k] = maxwell_raw_moment(L->expo[k], rho, u, trunc) -
+            maxwell_raw_moment(L->expo[k], 1.0, zero_u, trunc);
+  matvec(L->q, L->Minv, dm, out);
+}
+
+int lbm_oracle_equilibrium(const lbm_oracle_method* m, int64_t ncells,
+                           const double* rho, const double* u, double* df_out) {
+  int rc = check_method(m);
+  if (rc) return rc;
+  const lattice_t* L = &g_lat[m->stencil];
+  for (int64_t c = 0; c < ncells; ++c)
+    equilibrium_cell(L, m, rho[c], u + 3 * c, df_out + c * L->q);
+  return 0;
+}
+
+int lbm_oracle_init(const lbm_oracle_method* m, const int64_t* dims,
+                    const double* rho, const double* u, double* df) {
+  int rc = check_method(m);
+  if (rc) return rc;
+  const lattice_t* L = &g_lat[m->stencil];
+  const int64_t N = dims[0] * dims[1] * dims[2];
+  for (int64_t c = 0; c < N; ++c) {
+    double uc[3] = {u[c], u[N + c], L->d == 3 ? u[2 * N + c] : 0.0}, out[QMAX];
+    equilibrium_cell(L, m, rho[c], uc, out);
+    for (int i = 0; i < L->q; ++i) df[i * N + c] = out[i];
+  }
+  return 0;
+}
+
+int lbm_oracle_step(const lbm_oracle_method* m, const int64_t* dims,
+                    double* df, int64_t nsteps, int nthreads) {
+  int rc = check_method(m);
+  if (rc) return rc;
+  const lattice_t* L = &g_lat[m->stencil];
+  const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+  if (nx <= 0 || ny <= 0 || nz <= 0) return -1;
+  if (L->d == 2 && nz != 1) return -1;
+  const int64_t N = nx * ny * nz;
+  const int q = L->q;
+  double* out = (double*)malloc(sizeof(double) * q * N);
+  if (!out) return -1;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  int err = 0;
+  for (int64_t s = 0; s < nsteps && !err; ++s) {
+#pragma omp parallel for schedule(static) reduction(| : err)
+    for (int64_t c = 0; c < N; ++c) {
+      const int64_t x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
+      double in[QMAX], post[QMAX];
+      for (int i = 0; i < q; ++i) in[i] = df[i * N + c];
+      if (collide_cell(L, m, in, post)) err |= 1;
+      /* Eq. 2.1b: f_i(x + xi_i, t + 1) = f*_i(x, t), periodic */
+      for (int i = 0; i < q; ++i) {
+        int64_t xd = (x + L->xi[i][0] + nx) % nx;
+        int64_t yd = (y + L->xi[i][1] + ny) % ny;
+        int64_t zd = (z + L->xi[i][2] + nz) % nz;
+        out[i * N + (zd * ny + yd) * nx + xd] = post[i];
+      }
+    }
+    memcpy(df, out, sizeof(double) * q * N);
+  }
+  free(out);
+  return err ? -1 : 0;
+}
+
+int lbm_oracle_macroscopic(const lbm_oracle_method* m, const int64_t* dims,
+                           const double* df, double* rho, double* u) {
+  if (!m || build_lattice(m->stencil)) return -1;
+  const lattice_t* L = &g_lat[m->stencil];
+  const int64_t N = dims[0] * dims[1] * dims[2];
+  for (int64_t c = 0; c < N; ++c) {
+    double drho = 0.0, j[3] = {0, 0, 0};
+    for (int i = 0; i < L->q; ++i) {
+      drho += df[i * N + c];
+      for (int d = 0; d < 3; ++d) j[d] += L->xi[i][d] * df[i * N + c];
+    }
+    rho[c] = 1.0 + drho;
+    for (int d = 0; d < L->d; ++d) u[d * N + c] = j[d] / rho[c];
+  }
+  return 0;
+}

@@ -1,0 +1,129 @@
+/*
+ * lbm_oracle.h -- plain, slow FP64 CPU oracle for the zero-centered MRT
+ * lattice Boltzmann step (Hennig, Holzer, Ruede, arXiv 2211.02435).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this library: only tests/, the smoke check and the CPU-baseline leg
+ * of the benchmark do.  It shares no code, header, table or generator with
+ * the CUDA library.  Where the two must agree on an interface (enum codes,
+ * velocity order, array layout) each side writes its own copy of that
+ * documented interface.
+ *
+ * Every function follows the paper's definitions literally, with explicit
+ * dense matrices (M, M^-1, K(u), basis matrices) instead of the Chimera
+ * transforms the GPU path uses:
+ *   populations, zero-centering, conserved quantities   Sec. 2.1, Eq. 2.2-2.3
+ *   MRT collision (general / deviation-only / absolute)  Sec. 2.2, Eq. 2.4-2.6
+ *   raw moments, central moments, cumulants              Sec. 2.3, Eq. 2.7-2.11
+ *   Maxwellian equilibrium and background                Sec. 2.4, Eq. 2.12
+ *   second-order truncation of raw equilibrium moments   Sec. 4.2 (Table 1 setup)
+ *   streaming                                            Eq. 2.1b
+ *
+ * Layout: populations are zero-centered deviations df_i = f_i - w_i stored
+ * structure-of-arrays, df[i*N + (z*Ny + y)*Nx + x], i in the velocity order
+ * below.  The state passed to lbm_oracle_step is the pre-collision f(t).
+ *
+ * Velocity order (shared interface, documented in include/lbm.h too):
+ *   D2Q9 : 0 (0,0); 1 (1,0); 2 (-1,0); 3 (0,1); 4 (0,-1);
+ *          5 (1,1); 6 (-1,-1); 7 (1,-1); 8 (-1,1)
+ *   D3Q19: 0 rest; 1..6 faces (+x,-x,+y,-y,+z,-z);
+ *          7..18 edges (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1)
+ *                      (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+ *   D3Q27: D3Q19 followed by corners 19..26 (1,1,1) (-1,-1,-1) (1,1,-1)
+ *          (-1,-1,1) (1,-1,1) (-1,1,-1) (1,-1,-1) (-1,1,1)
+ *   Opposite pairs are adjacent: for i > 0, ibar = i + 1 if i is odd, i - 1
+ *   if i is even.
+ */
+#ifndef LBM_ORACLE_H
+#define LBM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* stencils */
+#define LBM_ORACLE_D2Q9 0
+#define LBM_ORACLE_D3Q19 1
+#define LBM_ORACLE_D3Q27 2
+/* collision spaces; NONE = identity collision (pure streaming) */
+#define LBM_ORACLE_SPACE_POPULATIONS 0
+#define LBM_ORACLE_SPACE_RAW 1
+#define LBM_ORACLE_SPACE_CENTRAL 2
+#define LBM_ORACLE_SPACE_CUMULANT 3
+#define LBM_ORACLE_SPACE_NONE 4
+/* equilibrium format: deviation-only (Eq. 2.5) or absolute (Eq. 2.6) */
+#define LBM_ORACLE_EQ_DELTA 0
+#define LBM_ORACLE_EQ_ABSOLUTE 1
+/* rate groups (row groups of the polynomial bases) */
+#define LBM_ORACLE_GROUP_CONSERVED -1
+#define LBM_ORACLE_GROUP_SHEAR 0
+#define LBM_ORACLE_GROUP_BULK 1
+#define LBM_ORACLE_GROUP_ORDER3 2 /* order k -> group k - 1 */
+
+typedef struct {
+  int stencil;     /* LBM_ORACLE_D2Q9 / D3Q19 / D3Q27 */
+  int space;       /* LBM_ORACLE_SPACE_* */
+  int equilibrium; /* LBM_ORACLE_EQ_* */
+  double rates[6]; /* shear, bulk, order 3, order 4, order 5, order 6 */
+} lbm_oracle_method;
+
+/* Error codes: 0 ok, -1 invalid argument, -3 inadmissible combination. */
+
+/* Lattice description: q, d, velocities xi[q][3], weights w[q] computed as
+ * M^-1 m0 (Sec. 2.4), monomial exponents expo[q][3] ordered by degree. */
+int lbm_oracle_lattice(int stencil, int* q, int* d, int* xi, double* w,
+                       int* expo);
+
+/* Dense matrices, row-major q x q: monomial raw-moment matrix M (Eq. 2.8),
+ * its inverse, the orthogonal raw basis Praw (rows = polynomials in monomial
+ * coordinates, unweighted Gram-Schmidt), the homogeneous basis Pcm used for
+ * central moments and cumulants, and the rate group of each basis row. */
+int lbm_oracle_matrices(int stencil, double* M, double* Minv, double* Praw,
+                        double* Pcm, int* group);
+
+/* Central-moment matrix K(u)[k][i] = prod_d (xi_{i,d} - u_d)^{e_{k,d}}
+ * (Sec. 2.3.2), row-major q x q. */
+int lbm_oracle_central_matrix(int stencil, const double* u, double* K);
+
+/* Cumulants of one absolute population vector f (Eq. 2.11, via the
+ * set-partition form of log M).  out[k] for monomial k: order 0 -> rho,
+ * order 1 -> u_d, order >= 2 -> rescaled cumulant C = rho * c. */
+int lbm_oracle_cumulants(int stencil, const double* f, double* out);
+
+/* Inverse: monomial raw moments m from (rho, u, C) in the layout above. */
+int lbm_oracle_moments_from_cumulants(int stencil, const double* c_in,
+                                      double* m);
+
+/* Joint cumulant of a multiset given normalized raw moments mu[a][b][c]
+ * (a,b,c in 0..2, mu[0][0][0] = 1), exponents (a,b,c). */
+double lbm_oracle_cumulant_of(const double* mu27, int a, int b, int c);
+
+/* One collision of ncells independent cells.  df_in/df_out are cell-major
+ * [ncells][q] zero-centered deviations (may alias). */
+int lbm_oracle_collide(const lbm_oracle_method* m, int64_t ncells,
+                       const double* df_in, double* df_out);
+
+/* The method's equilibrium, as deviations from w, for given rho and u
+ * (cell-major: rho[ncells], u[ncells][3], df_out[ncells][q]). */
+int lbm_oracle_equilibrium(const lbm_oracle_method* m, int64_t ncells,
+                           const double* rho, const double* u, double* df_out);
+
+/* Fill an SoA state df[q][N] with the equilibrium of rho[N], u[3][N]
+ * (u SoA: u[d*N + cell]). */
+int lbm_oracle_init(const lbm_oracle_method* m, const int64_t* dims,
+                    const double* rho, const double* u, double* df);
+
+/* nsteps of collide (Eq. 2.1a) then stream (Eq. 2.1b) with periodic wrap,
+ * in place on the SoA pre-collision state df[q][N]. */
+int lbm_oracle_step(const lbm_oracle_method* m, const int64_t* dims,
+                    double* df, int64_t nsteps, int nthreads);
+
+/* Density and velocity (Eq. 2.3) of the SoA state: rho[N], u[3][N]. */
+int lbm_oracle_macroscopic(const lbm_oracle_method* m, const int64_t* dims,
+                           const double* df, double* rho, double* u);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
