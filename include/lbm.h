@@ -1,0 +1,192 @@
+/*
+ * lbm.h -- C ABI of the B300 (sm_103a) zero-centered MRT lattice Boltzmann
+ * library (liblbm.so).  Method: Hennig, Holzer, Ruede, "Advanced Automatic
+ * Code Generation for Multiple Relaxation-Time Lattice Boltzmann Methods"
+ * (arXiv 2211.02435).
+ *
+ * One call of lbm_step advances every cell by the fused pull-stream +
+ * collide update of Eq. 2.1: gather the populations (Eq. 2.1b, pull or
+ * in-place AA pattern, Sec. 4.3), collide (Eq. 2.4-2.6) in raw-moment,
+ * central-moment or cumulant space (Sec. 2.3) using the raw-moment Chimera
+ * (Eq. 4.1), the binomial raw<->central Chimera (Eq. 4.3-4.4), the
+ * central<->cumulant relations (Eq. 4.5) and the split backward transform
+ * (Eq. 4.2), and store.  Populations are stored zero-centered,
+ * df_i = f_i - w_i (Sec. 2.1).
+ *
+ * Conventions shared by every call
+ *  - Return value: LBM_OK (0) or a negative LBM_ERR_* code.  No C++
+ *    exception crosses the ABI.  lbm_error_string() names a code.
+ *  - Ownership: the library owns the device state it allocates in
+ *    lbm_create (freed by lbm_destroy).  The caller owns every buffer it
+ *    passes in; the library keeps no pointer to it after the call returns.
+ *  - on_device = 1: the pointer is device memory of the context's GPU (e.g.
+ *    torch tensor.data_ptr()); 0: host memory.  Host-pointer calls copy
+ *    through the context's stream and synchronise it before returning.
+ *  - All device work is enqueued on params.stream (a cudaStream_t; NULL =
+ *    legacy default stream).  lbm_step returns without synchronising.
+ *  - There is no CPU fallback: without a usable CUDA device every call that
+ *    needs one returns LBM_ERR_CUDA.
+ *  - Field layout (inputs and outputs): structure of arrays with x fastest,
+ *    cell index c = (z*Ny + y)*Nx + x.  Scalars: a[c]; vectors: a[d*N + c]
+ *    with d = 0..D-1 (D = 2 for D2Q9, 3 otherwise); populations: a[i*N + c].
+ *  - Velocity order i (opposite pairs adjacent):
+ *      D2Q9 : 0 (0,0); 1 (1,0); 2 (-1,0); 3 (0,1); 4 (0,-1);
+ *             5 (1,1); 6 (-1,-1); 7 (1,-1); 8 (-1,1)
+ *      D3Q19: 0 rest; 1..6 (1,0,0) (-1,0,0) (0,1,0) (0,-1,0) (0,0,1) (0,0,-1);
+ *             7..18 (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1)
+ *                   (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+ *      D3Q27: the D3Q19 order followed by 19..26 (1,1,1) (-1,-1,-1) (1,1,-1)
+ *             (-1,-1,1) (1,-1,1) (-1,1,-1) (1,-1,-1) (-1,1,1)
+ *  - Time: after n steps the canonical state is the pre-collision
+ *    (post-streaming) f(n) of Eq. 2.1, f(0) being what lbm_init_velocity or
+ *    lbm_set_populations installed.  Every read-out call returns f(n) or
+ *    quantities of f(n), whatever the streaming pattern and its parity.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---- */
+#define LBM_OK 0
+#define LBM_ERR_INVALID -1        /* bad argument, size or NULL pointer      */
+#define LBM_ERR_UNSUPPORTED -2    /* valid request this build does not serve */
+#define LBM_ERR_INADMISSIBLE -3   /* combination the method forbids (Sec. 3) */
+#define LBM_ERR_OOM -4            /* device allocation failed                */
+#define LBM_ERR_CUDA -5           /* CUDA runtime error / no device          */
+#define LBM_ERR_DIVERGED -6       /* non-finite populations detected         */
+#define LBM_ERR_STATE_MISMATCH -7 /* checkpoint does not fit this context    */
+
+/* ---- method specification (Sec. 3, Fig. 2) ---- */
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 } lbm_stencil;
+
+/* Collision space (Sec. 2.3).  POPULATIONS is single relaxation time (BGK):
+ * it is run as raw-moment MRT with every rate equal to rates[0]. */
+typedef enum {
+  LBM_SPACE_POPULATIONS = 0,
+  LBM_SPACE_RAW = 1,      /* orthogonal raw moments, unweighted (O-MRT)  */
+  LBM_SPACE_CENTRAL = 2,  /* polynomial central moments (CM)             */
+  LBM_SPACE_CUMULANT = 3  /* polynomial cumulants (K)                    */
+} lbm_space;
+
+/* Equilibrium format (Sec. 2.2): relax deviations against the
+ * delta-equilibrium (Eq. 2.5) or the absolute equilibrium (Eq. 2.6).
+ * Cumulant space admits only LBM_EQ_ABSOLUTE (Sec. 2.4): the other is
+ * rejected with LBM_ERR_INADMISSIBLE.  Raw-moment methods use the
+ * continuous Maxwellian truncated at second order in u (Sec. 4.2);
+ * central-moment and cumulant methods the untruncated Maxwellian. */
+typedef enum { LBM_EQ_DELTA = 0, LBM_EQ_ABSOLUTE = 1 } lbm_equilibrium;
+
+/* Population storage.  F64 computes in FP64, the others in FP32.  The
+ * *_DELTA forms store h_i = round_rn(df_i * 2^s_i) in FP16 / BF16 with the
+ * per-direction scale exponent s_i = round(-log2 w_i):
+ *   D2Q9 1,3,5; D3Q19 2,4,5; D3Q27 2,4,6,8 (rest, |xi|^2 = 1, 2, 3). */
+typedef enum {
+  LBM_STORE_F64 = 0,
+  LBM_STORE_F32 = 1,
+  LBM_STORE_F16_DELTA = 2,
+  LBM_STORE_BF16_DELTA = 3
+} lbm_storage;
+
+/* Streaming pattern (Sec. 4.3): pull with two buffers, or the in-place
+ * AA pattern with one buffer. */
+typedef enum { LBM_PULL = 0, LBM_AA = 1 } lbm_streaming;
+
+#define LBM_PERIODIC 0 /* the only boundary; others -> LBM_ERR_UNSUPPORTED */
+
+/* Relaxation-rate slots (Sec. 2.2 matrix S, grouped): the rate of the
+ * traceless second-order quantities (shear), of the second-order trace
+ * (bulk), and of all quantities of order 3, 4, 5 and 6.  Conserved
+ * quantities are not relaxed.  Shear rate from viscosity:
+ * nu = (1/omega - 1/2) / 3. */
+enum {
+  LBM_RATE_SHEAR = 0,
+  LBM_RATE_BULK = 1,
+  LBM_RATE_ORDER3 = 2,
+  LBM_RATE_ORDER4 = 3,
+  LBM_RATE_ORDER5 = 4,
+  LBM_RATE_ORDER6 = 5
+};
+
+typedef struct {
+  int stencil;      /* lbm_stencil                                       */
+  int space;        /* lbm_space                                         */
+  int equilibrium;  /* lbm_equilibrium                                   */
+  int storage;      /* lbm_storage                                       */
+  int streaming;    /* lbm_streaming                                     */
+  double rates[6];  /* see LBM_RATE_*; each in (0, 2]                     */
+  int64_t dims[3];  /* Nx, Ny, Nz (Nz = 1 for D2Q9); each >= 1, Ny, Nz <=
+                       65535, Nx*Ny*Nz < 2^31                            */
+  int boundary;     /* LBM_PERIODIC                                      */
+  void* stream;     /* cudaStream_t for every enqueue; NULL = default     */
+} lbm_params;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Create a context and allocate its device state (pull: 2 buffers, AA: 1,
+ * each q*N elements of the storage type).  Populations start at zero
+ * (rest state rho = 1, u = 0).  Errors: INVALID (NULL, bad enum, dims or
+ * rates), INADMISSIBLE (cumulant + delta equilibrium), UNSUPPORTED
+ * (boundary), OOM, CUDA. */
+int lbm_create(lbm_ctx** out, const lbm_params* params);
+
+/* Install f(0) = the method's equilibrium (the collision's fixed point)
+ * for density rho[N] (NULL: rho = 1) and velocity u[D*N], FP64, field
+ * layout above.  Resets the step counter to 0.  Errors: INVALID, CUDA. */
+int lbm_init_velocity(lbm_ctx* ctx, const double* rho, const double* u,
+                      int on_device);
+
+/* Advance n >= 0 steps on the context's stream (asynchronous).
+ * Errors: INVALID, CUDA. */
+int lbm_step(lbm_ctx* ctx, int64_t n);
+
+/* Density rho[N] and velocity u[D*N] of f(n), Eq. 2.3, written as FP64.
+ * Either pointer may be NULL.  Errors: INVALID, CUDA. */
+int lbm_macroscopic(lbm_ctx* ctx, double* rho, double* u, int on_device);
+
+/* Read / write the canonical zero-centered populations df[q*N] of f(n)
+ * in FP64 (writing encodes them into the storage type and resets the AA
+ * parity; the step counter is kept).  Errors: INVALID, CUDA. */
+int lbm_get_populations(lbm_ctx* ctx, double* df, int on_device);
+int lbm_set_populations(lbm_ctx* ctx, const double* df, int on_device);
+
+/* Global FP64 reductions over f(n), deterministic (fixed-order two-pass):
+ * out[0] sum(rho - 1), out[1..3] sum(rho u_d), out[4] sum(rho |u|^2 / 2),
+ * out[5] max |u|, out[6] number of cells with a non-finite population,
+ * out[7] number of cells.  Synchronises the stream.  Uses a per-context
+ * device scratch buffer allocated at create time.  Errors: INVALID, CUDA,
+ * DIVERGED (out is still filled when out[6] > 0). */
+int lbm_invariants(lbm_ctx* ctx, double out[8]);
+
+/* Checkpoint: the raw device buffer plus a header (method, dims, storage,
+ * parity, step counter).  lbm_state_bytes gives the size; get/set copy
+ * through host memory.  A state from a context with other parameters is
+ * refused with STATE_MISMATCH. */
+int64_t lbm_state_bytes(const lbm_ctx* ctx);
+int lbm_get_state(lbm_ctx* ctx, void* buf, size_t bytes);
+int lbm_set_state(lbm_ctx* ctx, const void* buf, size_t bytes);
+
+/* Current step counter and AA parity (0 even, 1 odd). */
+int lbm_get_time(const lbm_ctx* ctx, int64_t* step, int* parity);
+
+/* Change the relaxation rates (Sec. 3: rates may stay symbolic until run
+ * time).  Errors: INVALID. */
+int lbm_set_rates(lbm_ctx* ctx, const double rates[6]);
+
+/* Change the stream later work is enqueued on. */
+int lbm_set_stream(lbm_ctx* ctx, void* stream);
+
+/* Free the context and its device memory.  NULL is ignored. */
+void lbm_destroy(lbm_ctx* ctx);
+
+const char* lbm_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,443 @@
+// lbm_api.cu -- C ABI (include/lbm.h): context management, validation,
+// buffer bookkeeping of the pull / AA streaming patterns and dispatch to
+// the per-(stencil, storage) kernel instantiations.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+namespace {
+
+using lbm::AuxArgs;
+using lbm::Geo;
+using lbm::StepArgs;
+
+typedef void (*step_fn)(const StepArgs&);
+typedef void (*aux_fn)(const AuxArgs&);
+
+const step_fn kStep[3][4] = {
+    {lbm::launch_step_0_0, lbm::launch_step_0_1, lbm::launch_step_0_2, lbm::launch_step_0_3},
+    {lbm::launch_step_1_0, lbm::launch_step_1_1, lbm::launch_step_1_2, lbm::launch_step_1_3},
+    {lbm::launch_step_2_0, lbm::launch_step_2_1, lbm::launch_step_2_2, lbm::launch_step_2_3}};
+const aux_fn kAux[3][4] = {
+    {lbm::launch_aux_0_0, lbm::launch_aux_0_1, lbm::launch_aux_0_2, lbm::launch_aux_0_3},
+    {lbm::launch_aux_1_0, lbm::launch_aux_1_1, lbm::launch_aux_1_2, lbm::launch_aux_1_3},
+    {lbm::launch_aux_2_0, lbm::launch_aux_2_1, lbm::launch_aux_2_2, lbm::launch_aux_2_3}};
+
+constexpr int G_PULL = 0, G_LOCAL = 1, G_AAODD = 2;
+constexpr uint64_t kStateMagic = 0x4c424d3253544154ull;  // "LBM2STAT"
+
+int q_of(int st) { return st == LBM_D2Q9 ? 9 : (st == LBM_D3Q19 ? 19 : 27); }
+int elem_bytes(int storage) {
+  return storage == LBM_STORE_F64 ? 8 : (storage == LBM_STORE_F32 ? 4 : 2);
+}
+
+struct StateHeader {
+  uint64_t magic;
+  int32_t stencil, space, equilibrium, storage, streaming, parity;
+  int64_t dims[3];
+  int64_t t;
+  int64_t payload;
+};
+
+}  // namespace
+
+struct lbm_ctx {
+  lbm_params p;
+  int q, d;
+  Geo g;
+  int eb;
+  void* buf[2];
+  int cur;     // pull: buffer holding the newest post-collision state
+  int parity;  // AA: number of completed steps mod 2
+  int64_t t;
+  cudaStream_t stream;
+  double* part;  // invariants scratch: nparts rows of 8 doubles, then 8
+  int nparts;
+  int space;  // effective collision space (POPULATIONS -> RAW)
+  double rates[6];
+  int reg;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
+
+int gather_mode(const lbm_ctx* c) {
+  if (c->p.streaming == LBM_PULL) return G_PULL;
+  return c->parity ? G_AAODD : G_LOCAL;
+}
+void* state_buf(const lbm_ctx* c) {
+  return c->p.streaming == LBM_PULL ? c->buf[c->cur] : c->buf[0];
+}
+
+void set_effective_rates(lbm_ctx* c, const double* r) {
+  for (int k = 0; k < 6; ++k) c->rates[k] = c->p.space == LBM_SPACE_POPULATIONS ? r[0] : r[k];
+  c->space = c->p.space == LBM_SPACE_POPULATIONS ? LBM_SPACE_RAW : c->p.space;
+  c->reg = 1;
+  for (int k = 1; k < 6; ++k)
+    if (c->rates[k] != 1.0) c->reg = 0;
+}
+
+int valid_rates(const double* r) {
+  for (int k = 0; k < 6; ++k)
+    if (!(r[k] > 0.0 && r[k] <= 2.0)) return 0;
+  return 1;
+}
+
+AuxArgs aux_base(const lbm_ctx* c, int op) {
+  AuxArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.op = op;
+  a.buf = state_buf(c);
+  a.g = c->g;
+  a.storage = c->p.storage;
+  a.space = c->space;
+  a.gather_mode = gather_mode(c);
+  a.stream = c->stream;
+  return a;
+}
+
+// Copy a host array to a temporary device buffer (or pass a device pointer
+// through).  The caller frees *tmp after synchronising the stream.
+int stage_in(const lbm_ctx* c, const double* p, size_t n, int on_device, const double** dev,
+             double** tmp) {
+  *tmp = nullptr;
+  if (!p || on_device) {
+    *dev = p;
+    return LBM_OK;
+  }
+  if (cudaMalloc((void**)tmp, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    *tmp = nullptr;
+    return LBM_ERR_OOM;
+  }
+  cudaError_t e = cudaMemcpyAsync(*tmp, p, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  *dev = *tmp;
+  return cuda_err(e);
+}
+
+}  // namespace
+
+namespace lbm {
+
+__global__ void __launch_bounds__(256) k_invariants_fold(const double* part, int nparts,
+                                                        double* out) {
+  __shared__ double sh[256][8];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int r = threadIdx.x; r < nparts; r += 256)
+    for (int k = 0; k < 8; ++k)
+      acc[k] = k == 5 ? fmax(acc[k], part[(int64_t)r * 8 + k]) : acc[k] + part[(int64_t)r * 8 + k];
+  for (int k = 0; k < 8; ++k) sh[threadIdx.x][k] = acc[k];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < 8; ++k)
+        sh[threadIdx.x][k] = k == 5 ? fmax(sh[threadIdx.x][k], sh[threadIdx.x + s][k])
+                                    : sh[threadIdx.x][k] + sh[threadIdx.x + s][k];
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) out[threadIdx.x] = sh[0][threadIdx.x];
+}
+
+void launch_invariants_fold(const double* part, int nparts, double* out, cudaStream_t s) {
+  k_invariants_fold<<<1, 256, 0, s>>>(part, nparts, out);
+}
+
+}  // namespace lbm
+
+extern "C" {
+
+const char* lbm_error_string(int code) {
+  switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_INVALID: return "invalid argument";
+    case LBM_ERR_UNSUPPORTED: return "unsupported";
+    case LBM_ERR_INADMISSIBLE: return "inadmissible method combination";
+    case LBM_ERR_OOM: return "device out of memory";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_DIVERGED: return "non-finite populations";
+    case LBM_ERR_STATE_MISMATCH: return "state does not match this context";
+    default: return "unknown error";
+  }
+}
+
+int lbm_create(lbm_ctx** out, const lbm_params* p) {
+  if (!out || !p) return LBM_ERR_INVALID;
+  *out = nullptr;
+  if (p->stencil < 0 || p->stencil > 2 || p->space < 0 || p->space > 3 || p->storage < 0 ||
+      p->storage > 3 || p->streaming < 0 || p->streaming > 1 ||
+      (p->equilibrium != LBM_EQ_DELTA && p->equilibrium != LBM_EQ_ABSOLUTE))
+    return LBM_ERR_INVALID;
+  if (p->space == LBM_SPACE_CUMULANT && p->equilibrium == LBM_EQ_DELTA)
+    return LBM_ERR_INADMISSIBLE;
+  if (p->boundary != LBM_PERIODIC) return LBM_ERR_UNSUPPORTED;
+  for (int k = 0; k < 3; ++k)
+    if (p->dims[k] < 1) return LBM_ERR_INVALID;
+  if (p->stencil == LBM_D2Q9 && p->dims[2] != 1) return LBM_ERR_INVALID;
+  if (p->dims[1] > 65535 || p->dims[2] > 65535) return LBM_ERR_INVALID;
+  if (p->dims[0] >= (int64_t(1) << 31) || p->dims[1] * p->dims[0] >= (int64_t(1) << 31))
+    return LBM_ERR_INVALID;
+  const int64_t N = p->dims[0] * p->dims[1] * p->dims[2];
+  if (N >= (int64_t(1) << 31)) return LBM_ERR_INVALID;
+  if (!valid_rates(p->rates)) return LBM_ERR_INVALID;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return LBM_ERR_CUDA;
+  }
+
+  lbm_ctx* c = new (std::nothrow) lbm_ctx;
+  if (!c) return LBM_ERR_OOM;
+  std::memset(c, 0, sizeof(*c));
+  c->p = *p;
+  c->q = q_of(p->stencil);
+  c->d = p->stencil == LBM_D2Q9 ? 2 : 3;
+  c->g.nx = int(p->dims[0]);
+  c->g.ny = int(p->dims[1]);
+  c->g.nz = int(p->dims[2]);
+  c->g.N = N;
+  c->eb = elem_bytes(p->storage);
+  c->stream = (cudaStream_t)p->stream;
+  set_effective_rates(c, p->rates);
+  const size_t bytes = size_t(c->q) * size_t(N) * size_t(c->eb);
+  const int nbuf = p->streaming == LBM_PULL ? 2 : 1;
+  for (int b = 0; b < nbuf; ++b) {
+    if (cudaMalloc(&c->buf[b], bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->buf[b] = nullptr;
+      lbm_destroy(c);
+      return LBM_ERR_OOM;
+    }
+    if (cudaMemsetAsync(c->buf[b], 0, bytes, c->stream) != cudaSuccess) {
+      lbm_destroy(c);
+      return LBM_ERR_CUDA;
+    }
+  }
+  const int64_t np = (N + 255) / 256;
+  c->nparts = int(np < 148 * 8 ? np : 148 * 8);
+  if (cudaMalloc((void**)&c->part, sizeof(double) * (size_t(c->nparts) * 8 + 8)) != cudaSuccess) {
+    cudaGetLastError();
+    c->part = nullptr;
+    lbm_destroy(c);
+    return LBM_ERR_OOM;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  for (int b = 0; b < 2; ++b)
+    if (c->buf[b]) cudaFree(c->buf[b]);
+  if (c->part) cudaFree(c->part);
+  delete c;
+}
+
+int lbm_set_stream(lbm_ctx* c, void* stream) {
+  if (!c) return LBM_ERR_INVALID;
+  c->stream = (cudaStream_t)stream;
+  c->p.stream = stream;
+  return LBM_OK;
+}
+
+int lbm_set_rates(lbm_ctx* c, const double rates[6]) {
+  if (!c || !rates || !valid_rates(rates)) return LBM_ERR_INVALID;
+  for (int k = 0; k < 6; ++k) c->p.rates[k] = rates[k];
+  set_effective_rates(c, rates);
+  return LBM_OK;
+}
+
+int lbm_get_time(const lbm_ctx* c, int64_t* step, int* parity) {
+  if (!c) return LBM_ERR_INVALID;
+  if (step) *step = c->t;
+  if (parity) *parity = c->parity;
+  return LBM_OK;
+}
+
+static int scatter(lbm_ctx* c, const double* df, const double* rho, const double* u) {
+  if (c->p.streaming == LBM_AA) c->parity = 0;
+  AuxArgs a = aux_base(c, lbm::AUX_SCATTER);
+  a.gather_mode = c->p.streaming == LBM_PULL ? G_PULL : G_LOCAL;
+  a.df_in = df;
+  a.rho_in = rho;
+  a.u_in = u;
+  kAux[c->p.stencil][c->p.storage](a);
+  return cuda_err(cudaGetLastError());
+}
+
+int lbm_init_velocity(lbm_ctx* c, const double* rho, const double* u, int on_device) {
+  if (!c || !u) return LBM_ERR_INVALID;
+  const size_t N = size_t(c->g.N);
+  const double *drho = nullptr, *du = nullptr;
+  double *trho = nullptr, *tu = nullptr;
+  int rc = stage_in(c, rho, N, on_device, &drho, &trho);
+  if (rc == LBM_OK) rc = stage_in(c, u, N * c->d, on_device, &du, &tu);
+  if (rc == LBM_OK) {
+    c->t = 0;
+    rc = scatter(c, nullptr, drho, du);
+  }
+  if (trho || tu) {
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+    if (trho) cudaFree(trho);
+    if (tu) cudaFree(tu);
+  }
+  return rc;
+}
+
+int lbm_set_populations(lbm_ctx* c, const double* df, int on_device) {
+  if (!c || !df) return LBM_ERR_INVALID;
+  const double* ddf = nullptr;
+  double* tmp = nullptr;
+  int rc = stage_in(c, df, size_t(c->g.N) * c->q, on_device, &ddf, &tmp);
+  if (rc == LBM_OK) rc = scatter(c, ddf, nullptr, nullptr);
+  if (tmp) {
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+    cudaFree(tmp);
+  }
+  return rc;
+}
+
+int lbm_step(lbm_ctx* c, int64_t n) {
+  if (!c || n < 0) return LBM_ERR_INVALID;
+  StepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = c->g;
+  for (int k = 0; k < 6; ++k) a.rates[k] = c->rates[k];
+  a.space = c->space;
+  a.reg = c->reg;
+  a.storage = c->p.storage;
+  a.stream = c->stream;
+  const step_fn fn = kStep[c->p.stencil][c->p.storage];
+  for (int64_t s = 0; s < n; ++s) {
+    if (c->p.streaming == LBM_PULL) {
+      a.mode = lbm::MODE_PULL;
+      a.src = c->buf[c->cur];
+      a.dst = c->buf[1 - c->cur];
+      fn(a);
+      c->cur = 1 - c->cur;
+    } else {
+      a.mode = c->parity ? lbm::MODE_AA_ODD : lbm::MODE_AA_EVEN;
+      a.src = c->buf[0];
+      a.dst = c->buf[0];
+      fn(a);
+      c->parity ^= 1;
+    }
+    c->t++;
+  }
+  return cuda_err(cudaGetLastError());
+}
+
+static int gather(lbm_ctx* c, double* df, double* rho, double* u, int on_device) {
+  const size_t N = size_t(c->g.N);
+  double *tdf = nullptr, *trho = nullptr, *tu = nullptr;
+  int rc = LBM_OK;
+  if (!on_device) {
+    if (df && cudaMalloc((void**)&tdf, N * c->q * sizeof(double)) != cudaSuccess) rc = LBM_ERR_OOM;
+    if (rho && cudaMalloc((void**)&trho, N * sizeof(double)) != cudaSuccess) rc = LBM_ERR_OOM;
+    if (u && cudaMalloc((void**)&tu, N * c->d * sizeof(double)) != cudaSuccess) rc = LBM_ERR_OOM;
+    if (rc != LBM_OK) cudaGetLastError();
+  }
+  if (rc == LBM_OK) {
+    AuxArgs a = aux_base(c, lbm::AUX_GATHER);
+    a.df = on_device ? df : tdf;
+    a.rho = on_device ? rho : trho;
+    a.u = on_device ? u : tu;
+    kAux[c->p.stencil][c->p.storage](a);
+    rc = cuda_err(cudaGetLastError());
+  }
+  if (rc == LBM_OK && !on_device) {
+    if (df)
+      rc = cuda_err(cudaMemcpyAsync(df, tdf, N * c->q * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream));
+    if (rho && rc == LBM_OK)
+      rc = cuda_err(
+          cudaMemcpyAsync(rho, trho, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (u && rc == LBM_OK)
+      rc = cuda_err(
+          cudaMemcpyAsync(u, tu, N * c->d * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+  }
+  if (tdf) cudaFree(tdf);
+  if (trho) cudaFree(trho);
+  if (tu) cudaFree(tu);
+  return rc;
+}
+
+int lbm_macroscopic(lbm_ctx* c, double* rho, double* u, int on_device) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!rho && !u) return LBM_OK;
+  return gather(c, nullptr, rho, u, on_device);
+}
+
+int lbm_get_populations(lbm_ctx* c, double* df, int on_device) {
+  if (!c || !df) return LBM_ERR_INVALID;
+  return gather(c, df, nullptr, nullptr, on_device);
+}
+
+int lbm_invariants(lbm_ctx* c, double out[8]) {
+  if (!c || !out) return LBM_ERR_INVALID;
+  AuxArgs a = aux_base(c, lbm::AUX_INVARIANTS);
+  a.part = c->part;
+  a.nparts = c->nparts;
+  kAux[c->p.stencil][c->p.storage](a);
+  lbm::launch_invariants_fold(c->part, c->nparts, c->part + size_t(c->nparts) * 8, c->stream);
+  int rc = cuda_err(cudaGetLastError());
+  if (rc == LBM_OK)
+    rc = cuda_err(cudaMemcpyAsync(out, c->part + size_t(c->nparts) * 8, 8 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->stream));
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+  if (rc == LBM_OK && out[6] > 0) rc = LBM_ERR_DIVERGED;
+  return rc;
+}
+
+int64_t lbm_state_bytes(const lbm_ctx* c) {
+  if (!c) return LBM_ERR_INVALID;
+  return int64_t(sizeof(StateHeader)) + int64_t(c->q) * c->g.N * c->eb;
+}
+
+int lbm_get_state(lbm_ctx* c, void* buf, size_t bytes) {
+  if (!c || !buf || int64_t(bytes) < lbm_state_bytes(c)) return LBM_ERR_INVALID;
+  StateHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = kStateMagic;
+  h.stencil = c->p.stencil;
+  h.space = c->p.space;
+  h.equilibrium = c->p.equilibrium;
+  h.storage = c->p.storage;
+  h.streaming = c->p.streaming;
+  h.parity = c->parity;
+  for (int k = 0; k < 3; ++k) h.dims[k] = c->p.dims[k];
+  h.t = c->t;
+  h.payload = int64_t(c->q) * c->g.N * c->eb;
+  std::memcpy(buf, &h, sizeof(h));
+  int rc = cuda_err(cudaMemcpyAsync((char*)buf + sizeof(h), state_buf(c), size_t(h.payload),
+                                    cudaMemcpyDeviceToHost, c->stream));
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+  return rc;
+}
+
+int lbm_set_state(lbm_ctx* c, const void* buf, size_t bytes) {
+  if (!c || !buf || bytes < sizeof(StateHeader)) return LBM_ERR_INVALID;
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (h.magic != kStateMagic || h.stencil != c->p.stencil || h.storage != c->p.storage ||
+      h.streaming != c->p.streaming || h.dims[0] != c->p.dims[0] || h.dims[1] != c->p.dims[1] ||
+      h.dims[2] != c->p.dims[2] || h.payload != int64_t(c->q) * c->g.N * c->eb ||
+      int64_t(bytes) < lbm_state_bytes(c) || (h.parity != 0 && h.parity != 1))
+    return LBM_ERR_STATE_MISMATCH;
+  c->parity = h.parity;
+  c->t = h.t;
+  int rc = cuda_err(cudaMemcpyAsync(state_buf(c), (const char*)buf + sizeof(h), size_t(h.payload),
+                                    cudaMemcpyHostToDevice, c->stream));
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+  return rc;
+}
+
+}  // extern "C"

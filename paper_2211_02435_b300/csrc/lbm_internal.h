@@ -1,0 +1,61 @@
+// lbm_internal.h -- host-side launch interface between the C ABI
+// (lbm_api.cu) and the per-(stencil, storage) kernel instantiations
+// (lbm_inst.cu, compiled once per combination).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+struct Geo {
+  int nx, ny, nz;
+  int64_t N;  // nx * ny * nz (< 2^31)
+};
+
+enum { STORE_F64 = 0, STORE_F32 = 1, STORE_F16 = 2, STORE_BF16 = 3 };
+enum { MODE_PULL = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2 };
+enum { AUX_GATHER = 0, AUX_SCATTER = 1, AUX_INVARIANTS = 2 };
+
+struct StepArgs {
+  const void* src;  // pull source buffer
+  void* dst;        // pull destination / AA in-place buffer
+  Geo g;
+  double rates[6];
+  int space;  // SP_RAW / SP_CENTRAL / SP_CUMULANT
+  int reg;    // bulk and orders >= 3 relaxed with rate 1 (compile-time)
+  int storage;
+  int mode;
+  cudaStream_t stream;
+};
+
+struct AuxArgs {
+  int op;
+  void* buf;
+  Geo g;
+  int storage;
+  int space;
+  int gather_mode;  // G_PULL / G_LOCAL / G_AAODD (scatter: G_PULL or G_LOCAL)
+  double* df;       // gather outputs (nullable)
+  double* rho;
+  double* u;
+  const double* df_in;  // scatter inputs (df_in, or rho_in / u_in)
+  const double* rho_in;
+  const double* u_in;
+  double* part;  // invariants partials [nparts][8]
+  int nparts;
+  cudaStream_t stream;
+};
+
+// one pair of entry points per (stencil, storage) object file
+#define LBM_DECL(ST, SO)                           \
+  void launch_step_##ST##_##SO(const StepArgs& a); \
+  void launch_aux_##ST##_##SO(const AuxArgs& a);
+LBM_DECL(0, 0) LBM_DECL(0, 1) LBM_DECL(0, 2) LBM_DECL(0, 3)
+LBM_DECL(1, 0) LBM_DECL(1, 1) LBM_DECL(1, 2) LBM_DECL(1, 3)
+LBM_DECL(2, 0) LBM_DECL(2, 1) LBM_DECL(2, 2) LBM_DECL(2, 3)
+#undef LBM_DECL
+
+void launch_invariants_fold(const double* part, int nparts, double* out, cudaStream_t s);
+
+}  // namespace lbm

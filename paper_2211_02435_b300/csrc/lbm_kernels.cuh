@@ -1,0 +1,293 @@
+// lbm_kernels.cuh -- CUDA kernels of the fused stream + collide step and
+// its read-out / set-up kernels, templated over stencil, storage type,
+// collision space and streaming pattern.  Included by lbm_inst.cu, which
+// instantiates the launchers declared in lbm_internal.h.
+//
+// Data layout in HBM: one structure-of-arrays buffer per population set,
+// buf[i * N + c] with c = (z * Ny + y) * Nx + x (x fastest), so a warp of
+// 32 consecutive x reads 32 consecutive elements of each population plane.
+// One thread updates one cell; a block covers LBM_BX consecutive x of one
+// (y, z) row; the grid is (ceil(Nx / LBM_BX), Ny, Nz).
+#pragma once
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+#ifndef LBM_BX
+#define LBM_BX 128
+#endif
+
+// how a kernel reads the canonical populations f(n) of a cell
+enum { G_PULL = 0, G_LOCAL = 1, G_AAODD = 2 };
+
+struct Nbr {
+  int x[3], y[3], z[3];  // coordinate of offset -1, 0, +1 (periodic)
+};
+
+LBM_D Nbr neighbours(int x, int y, int z, const Geo& g) {
+  Nbr n;
+  n.x[0] = x == 0 ? g.nx - 1 : x - 1;
+  n.x[1] = x;
+  n.x[2] = x + 1 == g.nx ? 0 : x + 1;
+  n.y[0] = y == 0 ? g.ny - 1 : y - 1;
+  n.y[1] = y;
+  n.y[2] = y + 1 == g.ny ? 0 : y + 1;
+  n.z[0] = z == 0 ? g.nz - 1 : z - 1;
+  n.z[1] = z;
+  n.z[2] = z + 1 == g.nz ? 0 : z + 1;
+  return n;
+}
+
+// cell index of the neighbour at offset (ox, oy, oz) in {-1, 0, 1}
+LBM_D int cell_at(const Nbr& n, const Geo& g, int ox, int oy, int oz) {
+  return (n.z[oz + 1] * g.ny + n.y[oy + 1]) * g.nx + n.x[ox + 1];
+}
+
+// Gather the canonical pre-collision populations f(n) of one cell.
+//   G_PULL : f_i(x) = buf[i][x - xi_i]       (pull buffer after a step)
+//   G_LOCAL: f_i(x) = buf[i][x]              (AA, even parity)
+//   G_AAODD: f_i(x) = buf[ibar][x - xi_i]    (AA, odd parity)
+template <int ST, class S, class T, int MODE>
+LBM_D void load_pops(const S* buf, const Geo& g, const Nbr& n, int c, T (&f)[q_of(ST)]) {
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1), cz = vel(ST, i, 2);
+    int src_c = c;
+    int slot = i;
+    if constexpr (MODE != G_LOCAL) src_c = cell_at(n, g, -cx, -cy, -cz);
+    if constexpr (MODE == G_AAODD) slot = opp(i);
+    const S v = buf[(int64_t)slot * g.N + src_c];
+    f[i] = Codec<S>::template dec<T>(v, scale_exp(ST, i));
+  });
+}
+
+// ------------------------------------------------------------ step kernels
+// pull: read f_i from x - xi_i of src, collide, write f*_i at x of dst
+template <int ST, class S, class T, int SPACE, bool REG>
+__global__ void __launch_bounds__(LBM_BX) k_pull(const S* __restrict__ src, S* __restrict__ dst,
+                                                 Geo g, Rates<T> keep) {
+  const int x = blockIdx.x * LBM_BX + threadIdx.x;
+  if (x >= g.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const Nbr n = neighbours(x, y, z, g);
+  const int c = (z * g.ny + y) * g.nx + x;
+  T f[q_of(ST)];
+  load_pops<ST, S, T, G_PULL>(src, g, n, c, f);
+  collide<ST, T, SPACE, REG>(f, keep);
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    dst[(int64_t)i * g.N + c] = Codec<S>::template enc<T>(f[i], scale_exp(ST, i));
+  });
+}
+
+// AA pattern, in place on one buffer (Sec. 4.3).  Even kernels read slot i
+// of the own cell and write f*_i into slot ibar of the own cell; odd
+// kernels read slot ibar at x - xi_i and write f*_i into slot i at
+// x + xi_i.  Each cell reads and writes the same set of addresses, so no
+// two threads touch one element.
+template <int ST, class S, class T, int SPACE, bool REG, bool ODD>
+__global__ void __launch_bounds__(LBM_BX) k_aa(S* buf, Geo g, Rates<T> keep) {
+  const int x = blockIdx.x * LBM_BX + threadIdx.x;
+  if (x >= g.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const Nbr n = neighbours(x, y, z, g);
+  const int c = (z * g.ny + y) * g.nx + x;
+  T f[q_of(ST)];
+  load_pops<ST, S, T, ODD ? G_AAODD : G_LOCAL>(buf, g, n, c, f);
+  collide<ST, T, SPACE, REG>(f, keep);
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1), cz = vel(ST, i, 2);
+    int dc = c, slot = opp(i);
+    if constexpr (ODD) {
+      dc = cell_at(n, g, cx, cy, cz);
+      slot = i;
+    }
+    buf[(int64_t)slot * g.N + dc] = Codec<S>::template enc<T>(f[i], scale_exp(ST, i));
+  });
+}
+
+// ------------------------------------------------------ read-out kernels
+// canonical populations -> FP64 SoA df[i * N + c] and / or macroscopic
+template <int ST, class S, class T, int MODE>
+__global__ void __launch_bounds__(LBM_BX) k_gather(const S* buf, Geo g, double* df, double* rho,
+                                                   double* u) {
+  const int x = blockIdx.x * LBM_BX + threadIdx.x;
+  if (x >= g.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const Nbr n = neighbours(x, y, z, g);
+  const int c = (z * g.ny + y) * g.nx + x;
+  T f[q_of(ST)];
+  load_pops<ST, S, T, MODE>(buf, g, n, c, f);
+  if (df) {
+    sfor<q_of(ST)>([&](auto I) { df[(int64_t)CI(I) * g.N + c] = double(f[CI(I)]); });
+  }
+  if (rho || u) {
+    double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
+    sfor<q_of(ST)>([&](auto I) {
+      constexpr int i = CI(I);
+      const double v = double(f[i]);
+      dr += v;
+      if constexpr (vel(ST, i, 0) != 0) j[0] += vel(ST, i, 0) * v;
+      if constexpr (vel(ST, i, 1) != 0) j[1] += vel(ST, i, 1) * v;
+      if constexpr (vel(ST, i, 2) != 0) j[2] += vel(ST, i, 2) * v;
+    });
+    const double r = 1.0 + dr;
+    if (rho) rho[c] = r;
+    if (u) {
+      for (int d = 0; d < dim_of(ST); ++d) u[(int64_t)d * g.N + c] = j[d] / r;
+    }
+  }
+}
+
+// write canonical populations (FP64 SoA df, or the method's equilibrium of
+// rho / u when df is NULL) into the storage so that the next gather returns
+// them: pull -> buf[i][x + xi_i] (un-streamed), AA -> buf[i][x] (even).
+template <int ST, class S, class T, int SPACE, bool PULL>
+__global__ void __launch_bounds__(LBM_BX) k_scatter(S* buf, Geo g, const double* df,
+                                                    const double* rho, const double* u) {
+  const int x = blockIdx.x * LBM_BX + threadIdx.x;
+  if (x >= g.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const Nbr n = neighbours(x, y, z, g);
+  const int c = (z * g.ny + y) * g.nx + x;
+  T f[q_of(ST)];
+  if (df) {
+    sfor<q_of(ST)>([&](auto I) { f[CI(I)] = T(df[(int64_t)CI(I) * g.N + c]); });
+  } else {
+    const T dr = rho ? T(rho[c] - 1.0) : T(0);
+    T uu[3] = {T(0), T(0), T(0)};
+    for (int d = 0; d < dim_of(ST); ++d) uu[d] = T(u[(int64_t)d * g.N + c]);
+    equilibrium<ST, T, SPACE>(dr, uu, f);
+  }
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    int dc = c;
+    if constexpr (PULL) dc = cell_at(n, g, vel(ST, i, 0), vel(ST, i, 1), vel(ST, i, 2));
+    buf[(int64_t)i * g.N + dc] = Codec<S>::template enc<T>(f[i], scale_exp(ST, i));
+  });
+}
+
+// FP64 invariant partial sums, one row of 8 per block (fixed cell order):
+// sum(rho-1), sum(rho u_x), sum(rho u_y), sum(rho u_z), sum(rho|u|^2/2),
+// max|u|, #non-finite cells, #cells.
+constexpr int INV_THREADS = 256;
+template <int ST, class S, class T, int MODE>
+__global__ void __launch_bounds__(INV_THREADS) k_invariants(const S* buf, Geo g, double* part) {
+  __shared__ double sh[INV_THREADS][8];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const int64_t stride = (int64_t)gridDim.x * INV_THREADS;
+  for (int64_t c = (int64_t)blockIdx.x * INV_THREADS + threadIdx.x; c < g.N; c += stride) {
+    const int x = int(c % g.nx), y = int((c / g.nx) % g.ny), z = int(c / ((int64_t)g.nx * g.ny));
+    const Nbr n = neighbours(x, y, z, g);
+    T f[q_of(ST)];
+    load_pops<ST, S, T, MODE>(buf, g, n, int(c), f);
+    double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
+    bool finite = true;
+    sfor<q_of(ST)>([&](auto I) {
+      constexpr int i = CI(I);
+      const double v = double(f[i]);
+      finite = finite && isfinite(v);
+      dr += v;
+      if constexpr (vel(ST, i, 0) != 0) j[0] += vel(ST, i, 0) * v;
+      if constexpr (vel(ST, i, 1) != 0) j[1] += vel(ST, i, 1) * v;
+      if constexpr (vel(ST, i, 2) != 0) j[2] += vel(ST, i, 2) * v;
+    });
+    if (!finite) {
+      acc[6] += 1.0;
+    } else {
+      const double r = 1.0 + dr;
+      const double u0 = j[0] / r, u1 = j[1] / r, u2 = j[2] / r;
+      const double uu = u0 * u0 + u1 * u1 + u2 * u2;
+      acc[0] += dr;
+      acc[1] += j[0];
+      acc[2] += j[1];
+      acc[3] += j[2];
+      acc[4] += 0.5 * r * uu;
+      acc[5] = fmax(acc[5], sqrt(uu));
+    }
+    acc[7] += 1.0;
+  }
+  for (int k = 0; k < 8; ++k) sh[threadIdx.x][k] = acc[k];
+  __syncthreads();
+  for (int s = INV_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < 8; ++k)
+        sh[threadIdx.x][k] = k == 5 ? fmax(sh[threadIdx.x][k], sh[threadIdx.x + s][k])
+                                    : sh[threadIdx.x][k] + sh[threadIdx.x + s][k];
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) part[(int64_t)blockIdx.x * 8 + threadIdx.x] = sh[0][threadIdx.x];
+}
+
+// --------------------------------------------------------------- launchers
+inline dim3 step_grid(const Geo& g) { return dim3((g.nx + LBM_BX - 1) / LBM_BX, g.ny, g.nz); }
+
+template <int ST, class S, class T, int SPACE, bool REG>
+void launch_step_typed(const StepArgs& a) {
+  Rates<T> keep;
+  for (int k = 0; k < 6; ++k) keep.om[k] = T(1.0 - a.rates[k]);
+  const dim3 grid = step_grid(a.g);
+  if (a.mode == MODE_PULL)
+    k_pull<ST, S, T, SPACE, REG><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.src, (S*)a.dst, a.g,
+                                                                   keep);
+  else if (a.mode == MODE_AA_EVEN)
+    k_aa<ST, S, T, SPACE, REG, false><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep);
+  else
+    k_aa<ST, S, T, SPACE, REG, true><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep);
+}
+
+template <int ST, class S, class T>
+void launch_step_space(const StepArgs& a) {
+  switch (a.space * 2 + (a.reg ? 1 : 0)) {
+    case SP_RAW * 2: launch_step_typed<ST, S, T, SP_RAW, false>(a); break;
+    case SP_RAW * 2 + 1: launch_step_typed<ST, S, T, SP_RAW, true>(a); break;
+    case SP_CENTRAL * 2: launch_step_typed<ST, S, T, SP_CENTRAL, false>(a); break;
+    case SP_CENTRAL * 2 + 1: launch_step_typed<ST, S, T, SP_CENTRAL, true>(a); break;
+    case SP_CUMULANT * 2: launch_step_typed<ST, S, T, SP_CUMULANT, false>(a); break;
+    default: launch_step_typed<ST, S, T, SP_CUMULANT, true>(a); break;
+  }
+}
+
+template <int ST, class S, class T>
+void launch_aux_typed(const AuxArgs& a) {
+  const dim3 grid = step_grid(a.g);
+  const int gm = a.gather_mode;
+  switch (a.op) {
+    case AUX_GATHER:
+      if (gm == G_PULL)
+        k_gather<ST, S, T, G_PULL><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u);
+      else if (gm == G_LOCAL)
+        k_gather<ST, S, T, G_LOCAL><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u);
+      else
+        k_gather<ST, S, T, G_AAODD><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u);
+      break;
+    case AUX_SCATTER: {
+      const bool pull = gm == G_PULL;
+      if (a.space == SP_RAW) {
+        if (pull)
+          k_scatter<ST, S, T, SP_RAW, true><<<grid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in);
+        else
+          k_scatter<ST, S, T, SP_RAW, false><<<grid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in);
+      } else {
+        if (pull)
+          k_scatter<ST, S, T, SP_CENTRAL, true><<<grid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in);
+        else
+          k_scatter<ST, S, T, SP_CENTRAL, false><<<grid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in);
+      }
+      break;
+    }
+    case AUX_INVARIANTS:
+      if (gm == G_PULL)
+        k_invariants<ST, S, T, G_PULL><<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
+      else if (gm == G_LOCAL)
+        k_invariants<ST, S, T, G_LOCAL><<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
+      else
+        k_invariants<ST, S, T, G_AAODD><<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
+      break;
+  }
+}
+
+}  // namespace lbm

@@ -1,0 +1,230 @@
+"""Thin ctypes binding of liblbm.so (include/lbm.h).
+
+Argument marshalling only: every step of the lattice Boltzmann update runs in
+the library's CUDA kernels.  numpy arrays are passed as host pointers
+(on_device = 0), CUDA torch tensors as device pointers (on_device = 1).  If
+the shared library is missing or a call fails, an exception is raised; there
+is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+D2Q9, D3Q19, D3Q27 = 0, 1, 2
+SPACE_POPULATIONS, SPACE_RAW, SPACE_CENTRAL, SPACE_CUMULANT = 0, 1, 2, 3
+EQ_DELTA, EQ_ABSOLUTE = 0, 1
+STORE_F64, STORE_F32, STORE_F16_DELTA, STORE_BF16_DELTA = 0, 1, 2, 3
+PULL, AA = 0, 1
+PERIODIC = 0
+Q_OF = {D2Q9: 9, D3Q19: 19, D3Q27: 27}
+ELEM_BYTES = {STORE_F64: 8, STORE_F32: 4, STORE_F16_DELTA: 2, STORE_BF16_DELTA: 2}
+
+ERRORS = {0: "ok", -1: "invalid argument", -2: "unsupported", -3: "inadmissible",
+          -4: "device out of memory", -5: "CUDA error", -6: "non-finite populations",
+          -7: "state mismatch"}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, 'error')} ({code})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("stencil", ctypes.c_int), ("space", ctypes.c_int),
+                ("equilibrium", ctypes.c_int), ("storage", ctypes.c_int),
+                ("streaming", ctypes.c_int), ("rates", ctypes.c_double * 6),
+                ("dims", ctypes.c_int64 * 3), ("boundary", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load liblbm.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2211_02435_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        d = ctypes.POINTER(ctypes.c_double)
+        L.lbm_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Params)]
+        L.lbm_init_velocity.argtypes = [vp, vp, vp, c_int]
+        L.lbm_step.argtypes = [vp, i64]
+        L.lbm_macroscopic.argtypes = [vp, vp, vp, c_int]
+        L.lbm_get_populations.argtypes = [vp, vp, c_int]
+        L.lbm_set_populations.argtypes = [vp, vp, c_int]
+        L.lbm_invariants.argtypes = [vp, d]
+        L.lbm_state_bytes.argtypes = [vp]
+        L.lbm_state_bytes.restype = i64
+        L.lbm_get_state.argtypes = [vp, vp, ctypes.c_size_t]
+        L.lbm_set_state.argtypes = [vp, vp, ctypes.c_size_t]
+        L.lbm_get_time.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(c_int)]
+        L.lbm_set_rates.argtypes = [vp, d]
+        L.lbm_set_stream.argtypes = [vp, vp]
+        L.lbm_destroy.argtypes = [vp]
+        L.lbm_destroy.restype = None
+        L.lbm_error_string.argtypes = [c_int]
+        L.lbm_error_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise LBMError(rc, where)
+
+
+def _ptr(a, n_expected, writable=False):
+    """(pointer, on_device) for a numpy array or a CUDA torch tensor."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("expected a C-contiguous float64 array")
+        if a.size != n_expected:
+            raise ValueError(f"expected {n_expected} elements, got {a.size}")
+        if writable and not a.flags.writeable:
+            raise ValueError("array is read-only")
+        return a.ctypes.data, 0
+    if getattr(a, "is_cuda", False):  # torch tensor, duck-typed
+        if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+            raise TypeError("expected a contiguous float64 CUDA tensor")
+        if a.numel() != n_expected:
+            raise ValueError(f"expected {n_expected} elements, got {a.numel()}")
+        return a.data_ptr(), 1
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def stream_handle(stream):
+    """cudaStream_t value of a torch stream, an int handle, or None."""
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Lattice:
+    """One periodic domain advanced by the fused stream + collide step."""
+
+    def __init__(self, stencil, space, equilibrium, storage, streaming, rates, dims,
+                 stream=None):
+        self.stencil, self.space, self.storage, self.streaming = stencil, space, storage, streaming
+        self.equilibrium = equilibrium
+        self.q = Q_OF[stencil]
+        self.d = 2 if stencil == D2Q9 else 3
+        dims = list(dims) + [1] * (3 - len(dims))
+        self.dims = tuple(int(x) for x in dims)
+        self.N = self.dims[0] * self.dims[1] * self.dims[2]
+        r = list(rates) + [1.0] * (6 - len(rates))
+        p = Params(stencil, space, equilibrium, storage, streaming, (ctypes.c_double * 6)(*r),
+                   (ctypes.c_int64 * 3)(*self.dims), PERIODIC, stream_handle(stream))
+        h = ctypes.c_void_p()
+        _check(lib().lbm_create(ctypes.byref(h), ctypes.byref(p)), "lbm_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def init_velocity(self, rho, u):
+        pr, dr = _ptr(rho, self.N)
+        pu, du = _ptr(u, self.d * self.N)
+        if rho is not None and dr != du:
+            raise TypeError("rho and u must both be host or both be device buffers")
+        _check(lib().lbm_init_velocity(self._h, pr, pu, du), "lbm_init_velocity")
+
+    def step(self, n=1):
+        _check(lib().lbm_step(self._h, int(n)), "lbm_step")
+
+    def macroscopic(self, rho=None, u=None):
+        """Fill rho[N] / u[d*N] (numpy or CUDA tensors).  With both None,
+        allocates numpy arrays and returns them shaped as fields."""
+        alloc = rho is None and u is None
+        if alloc:
+            rho = np.empty(self.N)
+            u = np.empty(self.d * self.N)
+        pr, dr = _ptr(rho, self.N, True)
+        pu, du = _ptr(u, self.d * self.N, True)
+        on_dev = dr if rho is not None else du
+        _check(lib().lbm_macroscopic(self._h, pr, pu, on_dev), "lbm_macroscopic")
+        if alloc:
+            nx, ny, nz = self.dims
+            return rho.reshape(nz, ny, nx), u.reshape(self.d, nz, ny, nx)
+        return rho, u
+
+    def get_populations(self, out=None):
+        alloc = out is None
+        if alloc:
+            out = np.empty(self.q * self.N)
+        p, dev = _ptr(out, self.q * self.N, True)
+        _check(lib().lbm_get_populations(self._h, p, dev), "lbm_get_populations")
+        if alloc:
+            nx, ny, nz = self.dims
+            return out.reshape(self.q, nz, ny, nx)
+        return out
+
+    def set_populations(self, df):
+        if isinstance(df, np.ndarray):
+            df = np.ascontiguousarray(df, dtype=np.float64).reshape(-1)
+        p, dev = _ptr(df, self.q * self.N)
+        _check(lib().lbm_set_populations(self._h, p, dev), "lbm_set_populations")
+
+    def invariants(self, check=True):
+        out = (ctypes.c_double * 8)()
+        rc = lib().lbm_invariants(self._h, out)
+        if rc != -6 or check:
+            _check(rc, "lbm_invariants")
+        keys = ("mass_dev", "jx", "jy", "jz", "energy", "max_u", "nonfinite", "cells")
+        return dict(zip(keys, list(out)))
+
+    def state_bytes(self):
+        return int(lib().lbm_state_bytes(self._h))
+
+    def get_state(self):
+        buf = np.empty(self.state_bytes(), dtype=np.uint8)
+        _check(lib().lbm_get_state(self._h, buf.ctypes.data, buf.size), "lbm_get_state")
+        return buf
+
+    def set_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(lib().lbm_set_state(self._h, buf.ctypes.data, buf.size), "lbm_set_state")
+
+    def time(self):
+        t, par = ctypes.c_int64(), ctypes.c_int()
+        _check(lib().lbm_get_time(self._h, ctypes.byref(t), ctypes.byref(par)), "lbm_get_time")
+        return t.value, par.value
+
+    def set_rates(self, rates):
+        r = list(rates) + [1.0] * (6 - len(rates))
+        _check(lib().lbm_set_rates(self._h, (ctypes.c_double * 6)(*r)), "lbm_set_rates")
+
+    def set_stream(self, stream):
+        _check(lib().lbm_set_stream(self._h, stream_handle(stream)), "lbm_set_stream")
