@@ -1,0 +1,338 @@
+"""Benchmark of the fused stream + collide step (MLUPS and HBM roofline).
+
+Workload (default): D3Q27 cumulant LBM, regularised (shear rate from
+nu = 1e-3, bulk and higher-order rates 1), periodic 512^3 Taylor-Green vortex
+u0 = 0.05 plus seeded uniform +-1e-3 velocity noise, populations stored as
+FP32 deviations, pull streaming.  The same step is also timed with FP16- and
+BF16-delta storage and reported under "forms" with its velocity error
+against an FP64 run of the same steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+
+Under torchrun (N > 1) every rank advances its own independent replica
+(the method does not shard here: replicas only); the reported value is the
+sum of all ranks' cell updates over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2211_02435_b300 import inputs as I  # noqa: E402
+
+METRIC = "MLUPS and % of HBM roofline, D3Q27 cumulant 512^3, FP32 vs FP16-delta storage"
+UNIT = "MLUPS"
+BYTES_PER_CELL = {"f64": 432, "f32": 216, "f16_delta": 108, "bf16_delta": 108}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_fields(n):
+    rho, u = I.taylor_green((n, n, n), 0.05)
+    u = I.add_uniform_noise(u, 1e-3, seed=1)
+    return rho, u
+
+
+def oracle_sample(n_cells_edge, steps, nthreads=0):
+    """Time the FP64 CPU oracle on a small cube of the same method and flow."""
+    import oracle as O
+    O.build()
+    nu = 1e-3
+    rates = [I.shear_viscosity_rate(nu)] + [1.0] * 5
+    m = O.method(O.D3Q27, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, rates)
+    dims = (n_cells_edge,) * 3
+    rho, u = make_fields(n_cells_edge)
+    df = O.init(m, dims, rho, u)
+    t0 = time.perf_counter()
+    O.step(m, dims, df, steps, nthreads)
+    dt = time.perf_counter() - t0
+    return n_cells_edge ** 3 * steps / dt / 1e6, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    edge = args.ref_edge
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        oracle_sample(edge, 1)
+    t_total, cells = 0.0, 0
+    for _ in range(args.steps):
+        _, dt = oracle_sample(edge, 1)
+        t_total += dt
+        cells += edge ** 3
+    v = cells / t_total / 1e6
+    sample = (f"{edge}^3 cells of the same D3Q27 cumulant TGV flow, one oracle step per "
+              f"timed step (bounded sample of the 512^3 workload)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"D3Q27 cumulant R- nu=1e-3, TGV u0=0.05 + 1e-3 noise, "
+                                   f"{edge}^3 sample", "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_cuda(args):
+    import torch
+    from paper_2211_02435_b300 import build as B
+    from paper_2211_02435_b300 import lbm as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        args.gpus = world
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+
+    n = args.size
+    N = n ** 3
+    rates = [I.shear_viscosity_rate(1e-3)] + [1.0] * 5
+    stream = torch.cuda.current_stream()
+    rho_h, u_h = make_fields(n)
+    rho_d = torch.from_numpy(rho_h.reshape(-1)).cuda()
+    u_d = torch.from_numpy(u_h.reshape(-1)).cuda()
+    peak, peak_kind = measured_peaks()
+
+    def time_form(storage, steps, warmup):
+        lat = L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, storage, L.PULL, rates,
+                        (n, n, n), stream=stream)
+        lat.init_velocity(rho_d, u_d)
+        lat.step(warmup)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return lat, ms
+
+    # ---- headline: FP32 storage, kernel-only (inputs resident in HBM)
+    with ClockSampler(local) as clk:
+        lat32, ms32 = time_form(L.STORE_F32, args.steps, args.warmup)
+    clocks = clk.summary()
+    ms_max = ms32
+    if dist:
+        t = torch.tensor([ms32], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    per_step_s = ms_max / 1e3 / args.steps
+    value = world * N * args.steps / (ms_max / 1e3) / 1e6
+    achieved = BYTES_PER_CELL["f32"] * N / (ms32 / 1e3 / args.steps) / 1e9
+    u32 = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+    lat32.macroscopic(None, u32)
+    lat32.close()
+    del lat32
+
+    forms = {}
+    if not args.no_forms:
+        # FP64 reference of the same number of steps for the velocity errors
+        lat64 = L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F64, L.PULL, rates,
+                          (n, n, n), stream=stream)
+        lat64.init_velocity(rho_d, u_d)
+        lat64.step(args.warmup + args.steps)
+        u64 = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+        lat64.macroscopic(None, u64)
+        lat64.close()
+        del lat64
+        umax = float(u64.abs().max())
+
+        def uerr(uu):
+            return float((uu - u64).abs().max()) / umax
+
+        forms["f32"] = {"mlups": N * args.steps / (ms32 / 1e3) / 1e6,
+                        "roofline_frac": achieved / peak, "u_rel_linf_vs_f64": uerr(u32)}
+        for name, st in (("f16_delta", L.STORE_F16_DELTA), ("bf16_delta", L.STORE_BF16_DELTA)):
+            lat, ms = time_form(st, args.steps, args.warmup)
+            uu = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+            lat.macroscopic(None, uu)
+            lat.close()
+            del lat
+            ach = BYTES_PER_CELL[name] * N / (ms / 1e3 / args.steps) / 1e9
+            forms[name] = {"mlups": N * args.steps / (ms / 1e3) / 1e6,
+                           "achieved_gbs": ach, "roofline_frac": ach / peak,
+                           "u_rel_linf_vs_f64": uerr(uu),
+                           "vs_f32_mlups": (N * args.steps / (ms / 1e3)) / (N * args.steps / (ms32 / 1e3))}
+            del uu
+        del u64
+    del u32
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        rho_p = torch.from_numpy(rho_h.reshape(-1)).pin_memory()
+        u_p = torch.from_numpy(u_h.reshape(-1)).pin_memory()
+        rho_out = torch.empty(N, dtype=torch.float64).pin_memory()
+        u_out = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+        lat = L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F32, L.PULL, rates,
+                        (n, n, n), stream=stream)
+        lat.init_velocity(rho_p.numpy(), u_p.numpy())  # warm the path once
+        lat.step(args.warmup)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        lat.init_velocity(rho_p.numpy(), u_p.numpy())
+        lat.step(args.steps)
+        lat.macroscopic(rho_out.numpy(), u_out.numpy())
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        lat.close()
+        e2e = {"value": world * N * args.steps / dt / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": 4 * N * 8 / args.steps,
+               "d2h_bytes_per_step": 4 * N * 8 / args.steps,
+               "job": f"host rho,u (FP64, pinned) -> init -> {args.steps} steps -> host rho,u"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        edge = args.ref_edge
+        v, dt = oracle_sample(edge, args.cpu_steps)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{edge}^3 cells x {args.cpu_steps} steps of the same method and flow "
+                         f"({dt:.1f} s, OpenMP over all cores)"}
+
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tr = json.load(f).get("k_pull_d3q27_cumulant_reg_f32")
+        if tr and tr.get("cells"):
+            traffic = tr["bytes_per_cell"] * N
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "D3Q27 cumulant LBM (R-: shear from nu=1e-3, bulk and "
+                                   "orders 3-6 rate 1), periodic 512^3 Taylor-Green u0=0.05 "
+                                   "+ uniform 1e-3 noise, FP32 zero-centered storage, pull",
+                       "cells": N, "global_batch": world, "parallelism": "replicas",
+                       "l2": "working set 29 GB >> 126 MB L2, no flush needed"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind,
+                         "bytes_per_cell": BYTES_PER_CELL["f32"],
+                         "kernel": "k_pull<D3Q27, float, cumulant, regularised>"},
+            "forms": forms, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--ref-edge", type=int, default=48)
+    ap.add_argument("--cpu-steps", type=int, default=40)
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "cuda":
+        args.warmup = 3
+    return run_reference(args) if args.impl == "reference" else run_cuda(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -27,7 +27,8 @@
 #include <utility>
 
 #define LBM_HD __host__ __device__ __forceinline__
-#define LBM_D __device__ __forceinline__
+// per-cell math is host-callable too (used by host-side unit checks)
+#define LBM_D __host__ __device__ __forceinline__
 #define CI(K) (decltype(K)::value)
 
 namespace lbm {
@@ -238,10 +239,10 @@ LBM_D void binomial(T (&A)[3][3][3], const T (&u)[3], const T (&u2)[3]) {
 
 template <class T>
 LBM_D T rcp(T x) {
-  if constexpr (std::is_same<T, float>::value)
-    return __frcp_rn(x);
-  else
-    return T(1) / x;
+#ifdef __CUDA_ARCH__
+  if constexpr (std::is_same<T, float>::value) return __frcp_rn(x);
+#endif
+  return T(1) / x;
 }
 
 // ------------------------------------------------ relaxation, raw moments

@@ -1,0 +1,83 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every function include/*.h declares, and validates
+parameters before it touches a device."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2211_02435_b300 import build as B
+from paper_2211_02435_b300 import lbm as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.lib()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(lbm_\w+)\s*\(", src, re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "lbm_step" in names and "lbm_create" in names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def _params(**kw):
+    p = dict(stencil=L.D3Q27, space=L.SPACE_CUMULANT, equilibrium=L.EQ_ABSOLUTE,
+             storage=L.STORE_F32, streaming=L.PULL, rates=[1.9] + [1.0] * 5,
+             dims=(8, 8, 8), boundary=L.PERIODIC)
+    p.update(kw)
+    return L.Params(p["stencil"], p["space"], p["equilibrium"], p["storage"], p["streaming"],
+                    (ctypes.c_double * 6)(*p["rates"]), (ctypes.c_int64 * 3)(*p["dims"]),
+                    p["boundary"], None)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(stencil=3), -1),
+    (dict(space=7), -1),
+    (dict(storage=9), -1),
+    (dict(streaming=2), -1),
+    (dict(equilibrium=5), -1),
+    (dict(dims=(0, 4, 4)), -1),
+    (dict(dims=(4, 70000, 4)), -1),
+    (dict(dims=(2048, 2048, 1024)), -1),
+    (dict(stencil=L.D2Q9, dims=(8, 8, 2)), -1),
+    (dict(rates=[2.5] + [1.0] * 5), -1),
+    (dict(rates=[0.0] + [1.0] * 5), -1),
+    (dict(space=L.SPACE_CUMULANT, equilibrium=L.EQ_DELTA), -3),
+    (dict(boundary=1), -2),
+])
+def test_create_rejects_bad_parameters(lib, kw, code):
+    h = ctypes.c_void_p()
+    assert lib.lbm_create(ctypes.byref(h), ctypes.byref(_params(**kw))) == code
+    assert not h.value
+
+
+def test_null_arguments(lib):
+    assert lib.lbm_create(None, None) == -1
+    assert lib.lbm_step(None, 1) == -1
+    assert lib.lbm_macroscopic(None, None, None, 0) == -1
+    assert lib.lbm_invariants(None, None) == -1
+    lib.lbm_destroy(None)
+    for c in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert lib.lbm_error_string(c)
+
+
+def test_python_binding_raises_on_error(lib):
+    with pytest.raises(L.LBMError) as e:
+        L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_DELTA, L.STORE_F32, L.PULL, [1.9], (8, 8, 8))
+    assert e.value.code == -3
