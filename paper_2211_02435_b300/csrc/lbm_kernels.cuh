@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(LBM_BX) k_gather(const S* buf, Geo g, double* 
 
 // write canonical populations (FP64 SoA df, or the method's equilibrium of
 // rho / u when df is NULL) into the storage so that the next gather returns
-// them: pull -> buf[i][x + xi_i] (un-streamed), AA -> buf[i][x] (even).
+// them: pull -> buf[i][x - xi_i] (moved back upstream, where the pull
+// gather of cell x looks), AA -> buf[i][x] (even parity).
 template <int ST, class S, class T, int SPACE, bool PULL>
 __global__ void __launch_bounds__(LBM_BX) k_scatter(S* buf, Geo g, const double* df,
                                                     const double* rho, const double* u) {
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(LBM_BX) k_scatter(S* buf, Geo g, const double*
   sfor<q_of(ST)>([&](auto I) {
     constexpr int i = CI(I);
     int dc = c;
-    if constexpr (PULL) dc = cell_at(n, g, vel(ST, i, 0), vel(ST, i, 1), vel(ST, i, 2));
+    if constexpr (PULL) dc = cell_at(n, g, -vel(ST, i, 0), -vel(ST, i, 1), -vel(ST, i, 2));
     buf[(int64_t)i * g.N + dc] = Codec<S>::template enc<T>(f[i], scale_exp(ST, i));
   });
 }
