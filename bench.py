@@ -99,6 +99,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_traffic_per_cell():
+    """DRAM bytes per cell update of the FP32 step kernel from the committed
+    ncu summary, or None when the kernel sources changed since the capture."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "ncu_k_pull_d3q27_cumulant_f32_256.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m1 = re.search(r"traffic_bytes_per_cell = ([0-9.]+)", txt)
+    m2 = re.search(r"kernel_source_sha1 = ([0-9a-f]+)", txt)
+    if not (m1 and m2):
+        return None
+    h = hashlib.sha1()
+    for f in ("lbm_device.cuh", "lbm_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2211_02435_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return float(m1.group(1)) if h.hexdigest() == m2.group(1) else None
+
+
 def make_fields(n):
     rho, u = I.taylor_green((n, n, n), 0.05)
     u = I.add_uniform_noise(u, 1e-3, seed=1)
@@ -284,13 +304,9 @@ def run_cuda(args):
                "sample": f"{edge}^3 cells x {args.cpu_steps} steps of the same method and flow "
                          f"({dt:.1f} s, OpenMP over all cores)"}
 
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tr = json.load(f).get("k_pull_d3q27_cumulant_reg_f32")
-        if tr and tr.get("cells"):
-            traffic = tr["bytes_per_cell"] * N
+    traffic = kernel_traffic_per_cell()
+    if traffic is not None:
+        traffic *= N
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_s * 1e3,

@@ -148,6 +148,16 @@ void launch_invariants_fold(const double* part, int nparts, double* out, cudaStr
   k_invariants_fold<<<1, 256, 0, s>>>(part, nparts, out);
 }
 
+void dispatch_step(int stencil, int storage, const StepArgs& a) { kStep[stencil][storage](a); }
+void dispatch_aux(int stencil, int storage, const AuxArgs& a) { kAux[stencil][storage](a); }
+
+typedef void (*batch_fn)(const BatchArgs&);
+static const batch_fn kBatch[3][4] = {
+    {launch_batch_0_0, launch_batch_0_1, launch_batch_0_2, launch_batch_0_3},
+    {launch_batch_1_0, launch_batch_1_1, launch_batch_1_2, launch_batch_1_3},
+    {launch_batch_2_0, launch_batch_2_1, launch_batch_2_2, launch_batch_2_3}};
+void dispatch_batch(int stencil, int storage, const BatchArgs& a) { kBatch[stencil][storage](a); }
+
 }  // namespace lbm
 
 extern "C" {

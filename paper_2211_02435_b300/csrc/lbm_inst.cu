@@ -35,5 +35,8 @@ void LBM_FN(launch_step_, LBM_ST, LBM_STORE)(const StepArgs& a) {
 void LBM_FN(launch_aux_, LBM_ST, LBM_STORE)(const AuxArgs& a) {
   launch_aux_typed<LBM_ST, StoreT, CompT>(a);
 }
+void LBM_FN(launch_batch_, LBM_ST, LBM_STORE)(const BatchArgs& a) {
+  launch_batch_space<LBM_ST, StoreT, CompT>(a);
+}
 
 }  // namespace lbm

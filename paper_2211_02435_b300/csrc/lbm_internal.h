@@ -56,6 +56,39 @@ LBM_DECL(1, 0) LBM_DECL(1, 1) LBM_DECL(1, 2) LBM_DECL(1, 3)
 LBM_DECL(2, 0) LBM_DECL(2, 1) LBM_DECL(2, 2) LBM_DECL(2, 3)
 #undef LBM_DECL
 
+// ----- batched ensemble (lbm_batch.cu)
+struct BInst {
+  int nx, ny, nz, N;  // box of the instance, N = nx * ny * nz
+  int64_t off;        // element offset of its population block
+  double keep_shear;  // 1 - shear rate of the instance
+};
+enum { BATCH_STEP = 0, BATCH_TGV = 1 };
+struct BatchArgs {
+  int op;
+  const void* src;  // BATCH_STEP: pull source buffer
+  void* dst;        // BATCH_STEP: destination; BATCH_TGV: buffer to set up
+  const BInst* inst;
+  const int2* tiles;  // (instance, first cell) of each tile
+  int ntiles;
+  int cpt;      // cells per thread
+  int threads;  // block size
+  int grid;     // persistent grid size
+  double rates[6];
+  int space, reg, storage;
+  const double* u0;  // BATCH_TGV: amplitude per instance (device)
+  cudaStream_t stream;
+};
+#define LBM_BDECL(ST, SO) void launch_batch_##ST##_##SO(const BatchArgs& a);
+LBM_BDECL(0, 0) LBM_BDECL(0, 1) LBM_BDECL(0, 2) LBM_BDECL(0, 3)
+LBM_BDECL(1, 0) LBM_BDECL(1, 1) LBM_BDECL(1, 2) LBM_BDECL(1, 3)
+LBM_BDECL(2, 0) LBM_BDECL(2, 1) LBM_BDECL(2, 2) LBM_BDECL(2, 3)
+#undef LBM_BDECL
+
 void launch_invariants_fold(const double* part, int nparts, double* out, cudaStream_t s);
+
+// table dispatch to the (stencil, storage) instantiations (lbm_api.cu)
+void dispatch_step(int stencil, int storage, const StepArgs& a);
+void dispatch_aux(int stencil, int storage, const AuxArgs& a);
+void dispatch_batch(int stencil, int storage, const BatchArgs& a);
 
 }  // namespace lbm

@@ -223,6 +223,85 @@ __global__ void __launch_bounds__(INV_THREADS) k_invariants(const S* buf, Geo g,
   if (threadIdx.x < 8) part[(int64_t)blockIdx.x * 8 + threadIdx.x] = sh[0][threadIdx.x];
 }
 
+// ------------------------------------------------------ batched ensemble
+// Persistent pull kernel over many instances: block b handles tiles b,
+// b + gridDim.x, ... of the tile list; a tile is threads * cpt consecutive
+// cells of one instance (cell index c -> x, y, z by division).
+constexpr int BATCH_MAX_THREADS = 256;
+
+LBM_D void cell_xyz(int c, const Geo& g, int& x, int& y, int& z) {
+  const int yz = c / g.nx;
+  x = c - yz * g.nx;
+  z = yz / g.ny;
+  y = yz - z * g.ny;
+}
+
+template <int ST, class S, class T, int SPACE, bool REG>
+__global__ void __launch_bounds__(BATCH_MAX_THREADS)
+    k_batch_pull(const S* __restrict__ src, S* __restrict__ dst, const BInst* __restrict__ inst,
+                 const int2* __restrict__ tiles, int ntiles, int cpt, Rates<T> keep) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int2 tl = tiles[t];
+    const BInst I = inst[tl.x];
+    const Geo g{I.nx, I.ny, I.nz, (int64_t)I.N};
+    Rates<T> k = keep;
+    k.om[0] = T(I.keep_shear);
+    const S* s = src + I.off;
+    S* d = dst + I.off;
+    for (int j = 0; j < cpt; ++j) {
+      const int c = tl.y + j * (int)blockDim.x + (int)threadIdx.x;
+      if (c >= I.N) break;
+      int x, y, z;
+      cell_xyz(c, g, x, y, z);
+      const Nbr n = neighbours(x, y, z, g);
+      T f[q_of(ST)];
+      load_pops<ST, S, T, G_PULL>(s, g, n, c, f);
+      collide<ST, T, SPACE, REG>(f, k);
+      sfor<q_of(ST)>([&](auto I_) {
+        constexpr int i = CI(I_);
+        d[(int64_t)i * g.N + c] = Codec<S>::template enc<T>(f[i], scale_exp(ST, i));
+      });
+    }
+  }
+}
+
+// Taylor-Green set-up of every instance (Eq. 5.1 at t = 0, z-invariant,
+// wavenumber 2 pi / N per axis): the method's equilibrium, written upstream
+// for the pull gather.
+template <int ST, class S, class T, int SPACE>
+__global__ void __launch_bounds__(BATCH_MAX_THREADS)
+    k_batch_tgv(S* __restrict__ buf, const BInst* __restrict__ inst, const int2* __restrict__ tiles,
+                int ntiles, int cpt, const double* __restrict__ u0) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int2 tl = tiles[t];
+    const BInst I = inst[tl.x];
+    const Geo g{I.nx, I.ny, I.nz, (int64_t)I.N};
+    const double a = u0[tl.x];
+    const double kx = 2.0 * 3.14159265358979323846 / I.nx;
+    const double ky = 2.0 * 3.14159265358979323846 / I.ny;
+    S* b = buf + I.off;
+    for (int j = 0; j < cpt; ++j) {
+      const int c = tl.y + j * (int)blockDim.x + (int)threadIdx.x;
+      if (c >= I.N) break;
+      int x, y, z;
+      cell_xyz(c, g, x, y, z);
+      const Nbr n = neighbours(x, y, z, g);
+      double sx, cx, sy, cy;
+      sincos(kx * x, &sx, &cx);
+      sincos(ky * y, &sy, &cy);
+      const double rho = 1.0 - 0.75 * a * a * (cos(2.0 * kx * x) + cos(2.0 * ky * y));
+      T uu[3] = {T(a * cx * sy), T(-a * sx * cy), T(0)};
+      T f[q_of(ST)];
+      equilibrium<ST, T, SPACE>(T(rho - 1.0), uu, f);
+      sfor<q_of(ST)>([&](auto I_) {
+        constexpr int i = CI(I_);
+        const int dc = cell_at(n, g, -vel(ST, i, 0), -vel(ST, i, 1), -vel(ST, i, 2));
+        b[(int64_t)i * g.N + dc] = Codec<S>::template enc<T>(f[i], scale_exp(ST, i));
+      });
+    }
+  }
+}
+
 // --------------------------------------------------------------- launchers
 inline dim3 step_grid(const Geo& g) { return dim3((g.nx + LBM_BX - 1) / LBM_BX, g.ny, g.nz); }
 
@@ -288,6 +367,31 @@ void launch_aux_typed(const AuxArgs& a) {
       else
         k_invariants<ST, S, T, G_AAODD><<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
       break;
+  }
+}
+
+template <int ST, class S, class T, int SPACE, bool REG>
+void launch_batch_typed(const BatchArgs& a) {
+  if (a.op == BATCH_TGV) {
+    k_batch_tgv<ST, S, T, (SPACE == SP_RAW ? SP_RAW : SP_CENTRAL)>
+        <<<a.grid, a.threads, 0, a.stream>>>((S*)a.dst, a.inst, a.tiles, a.ntiles, a.cpt, a.u0);
+    return;
+  }
+  Rates<T> keep;
+  for (int k = 0; k < 6; ++k) keep.om[k] = T(1.0 - a.rates[k]);
+  k_batch_pull<ST, S, T, SPACE, REG><<<a.grid, a.threads, 0, a.stream>>>(
+      (const S*)a.src, (S*)a.dst, a.inst, a.tiles, a.ntiles, a.cpt, keep);
+}
+
+template <int ST, class S, class T>
+void launch_batch_space(const BatchArgs& a) {
+  switch (a.space * 2 + (a.reg ? 1 : 0)) {
+    case SP_RAW * 2: launch_batch_typed<ST, S, T, SP_RAW, false>(a); break;
+    case SP_RAW * 2 + 1: launch_batch_typed<ST, S, T, SP_RAW, true>(a); break;
+    case SP_CENTRAL * 2: launch_batch_typed<ST, S, T, SP_CENTRAL, false>(a); break;
+    case SP_CENTRAL * 2 + 1: launch_batch_typed<ST, S, T, SP_CENTRAL, true>(a); break;
+    case SP_CUMULANT * 2: launch_batch_typed<ST, S, T, SP_CUMULANT, false>(a); break;
+    default: launch_batch_typed<ST, S, T, SP_CUMULANT, true>(a); break;
   }
 }
 
