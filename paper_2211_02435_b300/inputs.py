@@ -85,3 +85,18 @@ def shear_viscosity_rate(nu):
     """Shear relaxation rate for kinematic viscosity nu with c_s^2 = 1/3:
     nu = (1/omega - 1/2) / 3."""
     return 1.0 / (3.0 * nu + 0.5)
+
+
+def batch_ensemble(n=4096, edges=(16, 24, 32, 48, 64, 96), nu_range=(1e-4, 1e-1),
+                   u0_range=(0.01, 0.08), seed=4):
+    """Parameters of an ensemble of cubic periodic Taylor-Green domains: edge
+    lengths drawn uniformly from ``edges``, viscosity log-uniform in
+    ``nu_range``, amplitude uniform in ``u0_range``.  Returns (dims[n][3],
+    nu[n], u0[n])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    e = rng.choice(np.asarray(edges), size=n)
+    lo, hi = np.log(nu_range[0]), np.log(nu_range[1])
+    nu = np.exp(rng.uniform(lo, hi, size=n))
+    u0 = rng.uniform(u0_range[0], u0_range[1], size=n)
+    dims = np.stack([e, e, e], axis=1).astype(np.int64)
+    return dims, nu, u0

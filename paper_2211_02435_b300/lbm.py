@@ -44,6 +44,14 @@ class Params(ctypes.Structure):
                 ("stream", ctypes.c_void_p)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("cells_per_thread", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int), ("per_instance", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -75,6 +83,22 @@ def lib():
         L.lbm_destroy.restype = None
         L.lbm_error_string.argtypes = [c_int]
         L.lbm_error_string.restype = ctypes.c_char_p
+        L.lbm_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Params), c_int,
+                                       ctypes.POINTER(i64), d]
+        L.lbm_batch_init_velocity.argtypes = [vp, c_int, vp, vp, c_int]
+        L.lbm_batch_init_tgv.argtypes = [vp, d]
+        L.lbm_batch_step.argtypes = [vp, i64]
+        L.lbm_batch_get_populations.argtypes = [vp, c_int, vp, c_int]
+        L.lbm_batch_macroscopic.argtypes = [vp, c_int, vp, vp, c_int]
+        L.lbm_batch_cells.argtypes = [vp]
+        L.lbm_batch_cells.restype = i64
+        L.lbm_batch_size.argtypes = [vp]
+        L.lbm_batch_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+        L.lbm_batch_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+        L.lbm_batch_autotune.argtypes = [vp, c_int, ctypes.POINTER(Tuning), d]
+        L.lbm_batch_get_time.argtypes = [vp, ctypes.POINTER(i64)]
+        L.lbm_batch_destroy.argtypes = [vp]
+        L.lbm_batch_destroy.restype = None
         _lib = L
     return _lib
 
@@ -228,3 +252,123 @@ class Lattice:
 
     def set_stream(self, stream):
         _check(lib().lbm_set_stream(self._h, stream_handle(stream)), "lbm_set_stream")
+
+
+class Batch:
+    """Ensemble of independent periodic lattices advanced by one persistent
+    launch per step (include/lbm_batch.h)."""
+
+    def __init__(self, stencil, space, equilibrium, storage, rates, dims_list,
+                 shear_rates=None, stream=None):
+        self.stencil, self.space, self.storage = stencil, space, storage
+        self.q = Q_OF[stencil]
+        self.d = 2 if stencil == D2Q9 else 3
+        self.dims = [tuple(int(v) for v in (list(dm) + [1] * (3 - len(dm)))) for dm in dims_list]
+        n = len(self.dims)
+        flat = (ctypes.c_int64 * (3 * n))(*[v for dm in self.dims for v in dm])
+        r = list(rates) + [1.0] * (6 - len(rates))
+        p = Params(stencil, space, equilibrium, storage, PULL, (ctypes.c_double * 6)(*r),
+                   (ctypes.c_int64 * 3)(1, 1, 1), PERIODIC, stream_handle(stream))
+        sr = None if shear_rates is None else (ctypes.c_double * n)(*[float(x) for x in shear_rates])
+        h = ctypes.c_void_p()
+        _check(lib().lbm_batch_create(ctypes.byref(h), ctypes.byref(p), n, flat, sr),
+               "lbm_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __len__(self):
+        return len(self.dims)
+
+    def cells(self):
+        return int(lib().lbm_batch_cells(self._h))
+
+    def _n(self, k):
+        nx, ny, nz = self.dims[k]
+        return nx * ny * nz
+
+    def init_velocity(self, k, rho, u):
+        N = self._n(k)
+        pr, dr = _ptr(rho, N)
+        pu, du = _ptr(u, self.d * N)
+        _check(lib().lbm_batch_init_velocity(self._h, int(k), pr, pu, du), "lbm_batch_init_velocity")
+
+    def init_tgv(self, u0):
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        if u0.size != len(self):
+            raise ValueError("one amplitude per instance")
+        _check(lib().lbm_batch_init_tgv(self._h, u0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "lbm_batch_init_tgv")
+
+    def step(self, n=1):
+        _check(lib().lbm_batch_step(self._h, int(n)), "lbm_batch_step")
+
+    def get_populations(self, k):
+        nx, ny, nz = self.dims[k]
+        out = np.empty(self.q * self._n(k))
+        _check(lib().lbm_batch_get_populations(self._h, int(k), out.ctypes.data, 0),
+               "lbm_batch_get_populations")
+        return out.reshape(self.q, nz, ny, nx)
+
+    def macroscopic(self, k):
+        nx, ny, nz = self.dims[k]
+        rho = np.empty(self._n(k))
+        u = np.empty(self.d * self._n(k))
+        _check(lib().lbm_batch_macroscopic(self._h, int(k), rho.ctypes.data, u.ctypes.data, 0),
+               "lbm_batch_macroscopic")
+        return rho.reshape(nz, ny, nx), u.reshape(self.d, nz, ny, nx)
+
+    def set_tuning(self, threads=128, cells_per_thread=4, blocks_per_sm=8, per_instance=0):
+        t = Tuning(threads, cells_per_thread, blocks_per_sm, per_instance)
+        _check(lib().lbm_batch_set_tuning(self._h, ctypes.byref(t)), "lbm_batch_set_tuning")
+
+    def get_tuning(self):
+        t = Tuning()
+        _check(lib().lbm_batch_get_tuning(self._h, ctypes.byref(t)), "lbm_batch_get_tuning")
+        return t.as_dict()
+
+    def autotune(self, trial_steps=2, cache_path=None, key=None):
+        """Pick the launch shape by timing (advances the ensemble: call before
+        the init_* calls).  With cache_path, a JSON file maps key -> shape and
+        a cached shape is applied without timing."""
+        import json
+        import os
+        if cache_path and key and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                cache = json.load(f)
+            if key in cache:
+                self.set_tuning(**cache[key]["tuning"])
+                return cache[key]["tuning"], cache[key]["mlups"]
+        t = Tuning()
+        mlups = ctypes.c_double()
+        _check(lib().lbm_batch_autotune(self._h, int(trial_steps), ctypes.byref(t),
+                                        ctypes.byref(mlups)), "lbm_batch_autotune")
+        if cache_path and key:
+            cache = {}
+            if os.path.exists(cache_path):
+                with open(cache_path) as f:
+                    cache = json.load(f)
+            cache[key] = {"tuning": t.as_dict(), "mlups": mlups.value}
+            with open(cache_path, "w") as f:
+                json.dump(cache, f, indent=1)
+        return t.as_dict(), mlups.value
+
+    def time(self):
+        t = ctypes.c_int64()
+        _check(lib().lbm_batch_get_time(self._h, ctypes.byref(t)), "lbm_batch_get_time")
+        return t.value
