@@ -163,6 +163,39 @@ int lbm_set_populations(lbm_ctx* ctx, const double* df, int on_device);
  * DIVERGED (out is still filled when out[6] > 0). */
 int lbm_invariants(lbm_ctx* ctx, double out[8]);
 
+/* Allocation-free variant of lbm_invariants for callers that must not
+ * allocate device memory (a host framework that owns the whole device pool,
+ * a real-time loop where an allocation could stall or fail, or a caller that
+ * only hands this library existing buffers).  The paper has no counterpart;
+ * this is a convenience of the library.
+ *
+ * df: device pointer to the caller's zero-centered populations in the
+ * storage type `storage`, structure of arrays df[i*N + c] with slot i of
+ * cell c holding f_i of that cell (the canonical f(n), as an AA context holds
+ * it at even parity).  dims: Nx, Ny, Nz (Nz = 1 for D2Q9), at most
+ * LBM_STATIC_MAX_CELLS cells in all; larger or non-positive sizes are
+ * rejected with LBM_ERR_INVALID.  out: 8 doubles as lbm_invariants; a device
+ * pointer when on_device = 1 (the call then returns without synchronising
+ * and cannot report DIVERGED), else host memory (the call synchronises
+ * `stream` and returns LBM_ERR_DIVERGED when out[6] > 0).  stream: a
+ * cudaStream_t, NULL = legacy default stream.
+ *
+ * The partial sums live in one static device array of
+ * LBM_STATIC_SCRATCH_ROWS * 8 + 8 doubles (75,840 bytes) that every GPU
+ * which loads liblbm.so keeps until the process exits; no cudaMalloc,
+ * cudaFree or other allocating routine is called.  The first call on a
+ * device looks up that array's device address (with the device current),
+ * so make the first call before any stream capture.  All calls on a device
+ * share the array: calls whose work overlaps on the GPU (other streams, or
+ * other host threads) race and must be serialised by the caller.  Each call
+ * overwrites every partial row it reads, so no state carries over.
+ * Errors: INVALID, CUDA, DIVERGED. */
+#define LBM_STATIC_SCRATCH_ROWS 1184
+#define LBM_STATIC_MAX_CELLS 2147483647LL
+int lbm_invariants_noalloc(int stencil, int storage, const void* df,
+                           const int64_t dims[3], double out[8], int on_device,
+                           void* stream);
+
 /* Checkpoint: the raw device buffer plus a header (method, dims, storage,
  * parity, step counter).  lbm_state_bytes gives the size; get/set copy
  * through host memory.  A state from a context with other parameters is

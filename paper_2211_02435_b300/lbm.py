@@ -97,6 +97,7 @@ def lib():
         L.lbm_batch_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
         L.lbm_batch_autotune.argtypes = [vp, c_int, ctypes.POINTER(Tuning), d]
         L.lbm_batch_get_time.argtypes = [vp, ctypes.POINTER(i64)]
+        L.lbm_invariants_noalloc.argtypes = [c_int, c_int, vp, ctypes.POINTER(i64), vp, c_int, vp]
         L.lbm_batch_destroy.argtypes = [vp]
         L.lbm_batch_destroy.restype = None
         _lib = L
@@ -136,6 +137,28 @@ def stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def invariants_noalloc(stencil, storage, df, dims, out=None, stream=None):
+    """lbm_invariants_noalloc: FP64 invariants of a caller-owned device
+    population field (a CUDA tensor of the storage type, slot i of cell c at
+    i*N + c) without any device allocation in the library.  ``out``: None
+    (returns a dict, host result) or a CUDA float64 tensor of 8 elements
+    (filled asynchronously on ``stream``)."""
+    dims = list(dims) + [1] * (3 - len(dims))
+    d = (ctypes.c_int64 * 3)(*[int(v) for v in dims])
+    ptr = df.data_ptr() if hasattr(df, "data_ptr") else int(df)
+    if out is None:
+        host = (ctypes.c_double * 8)()
+        rc = lib().lbm_invariants_noalloc(stencil, storage, ptr, d, ctypes.addressof(host), 0,
+                                          stream_handle(stream))
+        _check(rc, "lbm_invariants_noalloc")
+        keys = ("mass_dev", "jx", "jy", "jz", "energy", "max_u", "nonfinite", "cells")
+        return dict(zip(keys, list(host)))
+    p, dev = _ptr(out, 8, True)
+    _check(lib().lbm_invariants_noalloc(stencil, storage, ptr, d, p, dev, stream_handle(stream)),
+           "lbm_invariants_noalloc")
+    return out
 
 
 class Lattice:
