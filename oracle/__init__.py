@@ -83,6 +83,11 @@ def lib():
         L.lbm_oracle_init.argtypes = [m, i64, d, d, d]
         L.lbm_oracle_step.argtypes = [m, i64, d, ctypes.c_int64, ctypes.c_int]
         L.lbm_oracle_macroscopic.argtypes = [m, i64, d, d, d]
+        L.lbm_oracle_closure_features.argtypes = [ctypes.c_int, d, ctypes.c_double, d]
+        L.lbm_oracle_closure_mlp.argtypes = [d, d, d, d, d]
+        L.lbm_oracle_closure_step.argtypes = [m, i64, d, d, d, d, ctypes.c_int]
+        L.lbm_oracle_closure_loss.argtypes = [m, i64, d, d, d, d, d, ctypes.c_int]
+        L.lbm_oracle_closure_loss.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -208,3 +213,38 @@ def macroscopic(m, dims, df):
                                         _dp(_f64(df)), _dp(rho), _dp(u)))
     shp = (dm[2], dm[1], dm[0])
     return rho.reshape(shp), u.reshape((d,) + shp)
+
+
+# ------------------------------------------------------------ learned closure
+CLOSURE_NPARAM = 1444
+
+
+def closure_features(stencil, df, omega_shear):
+    """Raw features [7] of one cell's zero-centered populations."""
+    out = np.zeros(7)
+    _check(lib().lbm_oracle_closure_features(stencil, _dp(_f64(df)), float(omega_shear), _dp(out)))
+    return out
+
+
+def closure_mlp(params, shift, scale, raw):
+    """Per-cell rates of orders 3..6 from raw features."""
+    om = np.zeros(4)
+    _check(lib().lbm_oracle_closure_mlp(_dp(_f64(params)), _dp(_f64(shift)), _dp(_f64(scale)),
+                                        _dp(_f64(raw)), _dp(om)))
+    return om
+
+
+def closure_step(m, dims, df, params, shift, scale, nthreads=0):
+    dm = _dims(dims)
+    out = _f64(df).copy()
+    _check(lib().lbm_oracle_closure_step(ctypes.byref(m), dm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                         _dp(out), _dp(_f64(params)), _dp(_f64(shift)),
+                                         _dp(_f64(scale)), int(nthreads)))
+    return out
+
+
+def closure_loss(m, dims, df_s, df_t, params, shift, scale, nthreads=0):
+    dm = _dims(dims)
+    return lib().lbm_oracle_closure_loss(ctypes.byref(m), dm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                         _dp(_f64(df_s)), _dp(_f64(df_t)), _dp(_f64(params)),
+                                         _dp(_f64(shift)), _dp(_f64(scale)), int(nthreads))

@@ -715,3 +715,175 @@ int lbm_oracle_macroscopic(const lbm_oracle_method* m, const int64_t* dims,
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* learned closure (test infrastructure for the GPU closure kernels)   */
+/* ------------------------------------------------------------------ */
+static double det3(const double A[3][3]) {
+  return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+         A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+         A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+}
+
+static double inv2(const double A[3][3]) { /* second principal invariant */
+  double tr = A[0][0] + A[1][1] + A[2][2], trsq = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) trsq += A[a][b] * A[b][a];
+  return 0.5 * (tr * tr - trsq);
+}
+
+static int features_cell(const lattice_t* L, const double* df, double omega_s,
+                         double* out) {
+  double f[QMAX], K[QMAX][QMAX], kappa[QMAX], u[3], drho = 0.0, j[3] = {0, 0, 0};
+  for (int i = 0; i < L->q; ++i) {
+    f[i] = df[i] + L->w[i];
+    drho += df[i];
+    for (int d = 0; d < 3; ++d) j[d] += L->xi[i][d] * df[i];
+  }
+  const double rho = 1.0 + drho;
+  for (int d = 0; d < 3; ++d) u[d] = j[d] / rho;
+  central_matrix(L, u, K);
+  matvec(L->q, K, f, kappa);
+  double Pi[3][3], S[3][3], D[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      int e[3] = {0, 0, 0};
+      e[a]++;
+      e[b]++;
+      const int k = L->mono[e[0]][e[1]][e[2]];
+      if (k < 0) return -1;
+      Pi[a][b] = kappa[k] / rho - (a == b ? 1.0 / 3.0 : 0.0);
+      S[a][b] = -1.5 * omega_s * Pi[a][b];
+    }
+  const double trP = Pi[0][0] + Pi[1][1] + Pi[2][2];
+  double fro = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      D[a][b] = Pi[a][b] - (a == b ? trP / 3.0 : 0.0);
+      fro += Pi[a][b] * Pi[a][b];
+    }
+  out[0] = S[0][0] + S[1][1] + S[2][2];
+  out[1] = inv2(S);
+  out[2] = det3(S);
+  out[3] = inv2(D);
+  out[4] = det3(D);
+  out[5] = sqrt(fro);
+  out[6] = drho;
+  return 0;
+}
+
+int lbm_oracle_closure_features(int stencil, const double* df,
+                                double omega_shear, double out[7]) {
+  if (build_lattice(stencil) || stencil == LBM_ORACLE_D2Q9 || !df || !out) return -1;
+  return features_cell(&g_lat[stencil], df, omega_shear, out);
+}
+
+int lbm_oracle_closure_mlp(const double* P, const double* shift,
+                           const double* scale, const double raw[7],
+                           double omega[4]) {
+  enum { NI = LBM_ORACLE_CLOSURE_NIN, NH = LBM_ORACLE_CLOSURE_NH, NO = LBM_ORACLE_CLOSURE_NOUT };
+  const double* W1 = P;
+  const double* b1 = W1 + NH * NI;
+  const double* W2 = b1 + NH;
+  const double* b2 = W2 + NH * NH;
+  const double* W3 = b2 + NH;
+  const double* b3 = W3 + NO * NH;
+  double x[NI], h1[NH], h2[NH];
+  int ok = 1;
+  for (int i = 0; i < NI; ++i) {
+    x[i] = (raw[i] - shift[i]) * scale[i];
+    ok = ok && isfinite(x[i]);
+  }
+  for (int r = 0; r < NH; ++r) {
+    double a = b1[r];
+    for (int c = 0; c < NI; ++c) a += W1[r * NI + c] * x[c];
+    h1[r] = tanh(a);
+  }
+  for (int r = 0; r < NH; ++r) {
+    double a = b2[r];
+    for (int c = 0; c < NH; ++c) a += W2[r * NH + c] * h1[c];
+    h2[r] = tanh(a);
+  }
+  for (int r = 0; r < NO; ++r) {
+    double z = b3[r];
+    for (int c = 0; c < NH; ++c) z += W3[r * NH + c] * h2[c];
+    double om = 2.0 / (1.0 + exp(-z));
+    if (om < 1e-3) om = 1e-3;
+    if (om > 1.999) om = 1.999;
+    omega[r] = om;
+    ok = ok && isfinite(om);
+  }
+  if (!ok)
+    for (int r = 0; r < NO; ++r) omega[r] = 1.0;
+  return 0;
+}
+
+int lbm_oracle_closure_step(const lbm_oracle_method* base,
+                            const int64_t* dims, double* df,
+                            const double* params, const double* shift,
+                            const double* scale, int nthreads) {
+  int rc = check_method(base);
+  if (rc) return rc;
+  const lattice_t* L = &g_lat[base->stencil];
+  if (L->d != 3) return -1;
+  const int64_t nx = dims[0], ny = dims[1], nz = dims[2], N = nx * ny * nz;
+  const int q = L->q;
+  double* out = (double*)malloc(sizeof(double) * q * N);
+  if (!out) return -1;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  int err = 0;
+#pragma omp parallel for schedule(static) reduction(| : err)
+  for (int64_t c = 0; c < N; ++c) {
+    const int64_t x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
+    double in[QMAX], post[QMAX], raw[7], om[4];
+    for (int i = 0; i < q; ++i) in[i] = df[i * N + c];
+    lbm_oracle_method m = *base;
+    if (features_cell(L, in, base->rates[0], raw)) err |= 1;
+    lbm_oracle_closure_mlp(params, shift, scale, raw, om);
+    for (int k = 0; k < 4; ++k) m.rates[2 + k] = om[k];
+    if (collide_cell(L, &m, in, post)) err |= 1;
+    for (int i = 0; i < q; ++i) {
+      int64_t xd = (x + L->xi[i][0] + nx) % nx;
+      int64_t yd = (y + L->xi[i][1] + ny) % ny;
+      int64_t zd = (z + L->xi[i][2] + nz) % nz;
+      out[i * N + (zd * ny + yd) * nx + xd] = post[i];
+    }
+  }
+  memcpy(df, out, sizeof(double) * q * N);
+  free(out);
+  return err ? -1 : 0;
+}
+
+double lbm_oracle_closure_loss(const lbm_oracle_method* base,
+                               const int64_t* dims, const double* df_s,
+                               const double* df_t, const double* params,
+                               const double* shift, const double* scale,
+                               int nthreads) {
+  if (check_method(base)) return NAN;
+  const lattice_t* L = &g_lat[base->stencil];
+  const int64_t N = dims[0] * dims[1] * dims[2];
+  double* work = (double*)malloc(sizeof(double) * L->q * N);
+  double *r1 = (double*)malloc(sizeof(double) * N), *r2 = (double*)malloc(sizeof(double) * N);
+  double *u1 = (double*)malloc(sizeof(double) * 3 * N), *u2 = (double*)malloc(sizeof(double) * 3 * N);
+  double loss = NAN;
+  if (work && r1 && r2 && u1 && u2) {
+    memcpy(work, df_s, sizeof(double) * L->q * N);
+    if (lbm_oracle_closure_step(base, dims, work, params, shift, scale, nthreads) == 0 &&
+        lbm_oracle_macroscopic(base, dims, work, r1, u1) == 0 &&
+        lbm_oracle_macroscopic(base, dims, df_t, r2, u2) == 0) {
+      double s = 0.0;
+      for (int64_t k = 0; k < 3 * N; ++k) s += (u1[k] - u2[k]) * (u1[k] - u2[k]);
+      loss = s / (double)N;
+    }
+  }
+  free(work);
+  free(r1);
+  free(r2);
+  free(u1);
+  free(u2);
+  return loss;
+}

@@ -123,6 +123,46 @@ int lbm_oracle_step(const lbm_oracle_method* m, const int64_t* dims,
 int lbm_oracle_macroscopic(const lbm_oracle_method* m, const int64_t* dims,
                            const double* df, double* rho, double* u);
 
+/* ------------------------------------------------------------------ */
+/* Learned closure (not in the paper): a per-cell MLP 7 -> 32 -> 32 -> 4 */
+/* sets the relaxation rates of orders 3..6 of the cumulant collision.    */
+/* ------------------------------------------------------------------ */
+#define LBM_ORACLE_CLOSURE_NIN 7
+#define LBM_ORACLE_CLOSURE_NH 32
+#define LBM_ORACLE_CLOSURE_NOUT 4
+#define LBM_ORACLE_CLOSURE_NPARAM 1444 /* W1[32][7] b1 W2[32][32] b2 W3[4][32] b3 */
+
+/* Raw features of one cell from its zero-centered populations df[q]:
+ * with Pi = kappa_2 / rho - I/3 (second-order central moments, Sec. 2.3.2),
+ * S = -(3 omega_shear / 2) Pi and D = Pi - tr(Pi)/3 I:
+ * out = {tr S, I2(S), det S, I2(D), det D, |Pi|_F, rho - 1}, where
+ * I2(A) = ((tr A)^2 - tr(A A)) / 2.  3-D stencils only. */
+int lbm_oracle_closure_features(int stencil, const double* df,
+                                double omega_shear, double out[7]);
+
+/* omega[4] (orders 3..6) = clamp(2 sigmoid(W3 tanh(W2 tanh(W1 x + b1) + b2)
+ * + b3), 1e-3, 1.999) with x_i = (raw_i - shift_i) * scale_i; all four are 1
+ * if any input or output is not finite. */
+int lbm_oracle_closure_mlp(const double* params, const double* shift,
+                           const double* scale, const double raw[7],
+                           double omega[4]);
+
+/* One step (collide with per-cell rates of orders 3..6 from the MLP, then
+ * stream) of the SoA pre-collision state df[q][N], in place.  base gives
+ * the stencil, space and the shear / bulk rates. */
+int lbm_oracle_closure_step(const lbm_oracle_method* base,
+                            const int64_t* dims, double* df,
+                            const double* params, const double* shift,
+                            const double* scale, int nthreads);
+
+/* One-step loss: mean over cells of |u(step(df_s)) - u(df_t)|^2 (Eq. 2.3
+ * velocities).  Returns NaN on error. */
+double lbm_oracle_closure_loss(const lbm_oracle_method* base,
+                               const int64_t* dims, const double* df_s,
+                               const double* df_t, const double* params,
+                               const double* shift, const double* scale,
+                               int nthreads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,151 @@
+"""Pins of the oracle's learned-closure functions (features, MLP, closure
+step, loss) against independent routes: eigenvalue invariants of directly
+summed moments, symmetry of the lattice, closed-form networks, and the
+already pinned fixed-rate collision."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from paper_2211_02435_b300 import inputs as I
+
+NP = 1444
+
+
+@pytest.fixture(scope="module")
+def O(oracle_lib):
+    return oracle_lib
+
+
+def _state(O, seed, st=2):
+    xi, w, _ = O.lattice(st)
+    rng = np.random.default_rng(seed)
+    m = O.method(st, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [1.8] + [1.0] * 5)
+    rho = 1 + 0.02 * rng.standard_normal()
+    u = 0.06 * rng.standard_normal(3)
+    return xi, w, O.equilibrium(m, rho, u)[0] + 3e-3 * w * rng.standard_normal(len(w))
+
+
+def _features_direct(xi, w, df, om):
+    f = df + w
+    rho = f.sum()
+    u = (f @ xi) / rho
+    c = xi - u
+    Pi = np.einsum("i,ia,ib->ab", f, c, c) / rho - np.eye(3) / 3
+    S = -1.5 * om * Pi
+    D = Pi - np.trace(Pi) / 3 * np.eye(3)
+
+    def inv(A):
+        ev = np.linalg.eigvalsh(A)
+        return ev.sum(), ev[0] * ev[1] + ev[1] * ev[2] + ev[0] * ev[2], ev.prod()
+
+    s1, s2, s3 = inv(S)
+    _, d2, d3 = inv(D)
+    return np.array([s1, s2, s3, d2, d3, np.sqrt((Pi * Pi).sum()), rho - 1])
+
+
+@pytest.mark.parametrize("st", [1, 2])
+def test_features_equal_eigenvalue_invariants_of_summed_moments(O, st):
+    for seed in range(5):
+        xi, w, df = _state(O, seed, st)
+        got = O.closure_features(st, df, 1.8)
+        ref = _features_direct(xi, w, df, 1.8)
+        np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-18)
+
+
+def test_features_vanish_at_the_maxwellian_equilibrium(O):
+    m = O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [1.8] + [1.0] * 5)
+    feq = O.equilibrium(m, 1.013, np.array([0.04, -0.03, 0.02]))[0]
+    got = O.closure_features(2, feq, 1.8)
+    assert np.abs(got[:6]).max() < 1e-15
+    assert abs(got[6] - 0.013) < 1e-15
+
+
+def test_features_are_invariant_under_lattice_symmetries(O):
+    xi, w, df = _state(O, 11)
+    base = O.closure_features(2, df, 1.7)
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product([1, -1], repeat=3):
+            P = np.zeros((3, 3))
+            for a in range(3):
+                P[a, perm[a]] = signs[a]
+            mapped = (xi @ P.T).astype(int)
+            idx = [int(np.where((xi == v).all(1))[0][0]) for v in mapped]
+            df2 = np.empty_like(df)
+            df2[idx] = df
+            np.testing.assert_allclose(O.closure_features(2, df2, 1.7), base, rtol=1e-10,
+                                       atol=1e-20)
+
+
+def test_mlp_closed_form_cases(O):
+    shift, scale = np.zeros(7), np.ones(7)
+    raw = np.array([0.3, -0.2, 0.1, 0.05, -0.4, 0.2, 0.01])
+    assert np.array_equal(O.closure_mlp(np.zeros(NP), shift, scale, raw), np.ones(4))
+    p = np.zeros(NP)
+    p[0] = 1.0  # W1[0][0]
+    o2 = 32 * 7 + 32
+    p[o2] = 1.0  # W2[0][0]
+    o3 = o2 + 32 * 32 + 32
+    c = np.array([0.7, -1.3, 2.0, -0.2])
+    for k in range(4):
+        p[o3 + k * 32] = c[k]  # W3[k][0]
+    ref = 2.0 / (1.0 + np.exp(-c * math.tanh(math.tanh(raw[0]))))
+    np.testing.assert_allclose(O.closure_mlp(p, shift, scale, raw), ref, rtol=1e-15)
+    # normalisation, clamping and the non-finite fallback
+    sh = np.array([0.1] + [0.0] * 6)
+    sc = np.array([3.0] + [1.0] * 6)
+    ref2 = 2.0 / (1.0 + np.exp(-c * math.tanh(math.tanh(3.0 * (raw[0] - 0.1)))))
+    np.testing.assert_allclose(O.closure_mlp(p, sh, sc, raw), ref2, rtol=1e-15)
+    big = p.copy()
+    big[o3:o3 + 4 * 32] *= 1e4
+    out = O.closure_mlp(big, shift, scale, raw)
+    assert set(np.round(out, 6)) <= {1e-3, 1.999}
+    bad = raw.copy()
+    bad[3] = np.nan
+    assert np.array_equal(O.closure_mlp(p, shift, scale, bad), np.ones(4))
+
+
+def _dims():
+    return (6, 5, 4)
+
+
+def _field(O, seed):
+    dims = _dims()
+    rho, u = I.taylor_green(dims, 0.05)
+    u = I.add_uniform_noise(u, 5e-3, seed=seed)
+    m = O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [1.9] + [1.0] * 5)
+    df = O.init(m, dims, rho, u)
+    _, w, _ = O.lattice(2)
+    pert = I.random_deviations(27, int(np.prod(dims)), 1e-3, seed=seed + 1)
+    return dims, df + (w[:, None] * pert).reshape(df.shape)
+
+
+def test_closure_step_with_constant_rates_is_the_plain_method(O):
+    dims, df = _field(O, 3)
+    shift, scale = np.zeros(7), np.ones(7)
+    base = O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [1.9, 1.0, 0.0, 0.0, 0.0, 0.0])
+    p = np.zeros(NP)
+    out = O.closure_step(base, dims, df, p, shift, scale)
+    plain = O.step(O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [1.9] + [1.0] * 5), dims, df, 1)
+    np.testing.assert_allclose(out, plain, rtol=0, atol=1e-17)
+    om = np.array([1.3, 0.7, 1.6, 1.1])
+    o3 = 32 * 7 + 32 + 32 * 32 + 32 + 4 * 32
+    p[o3:o3 + 4] = np.log(om / (2 - om))  # b3 = logit(omega / 2)
+    out = O.closure_step(base, dims, df, p, shift, scale)
+    plain = O.step(O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [1.9, 1.0] + list(om)), dims, df, 1)
+    np.testing.assert_allclose(out, plain, rtol=0, atol=1e-16)
+
+
+def test_closure_loss_is_mean_squared_velocity_error_of_one_step(O):
+    dims, df = _field(O, 5)
+    _, target = _field(O, 9)
+    base = O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [1.9, 1.0, 0.0, 0.0, 0.0, 0.0])
+    rng = np.random.default_rng(1)
+    p = 0.3 * rng.standard_normal(NP)
+    shift, scale = np.zeros(7), np.full(7, 50.0)
+    loss = O.closure_loss(base, dims, df, target, p, shift, scale)
+    stepped = O.closure_step(base, dims, df, p, shift, scale)
+    _, u1 = O.macroscopic(base, dims, stepped)
+    _, u2 = O.macroscopic(base, dims, target)
+    assert abs(loss - ((u1 - u2) ** 2).sum() / np.prod(dims)) < 1e-18
