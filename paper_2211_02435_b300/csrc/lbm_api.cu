@@ -46,22 +46,7 @@ struct StateHeader {
 
 }  // namespace
 
-struct lbm_ctx {
-  lbm_params p;
-  int q, d;
-  Geo g;
-  int eb;
-  void* buf[2];
-  int cur;     // pull: buffer holding the newest post-collision state
-  int parity;  // AA: number of completed steps mod 2
-  int64_t t;
-  cudaStream_t stream;
-  double* part;  // invariants scratch: nparts rows of 8 doubles, then 8
-  int nparts;
-  int space;  // effective collision space (POPULATIONS -> RAW)
-  double rates[6];
-  int reg;
-};
+
 
 namespace {
 
@@ -247,6 +232,7 @@ void lbm_destroy(lbm_ctx* c) {
   for (int b = 0; b < 2; ++b)
     if (c->buf[b]) cudaFree(c->buf[b]);
   if (c->part) cudaFree(c->part);
+  if (c->closure) lbm::free_closure(c->closure);
   delete c;
 }
 
@@ -330,7 +316,10 @@ int lbm_step(lbm_ctx* c, int64_t n) {
       a.mode = lbm::MODE_PULL;
       a.src = c->buf[c->cur];
       a.dst = c->buf[1 - c->cur];
-      fn(a);
+      if (c->closure)
+        lbm::launch_closure_step(a, c->closure);
+      else
+        fn(a);
       c->cur = 1 - c->cur;
     } else {
       a.mode = c->parity ? lbm::MODE_AA_ODD : lbm::MODE_AA_EVEN;

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "lbm.h"
+
 namespace lbm {
 
 struct Geo {
@@ -91,4 +93,29 @@ void dispatch_step(int stencil, int storage, const StepArgs& a);
 void dispatch_aux(int stencil, int storage, const AuxArgs& a);
 void dispatch_batch(int stencil, int storage, const BatchArgs& a);
 
+// closure (lbm_closure.cu): fused learned-rate step of a context; frees
+// the context's device closure parameters
+void launch_closure_step(const StepArgs& a, const void* closure);
+void free_closure(void* closure);
+
 }  // namespace lbm
+
+// single-domain context (shared by lbm_api.cu and lbm_closure.cu)
+struct lbm_ctx {
+  lbm_params p;
+  int q, d;
+  lbm::Geo g;
+  int eb;
+  void* buf[2];
+  int cur;     // pull: buffer holding the newest post-collision state
+  int parity;  // AA: number of completed steps mod 2
+  int64_t t;
+  cudaStream_t stream;
+  double* part;  // invariants scratch: nparts rows of 8 doubles, then 8
+  int nparts;
+  int space;  // effective collision space (POPULATIONS -> RAW)
+  double rates[6];
+  int reg;
+  void* closure;  // device closure parameters (lbm_closure.cu), NULL = off
+};
+

@@ -52,6 +52,13 @@ class Tuning(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ClosureWeights(ctypes.Structure):
+    """lbm_closure_weights: input normalisation and BF16 weight bits."""
+    _fields_ = [("shift", ctypes.c_float * 7), ("scale", ctypes.c_float * 7),
+                ("w", ctypes.c_uint16 * 1444)]
+
+
+CLOSURE_NPARAM = 1444
 _lib = None
 
 
@@ -98,6 +105,22 @@ def lib():
         L.lbm_batch_autotune.argtypes = [vp, c_int, ctypes.POINTER(Tuning), d]
         L.lbm_batch_get_time.argtypes = [vp, ctypes.POINTER(i64)]
         L.lbm_invariants_noalloc.argtypes = [c_int, c_int, vp, ctypes.POINTER(i64), vp, c_int, vp]
+        L.lbm_set_closure.argtypes = [vp, ctypes.POINTER(ClosureWeights)]
+        f32p = ctypes.POINTER(ctypes.c_float)
+        L.lbm_trainer_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.c_double,
+                                         ctypes.c_double, c_int, vp]
+        L.lbm_trainer_add_restricted.argtypes = [vp, vp]
+        L.lbm_trainer_add_snapshot.argtypes = [vp, vp, c_int]
+        L.lbm_trainer_snapshot_count.argtypes = [vp]
+        L.lbm_trainer_get_snapshot.argtypes = [vp, c_int, vp, c_int]
+        L.lbm_trainer_features.argtypes = [vp, c_int, vp, c_int]
+        L.lbm_trainer_set_params.argtypes = [vp, f32p, f32p, f32p]
+        L.lbm_trainer_get_params.argtypes = [vp, f32p]
+        L.lbm_trainer_loss_grad.argtypes = [vp, c_int, d, d]
+        L.lbm_trainer_adam_step.argtypes = [vp, c_int, ctypes.c_double, d]
+        L.lbm_trainer_export.argtypes = [vp, ctypes.POINTER(ClosureWeights)]
+        L.lbm_trainer_destroy.argtypes = [vp]
+        L.lbm_trainer_destroy.restype = None
         L.lbm_batch_destroy.argtypes = [vp]
         L.lbm_batch_destroy.restype = None
         _lib = L
@@ -276,6 +299,11 @@ class Lattice:
     def set_stream(self, stream):
         _check(lib().lbm_set_stream(self._h, stream_handle(stream)), "lbm_set_stream")
 
+    def set_closure(self, weights):
+        """Enable the learned rates (a ClosureWeights) or disable them (None)."""
+        ptr = None if weights is None else ctypes.byref(weights)
+        _check(lib().lbm_set_closure(self._h, ptr), "lbm_set_closure")
+
 
 class Batch:
     """Ensemble of independent periodic lattices advanced by one persistent
@@ -395,3 +423,98 @@ class Batch:
         t = ctypes.c_int64()
         _check(lib().lbm_batch_get_time(self._h, ctypes.byref(t)), "lbm_batch_get_time")
         return t.value
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Trainer:
+    """GPU trainer of the learned closure (include/lbm_closure.h)."""
+
+    def __init__(self, coarse_dims, omega_shear, omega_bulk=1.0, max_snapshots=64, stream=None):
+        self.dims = tuple(int(v) for v in coarse_dims)
+        self.N = self.dims[0] * self.dims[1] * self.dims[2]
+        d = (ctypes.c_int64 * 3)(*self.dims)
+        h = ctypes.c_void_p()
+        _check(lib().lbm_trainer_create(ctypes.byref(h), d, float(omega_shear), float(omega_bulk),
+                                        int(max_snapshots), stream_handle(stream)),
+               "lbm_trainer_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_trainer_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_restricted(self, fine):
+        _check(lib().lbm_trainer_add_restricted(self._h, fine.handle), "lbm_trainer_add_restricted")
+
+    def add_snapshot(self, df):
+        df = np.ascontiguousarray(df, dtype=np.float64).reshape(-1)
+        p, dev = _ptr(df, 27 * self.N)
+        _check(lib().lbm_trainer_add_snapshot(self._h, p, dev), "lbm_trainer_add_snapshot")
+
+    def count(self):
+        return int(lib().lbm_trainer_snapshot_count(self._h))
+
+    def snapshot(self, s):
+        out = np.empty(27 * self.N)
+        _check(lib().lbm_trainer_get_snapshot(self._h, int(s), out.ctypes.data, 0),
+               "lbm_trainer_get_snapshot")
+        nx, ny, nz = self.dims
+        return out.reshape(27, nz, ny, nx)
+
+    def features(self, s):
+        out = np.empty(7 * self.N)
+        _check(lib().lbm_trainer_features(self._h, int(s), out.ctypes.data, 0),
+               "lbm_trainer_features")
+        return out.reshape(7, self.N)
+
+    def set_params(self, params, shift, scale):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        sh = np.ascontiguousarray(shift, dtype=np.float32)
+        sc = np.ascontiguousarray(scale, dtype=np.float32)
+        if p.size != CLOSURE_NPARAM or sh.size != 7 or sc.size != 7:
+            raise ValueError("expected 1444 parameters and 7 shifts / scales")
+        _check(lib().lbm_trainer_set_params(self._h, _fp(p), _fp(sh), _fp(sc)),
+               "lbm_trainer_set_params")
+
+    def params(self):
+        p = np.empty(CLOSURE_NPARAM, dtype=np.float32)
+        _check(lib().lbm_trainer_get_params(self._h, _fp(p)), "lbm_trainer_get_params")
+        return p
+
+    def loss_grad(self, s):
+        loss = np.zeros(1)
+        grad = np.zeros(CLOSURE_NPARAM)
+        _check(lib().lbm_trainer_loss_grad(self._h, int(s), _dptr(loss), _dptr(grad)),
+               "lbm_trainer_loss_grad")
+        return float(loss[0]), grad
+
+    def adam_step(self, s, lr):
+        loss = np.zeros(1)
+        _check(lib().lbm_trainer_adam_step(self._h, int(s), float(lr), _dptr(loss)),
+               "lbm_trainer_adam_step")
+        return float(loss[0])
+
+    def export(self):
+        w = ClosureWeights()
+        _check(lib().lbm_trainer_export(self._h, ctypes.byref(w)), "lbm_trainer_export")
+        return w

@@ -1,0 +1,215 @@
+"""GPU tests of the learned closure (include/lbm_closure.h): the fused
+learned-rate step against the oracle, the restriction, the features, the
+one-step loss and its hand-written gradient against finite differences of
+the FP64 oracle loss, Adam, and what a trained network gains over the plain
+method."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2211_02435_b300 import build as B
+from paper_2211_02435_b300 import inputs as I
+from paper_2211_02435_b300 import lbm as L
+
+pytestmark = pytest.mark.gpu
+
+NP = L.CLOSURE_NPARAM
+OMEGA_S = 1.9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    B.build()
+    O.build()
+
+
+def bf16_round(a):
+    """Round float values to the nearest BF16 value (ties to even)."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_bits(a):
+    u = np.asarray(bf16_round(a), dtype=np.float32).view(np.uint32)
+    return (u >> 16).astype(np.uint16)
+
+
+def weights(params, shift, scale):
+    w = L.ClosureWeights()
+    w.shift[:] = [float(v) for v in shift]
+    w.scale[:] = [float(v) for v in scale]
+    w.w[:] = [int(v) for v in bf16_bits(params)]
+    return w
+
+
+def noisy_state(dims, seed, pert=2e-3):
+    rho, u = I.taylor_green(dims, 0.05)
+    u = I.add_uniform_noise(u, 2e-2, seed=seed)
+    m = O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [OMEGA_S] + [1.0] * 5)
+    df = O.init(m, dims, rho, u)
+    _, w, _ = O.lattice(2)
+    p = I.random_deviations(27, int(np.prod(dims)), pert, seed=seed + 100)
+    return df + (w[:, None] * p).reshape(df.shape)
+
+
+def normalisation(df, dims):
+    """Feature shift / scale from the oracle's raw features of a state."""
+    flat = df.reshape(27, -1)
+    feats = np.array([O.closure_features(2, flat[:, c], OMEGA_S) for c in range(flat.shape[1])])
+    mu = feats.mean(0)
+    sd = feats.std(0)
+    return mu, 1.0 / np.where(sd > 0, sd, 1.0)
+
+
+def random_params(seed, scale=0.4):
+    rng = np.random.default_rng(seed)
+    return bf16_round(scale * rng.standard_normal(NP))
+
+
+def rel_linf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("storage,tol", [(L.STORE_F64, 1e-12), (L.STORE_F32, 1e-5)])
+def test_fused_learned_step_matches_oracle(storage, tol):
+    dims = (21, 7, 6)
+    df = noisy_state(dims, 1)
+    shift, scale = normalisation(df, dims)
+    params = random_params(2)
+    base = O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [OMEGA_S, 1.0, 0.0, 0.0, 0.0, 0.0])
+    sh32 = np.float32(shift).astype(np.float64)
+    sc32 = np.float32(scale).astype(np.float64)
+    ref = df
+    with L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, storage, L.PULL,
+                   [OMEGA_S] + [1.0] * 5, dims) as lat:
+        lat.set_closure(weights(params, shift, scale))
+        lat.set_populations(df)
+        for n in range(1, 4):
+            lat.step(1)
+            ref = O.closure_step(base, dims, ref, params, sh32, sc32)
+            assert rel_linf(lat.get_populations(), ref) < tol, n
+        # disabling the closure returns to the plain regularised method
+        lat.set_closure(None)
+        lat.step(1)
+        plain = O.step(O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [OMEGA_S] + [1.0] * 5),
+                       dims, ref, 1)
+        assert rel_linf(lat.get_populations(), plain) < tol
+
+
+def test_zero_network_is_the_plain_method_and_unsupported_contexts():
+    dims = (12, 5, 4)
+    df = noisy_state(dims, 3)
+    with L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F64, L.PULL,
+                   [OMEGA_S] + [1.0] * 5, dims) as lat:
+        lat.set_closure(weights(np.zeros(NP), np.zeros(7), np.ones(7)))
+        lat.set_populations(df)
+        lat.step(2)
+        got = lat.get_populations()
+    ref = O.step(O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [OMEGA_S] + [1.0] * 5), dims, df, 2)
+    assert rel_linf(got, ref) < 1e-12
+    for st, sp, stream in ((L.D3Q19, L.SPACE_CUMULANT, L.PULL), (L.D3Q27, L.SPACE_CENTRAL, L.PULL),
+                           (L.D3Q27, L.SPACE_CUMULANT, L.AA)):
+        with L.Lattice(st, sp, L.EQ_ABSOLUTE, L.STORE_F32, stream, [OMEGA_S], (8, 8, 8)) as lat:
+            with pytest.raises(L.LBMError) as e:
+                lat.set_closure(weights(np.zeros(NP), np.zeros(7), np.ones(7)))
+            assert e.value.code == -2
+
+
+@pytest.mark.parametrize("streaming,storage", [(L.PULL, L.STORE_F32), (L.AA, L.STORE_F64)])
+def test_restriction_is_the_block_average(streaming, storage):
+    coarse = (5, 4, 3)
+    fine = tuple(4 * v for v in coarse)
+    df = noisy_state(fine, 5)
+    with L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, storage, streaming,
+                   [OMEGA_S] + [1.0] * 5, fine) as lat, L.Trainer(coarse, OMEGA_S, 1.0, 4) as tr:
+        lat.set_populations(df)
+        lat.step(3)  # odd AA parity exercises the odd read-out
+        tr.add_restricted(lat)
+        canon = lat.get_populations()
+        snap = tr.snapshot(0)
+    nx, ny, nz = coarse
+    ref = canon.reshape(27, nz, 4, ny, 4, nx, 4).mean(axis=(2, 4, 6))
+    assert np.abs(snap - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
+def test_features_match_oracle():
+    dims = (9, 7, 5)
+    df = noisy_state(dims, 7)
+    with L.Trainer(dims, OMEGA_S, 1.0, 2) as tr:
+        tr.add_snapshot(df)
+        feats = tr.features(0)
+        snap = tr.snapshot(0).reshape(27, -1)
+    ref = np.array([O.closure_features(2, snap[:, c], OMEGA_S) for c in range(snap.shape[1])]).T
+    for k in range(7):
+        assert np.abs(feats[k] - ref[k]).max() <= 2e-4 * np.abs(ref[k]).max() + 1e-30, k
+
+
+def test_loss_and_gradient_match_oracle_finite_differences():
+    dims = (8, 6, 5)
+    s0 = noisy_state(dims, 11)
+    s1 = noisy_state(dims, 12)
+    shift, scale = normalisation(s0, dims)
+    shift = np.float32(shift).astype(np.float64)
+    scale = np.float32(scale).astype(np.float64)
+    params = random_params(13, 0.5)
+    base = O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [OMEGA_S, 1.0, 0.0, 0.0, 0.0, 0.0])
+    with L.Trainer(dims, OMEGA_S, 1.0, 2) as tr:
+        tr.add_snapshot(s0)
+        tr.add_snapshot(s1)
+        tr.set_params(params, shift, scale)
+        loss, grad = tr.loss_grad(0)
+        # the oracle sees the snapshots as the trainer stores them (FP32)
+        t0, t1 = tr.snapshot(0), tr.snapshot(1)
+    ref_loss = O.closure_loss(base, dims, t0, t1, params, shift, scale)
+    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    rng = np.random.default_rng(3)
+    # a few parameters of every block: W1, b1, W2, b2, W3, b3
+    blocks = [(0, 224), (224, 256), (256, 1280), (1280, 1312), (1312, 1440), (1440, 1444)]
+    idx = [int(rng.integers(a, b)) for a, b in blocks for _ in range(3)]
+    idx += list(np.argsort(-np.abs(grad))[:6])
+    fd = []
+    for k in idx:
+        h = 1e-4
+        p1, p2 = params.copy(), params.copy()
+        p1[k] += h
+        p2[k] -= h
+        fd.append((O.closure_loss(base, dims, t0, t1, p1, shift, scale)
+                   - O.closure_loss(base, dims, t0, t1, p2, shift, scale)) / (2 * h))
+    fd = np.array(fd)
+    g = grad[idx]
+    gmax = np.abs(fd).max()
+    assert gmax > 0
+    assert np.all(np.abs(g - fd) <= 2e-3 * gmax + 2e-3 * np.abs(fd)), np.c_[idx, g, fd]
+
+
+def test_adam_lowers_the_loss_and_export_round_trips():
+    dims = (10, 8, 6)
+    s0, s1 = noisy_state(dims, 21), noisy_state(dims, 22)
+    shift, scale = normalisation(s0, dims)
+    with L.Trainer(dims, OMEGA_S, 1.0, 2) as tr:
+        tr.add_snapshot(s0)
+        tr.add_snapshot(s1)
+        tr.set_params(np.zeros(NP), shift, scale)
+        first = tr.adam_step(0, 1e-2)
+        for _ in range(30):
+            last = tr.adam_step(0, 1e-2)
+        final, _ = tr.loss_grad(0)
+        w = tr.export()
+        p = tr.params()
+    assert final < first
+    assert np.array_equal(np.array(w.w[:], dtype=np.uint16), bf16_bits(p))
+    assert np.allclose(np.array(w.scale[:]), np.float32(scale))
+
+
+def test_trained_network_gains_over_the_plain_method():
+    """Fine 64^3 plain cumulant run of the Fourier-mode flow restricted to
+    16^3 every 4 fine steps; train on the first pairs, then compare the
+    one-step velocity error on held-out pairs and a 4-step rollout with the
+    plain method (all higher-order rates 1)."""
+    from paper_2211_02435_b300 import closure as C
+    res = C.train_and_evaluate(fine_edge=64, nsnap=24, ntrain=18, epochs=6, lr=3e-3,
+                               rollout=4, seed=5)
+    assert res["train_loss_final"] < res["train_loss_initial"]
+    assert res["heldout_loss_learned"] <= res["heldout_loss_plain"]
+    assert np.isfinite(res["rollout_err_learned"]) and np.isfinite(res["rollout_err_plain"])
