@@ -71,11 +71,26 @@ def rel_linf(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
-@pytest.mark.parametrize("storage,tol", [(L.STORE_F64, 1e-12), (L.STORE_F32, 1e-5)])
-def test_fused_learned_step_matches_oracle(storage, tol):
+# Input scales that make every normalised input O(1) for this flow without
+# amplifying rounding: the raw features are ~1e-2 (tr S), 1e-5 (I2 S), 1e-8
+# (det S), 1e-6 (I2 D), 1e-9 (det D), 1e-3 (|Pi|), 1e-3 (drho).
+FIXED_SCALE = np.array([1e2, 1e4, 1e6, 1e5, 1e7, 1e2, 1e2])
+
+
+@pytest.mark.parametrize("norm,storage,tol", [
+    ("fixed", L.STORE_F64, 1e-12), ("fixed", L.STORE_F32, 1e-5),
+    # Data-derived scales reach 1e11 (1/std of det D): the oracle's features
+    # come from absolute second moments (kappa ~ 1/3) whose FP64 rounding,
+    # ~1e-16 absolute, the scale turns into rate differences of ~1e-10 and
+    # f* differences of ~1e-11 relative; hence 1e-9 for FP64 in that case.
+    ("data", L.STORE_F64, 1e-9), ("data", L.STORE_F32, 1e-5)])
+def test_fused_learned_step_matches_oracle(norm, storage, tol):
     dims = (21, 7, 6)
     df = noisy_state(dims, 1)
-    shift, scale = normalisation(df, dims)
+    if norm == "fixed":
+        shift, scale = np.zeros(7), FIXED_SCALE
+    else:
+        shift, scale = normalisation(df, dims)
     params = random_params(2)
     base = O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [OMEGA_S, 1.0, 0.0, 0.0, 0.0, 0.0])
     sh32 = np.float32(shift).astype(np.float64)
@@ -85,16 +100,23 @@ def test_fused_learned_step_matches_oracle(storage, tol):
                    [OMEGA_S] + [1.0] * 5, dims) as lat:
         lat.set_closure(weights(params, shift, scale))
         lat.set_populations(df)
+        prev = df
         for n in range(1, 4):
             lat.step(1)
+            got = lat.get_populations()
+            # one step from the GPU's own previous state, and the full run
+            one = O.closure_step(base, dims, prev, params, sh32, sc32)
+            assert rel_linf(got, one) < tol, n
             ref = O.closure_step(base, dims, ref, params, sh32, sc32)
-            assert rel_linf(lat.get_populations(), ref) < tol, n
+            if norm == "fixed":  # with 1e11 scales the multi-step run is ill-conditioned
+                assert rel_linf(got, ref) < tol, n
+            prev = got
         # disabling the closure returns to the plain regularised method
         lat.set_closure(None)
         lat.step(1)
         plain = O.step(O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [OMEGA_S] + [1.0] * 5),
-                       dims, ref, 1)
-        assert rel_linf(lat.get_populations(), plain) < tol
+                       dims, prev, 1)
+        assert rel_linf(lat.get_populations(), plain) < min(tol, 1e-12 if storage == L.STORE_F64 else 1e-5)
 
 
 def test_zero_network_is_the_plain_method_and_unsupported_contexts():
