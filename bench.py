@@ -99,6 +99,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (x itself without a process
+    group): the slowest rank's time defines the whole job's time."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world, cells_per_rank, steps, seconds):
+    """Whole-job throughput of `world` independent replicas."""
+    return world * cells_per_rank * steps / seconds / 1e6
+
+
 def kernel_traffic_per_cell():
     """DRAM bytes per cell update of the FP32 step kernel from the committed
     ncu summary, or None when the kernel sources changed since the capture."""
@@ -221,6 +237,39 @@ def run_batched(args, L, torch, stream, peak):
     return out
 
 
+def run_learned(args, L, torch, stream):
+    """Learned closure: fine 512^3 plain cumulant run (nu = 2e-4, seeded
+    Fourier-mode flow) restricted to 128^3 every 4 steps, GPU training of
+    the rate network, held-out one-step and rollout errors against the plain
+    method, and the fused learned-rate kernel's MLUPS against the plain
+    kernel's at 128^3."""
+    from paper_2211_02435_b300 import closure as C
+    res = C.train_and_evaluate(fine_edge=args.learned_fine, nsnap=160, ntrain=128, epochs=8,
+                               lr=3e-3, rollout=31, nu_fine=2e-4, seed=5, stream=stream)
+    w = res.pop("weights")
+    n = args.learned_fine // 4
+    omega_c = I.shear_viscosity_rate(2e-4 / 4)
+    rho, u = I.fourier_modes((n, n, n), seed=5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rates = {}
+    for name, weights in (("plain", None), ("learned", w)):
+        with L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F32, L.PULL,
+                       [omega_c] + [1.0] * 5, (n, n, n), stream=stream) as lat:
+            if weights is not None:
+                lat.set_closure(weights)
+            lat.init_velocity(rho.reshape(-1), u.reshape(-1))
+            lat.step(args.warmup)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            lat.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rates[name] = n ** 3 * args.steps / (e0.elapsed_time(e1) / 1e3) / 1e6
+    res["mlups_128_plain_kernel"] = rates["plain"]
+    res["mlups_128_learned_kernel"] = rates["learned"]
+    return res
+
+
 def run_cuda(args):
     import torch
     from paper_2211_02435_b300 import build as B
@@ -271,13 +320,9 @@ def run_cuda(args):
     with ClockSampler(local) as clk:
         lat32, ms32 = time_form(L.STORE_F32, args.steps, args.warmup)
     clocks = clk.summary()
-    ms_max = ms32
-    if dist:
-        t = torch.tensor([ms32], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms32, dist, "cuda")
     per_step_s = ms_max / 1e3 / args.steps
-    value = world * N * args.steps / (ms_max / 1e3) / 1e6
+    value = job_mlups(world, N, args.steps, ms_max / 1e3)
     achieved = BYTES_PER_CELL["f32"] * N / (ms32 / 1e3 / args.steps) / 1e9
     u32 = torch.empty(3 * N, dtype=torch.float64, device="cuda")
     lat32.macroscopic(None, u32)
@@ -336,13 +381,9 @@ def run_cuda(args):
         lat.step(args.steps)
         lat.macroscopic(rho_out.numpy(), u_out.numpy())
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         lat.close()
-        e2e = {"value": world * N * args.steps / dt / 1e6, "unit": UNIT,
+        e2e = {"value": job_mlups(world, N, args.steps, dt), "unit": UNIT,
                "h2d_bytes_per_step": 4 * N * 8 / args.steps,
                "d2h_bytes_per_step": 4 * N * 8 / args.steps,
                "job": f"host rho,u (FP64, pinned) -> init -> {args.steps} steps -> host rho,u"}
@@ -352,6 +393,11 @@ def run_cuda(args):
         del rho_d, u_d
         torch.cuda.empty_cache()
         batched = run_batched(args, L, torch, stream, peak)
+
+    learned = None
+    if not args.no_learned:
+        torch.cuda.empty_cache()
+        learned = run_learned(args, L, torch, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -379,7 +425,7 @@ def run_cuda(args):
                          "peak_kind": peak_kind,
                          "bytes_per_cell": BYTES_PER_CELL["f32"],
                          "kernel": "k_pull<D3Q27, float, cumulant, regularised>"},
-            "forms": forms, "batched": batched, "clocks": clocks, "e2e": e2e,
+            "forms": forms, "batched": batched, "learned": learned, "clocks": clocks, "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": args.steps}
     if rank == 0:
@@ -403,6 +449,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-fine", type=int, default=512)
     ap.add_argument("--batch-n", type=int, default=4096)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "cuda":
