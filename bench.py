@@ -299,8 +299,8 @@ def run_cuda(args):
     u_d = torch.from_numpy(u_h.reshape(-1)).cuda()
     peak, peak_kind = measured_peaks()
 
-    def time_form(storage, steps, warmup):
-        lat = L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, storage, L.PULL, rates,
+    def time_form(storage, steps, warmup, streaming=L.PULL):
+        lat = L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, storage, streaming, rates,
                         (n, n, n), stream=stream)
         lat.init_velocity(rho_d, u_d)
         lat.step(warmup)
@@ -316,14 +316,16 @@ def run_cuda(args):
         ms = e0.elapsed_time(e1)
         return lat, ms
 
-    # ---- headline: FP32 storage, kernel-only (inputs resident in HBM)
+    # ---- headline: FP32 storage (or --storage), kernel-only, inputs in HBM
+    main_store = {"f32": L.STORE_F32, "f16": L.STORE_F16_DELTA, "bf16": L.STORE_BF16_DELTA}[args.storage]
+    main_key = {"f32": "f32", "f16": "f16_delta", "bf16": "bf16_delta"}[args.storage]
     with ClockSampler(local) as clk:
-        lat32, ms32 = time_form(L.STORE_F32, args.steps, args.warmup)
+        lat32, ms32 = time_form(main_store, args.steps, args.warmup)
     clocks = clk.summary()
     ms_max = max_over_ranks(ms32, dist, "cuda")
     per_step_s = ms_max / 1e3 / args.steps
     value = job_mlups(world, N, args.steps, ms_max / 1e3)
-    achieved = BYTES_PER_CELL["f32"] * N / (ms32 / 1e3 / args.steps) / 1e9
+    achieved = BYTES_PER_CELL[main_key] * N / (ms32 / 1e3 / args.steps) / 1e9
     u32 = torch.empty(3 * N, dtype=torch.float64, device="cuda")
     lat32.macroscopic(None, u32)
     lat32.close()
@@ -359,6 +361,20 @@ def run_cuda(args):
                            "u_rel_linf_vs_f64": uerr(uu),
                            "vs_f32_mlups": (N * args.steps / (ms / 1e3)) / (N * args.steps / (ms32 / 1e3))}
             del uu
+        # in-place AA pattern (one buffer), FP32, even number of steps
+        lat, ms = time_form(L.STORE_F32, 2 * (args.steps // 2), args.warmup + args.warmup % 2,
+                            streaming=L.AA)
+        uu = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+        lat.macroscopic(None, uu)
+        lat.close()
+        del lat
+        st_aa = 2 * (args.steps // 2)
+        ach = BYTES_PER_CELL["f32"] * N / (ms / 1e3 / st_aa) / 1e9
+        forms["f32_aa"] = {"mlups": N * st_aa / (ms / 1e3) / 1e6, "achieved_gbs": ach,
+                           "roofline_frac": ach / peak, "buffers": 1,
+                           "u_rel_linf_vs_f64": uerr(uu) if st_aa + args.warmup + args.warmup % 2
+                           == args.steps + args.warmup else None}
+        del uu
         del u64
     del u32
 
@@ -407,24 +423,25 @@ def run_cuda(args):
                "sample": f"{edge}^3 cells x {args.cpu_steps} steps of the same method and flow "
                          f"({dt:.1f} s, OpenMP over all cores)"}
 
-    traffic = kernel_traffic_per_cell()
+    traffic = kernel_traffic_per_cell() if args.storage == "f32" else None
     if traffic is not None:
         traffic *= N
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_s * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.storage == "f32" else f"f32 compute, {args.storage} storage",
             "data": "synthetic",
             "config": {"workload": "D3Q27 cumulant LBM (R-: shear from nu=1e-3, bulk and "
                                    "orders 3-6 rate 1), periodic 512^3 Taylor-Green u0=0.05 "
-                                   "+ uniform 1e-3 noise, FP32 zero-centered storage, pull",
+                                   f"+ uniform 1e-3 noise, {main_key} zero-centered storage, pull",
                        "cells": N, "global_batch": world, "parallelism": "replicas",
                        "l2": "working set 29 GB >> 126 MB L2, no flush needed"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
-                         "bytes_per_cell": BYTES_PER_CELL["f32"],
-                         "kernel": "k_pull<D3Q27, float, cumulant, regularised>"},
+                         "bytes_per_cell": BYTES_PER_CELL[main_key],
+                         "kernel": f"k_pull<D3Q27, {main_key} storage, cumulant, regularised>"},
             "forms": forms, "batched": batched, "learned": learned, "clocks": clocks, "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": args.steps}
@@ -449,6 +466,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
+                    help="storage of the headline form (default FP32)")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-fine", type=int, default=512)
     ap.add_argument("--batch-n", type=int, default=4096)

@@ -139,15 +139,32 @@ LBM_D void fwd_raw_chimera(const T (&f)[q_of(ST)], T (&A)[3][3][3]) {
   });
 }
 
-// raw monomial moment deviations -> zero-centered populations
-template <int ST, class T>
+// inverse pass without the 1/2: (m0, m1, m2) -> (2 f(-1), f(0), 2 f(+1))
+template <class T>
+LBM_D void bwd3_x2(T& v0, T& v1, T& v2) {
+  const T f0 = v0 - v2;
+  const T fm = v2 - v1;
+  v2 = v2 + v1;
+  v0 = fm;
+  v1 = f0;
+}
+
+// raw monomial moment deviations -> zero-centered populations.  DEFER
+// leaves out the exact power-of-two factors of the split: population i is
+// then returned multiplied by 2^(|xi_i|^2), for callers that rescale anyway.
+template <int ST, class T, bool DEFER = false>
 LBM_D void bwd_raw(T (&A)[3][3][3], T (&f)[q_of(ST)]) {
   if constexpr (ST == D3Q19) {
     // D3Q19 is no tensor product: solve M f = m in closed form, plane by
     // plane, with the symmetric / antisymmetric split of Eq. 4.2
-    const T q4 = T(0.25);
+    const T q4 = T(DEFER ? 1.0 : 0.25);
     auto edge = [&](T m22, T m21, T m12, T m11, T& fpp, T& fpm, T& fmp, T& fmm) {
-      const T s = q4 * m22, a2 = q4 * m21, a1 = q4 * m12, c = q4 * m11;
+      T s, a2, a1, c;
+      if constexpr (DEFER) {
+        s = m22, a2 = m21, a1 = m12, c = m11;
+      } else {
+        s = q4 * m22, a2 = q4 * m21, a1 = q4 * m12, c = q4 * m11;
+      }
       const T sp = s + a1, sm = s - a1;  // first axis +1 / -1
       fpp = sp + a2 + c;
       fpm = sp - a2 - c;
@@ -161,33 +178,47 @@ LBM_D void bwd_raw(T (&A)[3][3][3], T (&f)[q_of(ST)]) {
     // yz edges: 15 (0,1,1) 16 (0,-1,-1) 17 (0,1,-1) 18 (0,-1,1)
     edge(A[0][2][2], A[0][2][1], A[0][1][2], A[0][1][1], f[15], f[17], f[18], f[16]);
     const T h = T(0.5);
+    (void)h;
     const T sx = A[2][0][0] - A[2][2][0] - A[2][0][2];
     const T ax = A[1][0][0] - A[1][2][0] - A[1][0][2];
     const T sy = A[0][2][0] - A[2][2][0] - A[0][2][2];
     const T ay = A[0][1][0] - A[2][1][0] - A[0][1][2];
     const T sz = A[0][0][2] - A[2][0][2] - A[0][2][2];
     const T az = A[0][0][1] - A[2][0][1] - A[0][2][1];
-    f[1] = h * (sx + ax);
-    f[2] = h * (sx - ax);
-    f[3] = h * (sy + ay);
-    f[4] = h * (sy - ay);
-    f[5] = h * (sz + az);
-    f[6] = h * (sz - az);
+    if constexpr (DEFER) {
+      f[1] = sx + ax;
+      f[2] = sx - ax;
+      f[3] = sy + ay;
+      f[4] = sy - ay;
+      f[5] = sz + az;
+      f[6] = sz - az;
+    } else {
+      f[1] = h * (sx + ax);
+      f[2] = h * (sx - ax);
+      f[3] = h * (sy + ay);
+      f[4] = h * (sy - ay);
+      f[5] = h * (sz + az);
+      f[6] = h * (sz - az);
+    }
     f[0] = A[0][0][0] - (A[2][0][0] + A[0][2][0] + A[0][0][2]) +
            (A[2][2][0] + A[2][0][2] + A[0][2][2]);
   } else {
+    auto pass = [](T& v0, T& v1, T& v2) {
+      if constexpr (DEFER) bwd3_x2(v0, v1, v2);
+      else bwd3(v0, v1, v2);
+    };
     sfor<9>([&](auto K) {
       constexpr int b = CI(K) / 3, c = CI(K) % 3;
-      if constexpr (dim_of(ST) == 3 || c == 0) bwd3(A[0][b][c], A[1][b][c], A[2][b][c]);
+      if constexpr (dim_of(ST) == 3 || c == 0) pass(A[0][b][c], A[1][b][c], A[2][b][c]);
     });
     sfor<9>([&](auto K) {
       constexpr int x = CI(K) / 3, c = CI(K) % 3;
-      if constexpr (dim_of(ST) == 3 || c == 0) bwd3(A[x][0][c], A[x][1][c], A[x][2][c]);
+      if constexpr (dim_of(ST) == 3 || c == 0) pass(A[x][0][c], A[x][1][c], A[x][2][c]);
     });
     if constexpr (dim_of(ST) == 3) {
       sfor<9>([&](auto K) {
         constexpr int x = CI(K) / 3, y = CI(K) % 3;
-        bwd3(A[x][y][0], A[x][y][1], A[x][y][2]);
+        pass(A[x][y][0], A[x][y][1], A[x][y][2]);
       });
     }
     sfor<q_of(ST)>([&](auto I) {
@@ -434,7 +465,7 @@ LBM_D void cumulant_bwd(const T (&C)[3][3][3], T (&K)[3][3][3]) {
 // ------------------------------------------------------------ collision
 // In: zero-centered pre-collision populations f.  Out: zero-centered
 // post-collision populations f*.  keep.om[g] = 1 - omega_g.
-template <int ST, class T, int SPACE, bool REG>
+template <int ST, class T, int SPACE, bool REG, bool DEFER = false>
 LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep) {
   T A[3][3][3];
   fwd_raw_chimera<ST, T>(f, A);
@@ -547,7 +578,7 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep) {
   A[1][0][0] = j[0];
   A[0][1][0] = j[1];
   if constexpr (dim_of(ST) == 3) A[0][0][1] = j[2];
-  bwd_raw<ST, T>(A, f);
+  bwd_raw<ST, T, DEFER>(A, f);
 }
 
 // The method's equilibrium as zero-centered populations (the collision's

@@ -12,6 +12,7 @@
 
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
+#include "lbm_packed.cuh"
 
 namespace lbm {
 
@@ -64,21 +65,82 @@ LBM_D void load_pops(const S* buf, const Geo& g, const Nbr& n, int c, T (&f)[q_o
 }
 
 // ------------------------------------------------------------ step kernels
+// Per-direction plane pointers of the pull kernel.  src[i] points at plane i
+// of the source buffer already shifted by the interior stencil offset
+// -(xi_z*Ny*Nx + xi_y*Nx + xi_x), so the gather of cell c reads
+// src[i][c + wrap_i] with wrap_i nonzero only on the periodic boundary:
+// one integer add and one wide address computation per load.
+template <class S>
+struct PullPtrs {
+  const S* src[27];
+  S* dst[27];
+};
+
 // pull: read f_i from x - xi_i of src, collide, write f*_i at x of dst
 template <int ST, class S, class T, int SPACE, bool REG>
-__global__ void __launch_bounds__(LBM_BX) k_pull(const S* __restrict__ src, S* __restrict__ dst,
-                                                 Geo g, Rates<T> keep) {
+__global__ void __launch_bounds__(LBM_BX) k_pull(const __grid_constant__ PullPtrs<S> P, Geo g,
+                                                 Rates<T> keep) {
   const int x = blockIdx.x * LBM_BX + threadIdx.x;
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
-  const Nbr n = neighbours(x, y, z, g);
   const int c = (z * g.ny + y) * g.nx + x;
+  const int nxy = g.nx * g.ny;
+  // wrap corrections for a read at x - xi (xi = +1 reads x-1, -1 reads x+1)
+  const int wxp = x == 0 ? g.nx : 0, wxm = x == g.nx - 1 ? -g.nx : 0;
+  const int wyp = y == 0 ? nxy : 0, wym = y == g.ny - 1 ? -nxy : 0;
+  const int wzp = z == 0 ? int(g.N) : 0, wzm = z == g.nz - 1 ? -int(g.N) : 0;
   T f[q_of(ST)];
-  load_pops<ST, S, T, G_PULL>(src, g, n, c, f);
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1), cz = vel(ST, i, 2);
+    const int wyz = (cy > 0 ? wyp : (cy < 0 ? wym : 0)) + (cz > 0 ? wzp : (cz < 0 ? wzm : 0));
+    const int wx = cx > 0 ? wxp : (cx < 0 ? wxm : 0);
+    const S v = P.src[i][c + wx + wyz];
+    f[i] = Codec<S>::template dec<T>(v, scale_exp(ST, i));
+  });
   collide<ST, T, SPACE, REG>(f, keep);
   sfor<q_of(ST)>([&](auto I) {
     constexpr int i = CI(I);
-    dst[(int64_t)i * g.N + c] = Codec<S>::template enc<T>(f[i], scale_exp(ST, i));
+    P.dst[i][c] = Codec<S>::template enc<T>(f[i], scale_exp(ST, i));
+  });
+}
+
+// Two cells per thread (x even, x + 1) with the collision on packed FP32
+// pairs, for FP16 / BF16 delta storage and even Nx.  Directions with
+// xi_x = 0 read both cells with one aligned 2-element load; the others read
+// the two cells separately (their x wrap differs at the row ends).  Stores
+// are aligned 2-element stores.
+template <int ST, class S, int SPACE, bool REG>
+__global__ void __launch_bounds__(LBM_BX) k_pull2(const __grid_constant__ PullPtrs<S> P, Geo g,
+                                                  Rates<P2> keep) {
+  const int x = 2 * (blockIdx.x * LBM_BX + threadIdx.x);
+  if (x >= g.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int c = (z * g.ny + y) * g.nx + x;
+  const int nxy = g.nx * g.ny;
+  const int wxp0 = x == 0 ? g.nx : 0;           // cell x reading x - 1
+  const int wxm1 = x + 2 == g.nx ? -g.nx : 0;   // cell x + 1 reading x + 2
+  const int wyp = y == 0 ? nxy : 0, wym = y == g.ny - 1 ? -nxy : 0;
+  const int wzp = z == 0 ? int(g.N) : 0, wzm = z == g.nz - 1 ? -int(g.N) : 0;
+  P2 f[q_of(ST)];
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1), cz = vel(ST, i, 2);
+    const int off = c + (cy > 0 ? wyp : (cy < 0 ? wym : 0)) + (cz > 0 ? wzp : (cz < 0 ? wzm : 0));
+    P2 v;
+    if constexpr (cx == 0) v = Pack<S>::load2(P.src[i] + off);
+    else if constexpr (cx > 0) v = Pack<S>::load11(P.src[i] + off + wxp0, P.src[i] + off + 1);
+    else v = Pack<S>::load11(P.src[i] + off, P.src[i] + off + 1 + wxm1);
+    f[i] = v * P2(1.0f / float(1u << scale_exp(ST, i)));
+  });
+  // the backward transform leaves population i multiplied by 2^|xi_i|^2;
+  // the storage scale 2^s_i absorbs it exactly
+  collide<ST, P2, SPACE, REG, true>(f, keep);
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    constexpr int k = vel(ST, i, 0) * vel(ST, i, 0) + vel(ST, i, 1) * vel(ST, i, 1) +
+                      vel(ST, i, 2) * vel(ST, i, 2);
+    Pack<S>::store2(P.dst[i] + c, f[i] * P2(float(1u << (scale_exp(ST, i) - k))));
   });
 }
 
@@ -310,9 +372,27 @@ void launch_step_typed(const StepArgs& a) {
   Rates<T> keep;
   for (int k = 0; k < 6; ++k) keep.om[k] = T(1.0 - a.rates[k]);
   const dim3 grid = step_grid(a.g);
-  if (a.mode == MODE_PULL)
-    k_pull<ST, S, T, SPACE, REG><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.src, (S*)a.dst, a.g,
-                                                                   keep);
+  if (a.mode == MODE_PULL) {
+    PullPtrs<S> P;
+    const int64_t nx = a.g.nx, nxy = int64_t(a.g.nx) * a.g.ny;
+    for (int i = 0; i < q_of(ST); ++i) {
+      const int64_t delta = -(vel(ST, i, 2) * nxy + vel(ST, i, 1) * nx + vel(ST, i, 0));
+      P.src[i] = (const S*)a.src + (int64_t(i) * a.g.N + delta);
+      P.dst[i] = (S*)a.dst + int64_t(i) * a.g.N;
+    }
+    for (int i = q_of(ST); i < 27; ++i) P.src[i] = nullptr, P.dst[i] = nullptr;
+    constexpr bool half = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
+    if constexpr (half) {
+      if (a.g.nx % 2 == 0) {
+        Rates<P2> k2;
+        for (int k = 0; k < 6; ++k) k2.om[k] = P2(1.0 - a.rates[k]);
+        const dim3 grid2((a.g.nx / 2 + LBM_BX - 1) / LBM_BX, a.g.ny, a.g.nz);
+        k_pull2<ST, S, SPACE, REG><<<grid2, LBM_BX, 0, a.stream>>>(P, a.g, k2);
+        return;
+      }
+    }
+    k_pull<ST, S, T, SPACE, REG><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep);
+  }
   else if (a.mode == MODE_AA_EVEN)
     k_aa<ST, S, T, SPACE, REG, false><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep);
   else

@@ -260,3 +260,32 @@ def test_taylor_green_config_d3q19_omrt_fp64():
             assert rel_linf(lat.get_populations(), ref) < 1e-12
             _, u_g = lat.macroscopic()
             assert rel_linf(u_g, u_r) < 1e-12
+
+
+EVEN_DIMS = {0: (134, 37, 1), 1: (134, 6, 5), 2: (134, 6, 5)}
+
+
+@pytest.mark.parametrize("storage,p", [(L.STORE_F16_DELTA, 10), (L.STORE_BF16_DELTA, 7)])
+@pytest.mark.parametrize("method", METHODS[1:], ids=lambda m: f"sp{m[0]}eq{m[1]}reg{int(m[2])}")
+@pytest.mark.parametrize("st", [0, 1, 2], ids=["D2Q9", "D3Q19", "D3Q27"])
+def test_packed_half_kernel_error_bound(st, method, storage, p):
+    """Even Nx routes FP16 / BF16 pull steps to the two-cells-per-thread
+    kernel with packed FP32 arithmetic; same rounding bound as the scalar
+    kernel (see test_half_storage_error_bound)."""
+    space, eq, reg = method
+    dims = EVEN_DIMS[st]
+    d = 2 if st == 0 else 3
+    rho, u = I.taylor_green(dims, 0.05, d=d)
+    u = I.add_uniform_noise(u, 1e-3, seed=11)
+    m = O.method(st, space, eq, rates_of(space, reg))
+    df0 = O.init(m, dims, rho, u)
+    _, w, _ = O.lattice(st)
+    pert = I.random_deviations(len(w), int(np.prod(dims)), 2e-3, seed=12)
+    df0 = df0 + (w[:, None] * pert).reshape(df0.shape)
+    n = 4
+    with L.Lattice(st, space, eq, storage, L.PULL, rates_of(space, reg), dims) as lat:
+        lat.set_populations(df0)
+        lat.step(n)
+        got = lat.get_populations()
+    ref = O.step(m, dims, df0, n)
+    assert rel_linf(got, ref) < (n + 1) * 2.0 ** -(p + 1)
