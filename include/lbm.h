@@ -26,6 +26,8 @@
  *    legacy default stream).  lbm_step returns without synchronising.
  *  - There is no CPU fallback: without a usable CUDA device every call that
  *    needs one returns LBM_ERR_CUDA.
+ *  - Populations read or written through this interface are always the
+ *    zero-centered df = f - w, also for LBM_STORE_F64_ABSOLUTE.
  *  - Field layout (inputs and outputs): structure of arrays with x fastest,
  *    cell index c = (z*Ny + y)*Nx + x.  Scalars: a[c]; vectors: a[d*N + c]
  *    with d = 0..D-1 (D = 2 for D2Q9, 3 otherwise); populations: a[i*N + c].
@@ -65,8 +67,9 @@ extern "C" {
 /* ---- method specification (Sec. 3, Fig. 2) ---- */
 typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 } lbm_stencil;
 
-/* Collision space (Sec. 2.3).  POPULATIONS is single relaxation time (BGK):
- * it is run as raw-moment MRT with every rate equal to rates[0]. */
+/* Collision space (Sec. 2.3).  POPULATIONS is single relaxation time (BGK)
+ * in population space, f* = f + omega (f_eq - f) with omega = rates[0] and
+ * f_eq = M^-1 m_eq (the raw-moment equilibrium below). */
 typedef enum {
   LBM_SPACE_POPULATIONS = 0,
   LBM_SPACE_RAW = 1,      /* orthogonal raw moments, unweighted (O-MRT)  */
@@ -90,8 +93,21 @@ typedef enum {
   LBM_STORE_F64 = 0,
   LBM_STORE_F32 = 1,
   LBM_STORE_F16_DELTA = 2,
-  LBM_STORE_BF16_DELTA = 3
+  LBM_STORE_BF16_DELTA = 3,
+  LBM_STORE_F64_ABSOLUTE = 4 /* absolute populations f, not df (Sec. 2.1):
+                                collides with Eq. 2.4 in absolute FP64
+                                arithmetic; needs LBM_EQ_ABSOLUTE (Sec. 3);
+                                pull streaming only */
 } lbm_storage;
+
+/* Collision arithmetic.  DEVIATION (default): every moment, central moment
+ * and cumulant is carried as a deviation from the rest state, whichever
+ * equilibrium format is chosen (algebraically Eq. 2.5 / 2.6).  AS_WRITTEN:
+ * the arithmetic the paper writes, for round-off studies (Sec. 5.1):
+ * LBM_EQ_DELTA relaxes deviations against the delta-equilibrium (Eq. 2.5),
+ * LBM_EQ_ABSOLUTE adds f0 back and collides absolute populations (Eq. 2.6).
+ * AS_WRITTEN is served for FP64 storage with pull streaming. */
+typedef enum { LBM_ARITH_DEVIATION = 0, LBM_ARITH_AS_WRITTEN = 1 } lbm_arithmetic;
 
 /* Streaming pattern (Sec. 4.3): pull with two buffers, or the in-place
  * AA pattern with one buffer. */
@@ -124,6 +140,7 @@ typedef struct {
                        65535, Nx*Ny*Nz < 2^31                            */
   int boundary;     /* LBM_PERIODIC                                      */
   void* stream;     /* cudaStream_t for every enqueue; NULL = default     */
+  int arithmetic;   /* lbm_arithmetic (0 = deviations throughout)         */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;

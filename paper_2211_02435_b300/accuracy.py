@@ -8,6 +8,11 @@
   Fourier flow (max |u| = 0.08), FP16 / BF16 delta storage and FP32 storage
   against FP64 storage, velocity and density-deviation errors (relative L-inf
   and L2) at fixed intervals.
+* ``tgv_plateau``: the round-off plateau of the decaying Taylor-Green vortex
+  (Sec. 5.1, Eq. 5.1/5.2, Table 3): D3Q27, L x L x 1 (the flow is
+  z-invariant), u0 = 0.25, nu = 1/6 (every rate 1), FP64; the relative
+  kinetic energy E(t)/E0 of SRT, R-O-MRT, R-CM and R-K in each storage /
+  equilibrium / arithmetic form, against the analytic exp(-4 nu kappa^2 t).
 
 The FP64 GPU runs are tied to the CPU oracle by the parity tests (1e-12 per
 step); these studies measure how the reduced forms drift from them over
@@ -101,11 +106,65 @@ def half_storage(n=512, nu=1e-3, steps=5000, every=1000, seed=3, stream=None):
                       f"(seed {seed}), nu={nu}", "steps": steps, "rows": rows}
 
 
+PLATEAU_METHODS = (("SRT", L.SPACE_POPULATIONS), ("R-O-MRT", L.SPACE_RAW),
+                   ("R-CM", L.SPACE_CENTRAL), ("R-K", L.SPACE_CUMULANT))
+# (name, storage, equilibrium, arithmetic): the three forms of Table 3 and
+# this library's default (absolute equilibrium in deviation arithmetic)
+PLATEAU_FORMS = (
+    ("absolute", L.STORE_F64_ABSOLUTE, L.EQ_ABSOLUTE, L.ARITH_AS_WRITTEN),
+    ("zc_feq", L.STORE_F64, L.EQ_ABSOLUTE, L.ARITH_AS_WRITTEN),
+    ("zc_dfeq", L.STORE_F64, L.EQ_DELTA, L.ARITH_DEVIATION),
+    ("zc_feq_deviation", L.STORE_F64, L.EQ_ABSOLUTE, L.ARITH_DEVIATION),
+)
+
+
+def tgv_plateau(n=256, steps=200_000, every=10_000, u0=0.25, methods=None, forms=None,
+                stream=None):
+    """E(t)/E0 every `every` steps for each admissible (method, form) pair.
+
+    E is the lattice sum of rho |u|^2 / 2 (lbm_invariants, a deterministic
+    FP64 reduction); E0 is its value at t = 0, the equilibrium of Eq. 5.1.
+    With nu = 1/6 the shear rate is 1 and every higher rate is 1 as well,
+    so the raw-moment method is the same in any orthogonal basis (all
+    non-conserved moments are set to equilibrium)."""
+    nu = 1.0 / 6.0
+    kappa = 2 * np.pi / n
+    rho, u = I.taylor_green((n, n, 1), u0)
+    rates = [1.0] * 6
+    methods = methods or [m for m, _ in PLATEAU_METHODS]
+    forms = forms or [f for f, *_ in PLATEAU_FORMS]
+    times = list(range(0, steps + 1, every))
+    if times[-1] != steps:
+        times.append(steps)
+    out = {"config": f"D3Q27 {n}x{n}x1 TGV u0={u0} nu=1/6 (all rates 1), FP64, {steps} steps",
+           "steps": times, "analytic": [float(np.exp(-4 * nu * kappa * kappa * t)) for t in times],
+           "runs": {}, "seconds": {}}
+    for mname, space in PLATEAU_METHODS:
+        if mname not in methods:
+            continue
+        for fname, storage, eq, arith in PLATEAU_FORMS:
+            if fname not in forms or (space == L.SPACE_CUMULANT and eq == L.EQ_DELTA):
+                continue  # no zero-centered cumulants (Sec. 3)
+            t0 = time.perf_counter()
+            with L.Lattice(L.D3Q27, space, eq, storage, L.PULL, rates, (n, n, 1), stream=stream,
+                           arithmetic=arith) as lat:
+                lat.init_velocity(rho.reshape(-1), u.reshape(-1))
+                e0 = lat.invariants()["energy"]
+                series, done = [1.0], 0
+                for t in times[1:]:
+                    lat.step(t - done)
+                    done = t
+                    series.append(lat.invariants()["energy"] / e0)
+            out["runs"][f"{mname}/{fname}"] = series
+            out["seconds"][f"{mname}/{fname}"] = time.perf_counter() - t0
+    return out
+
+
 def main():
     import argparse
     import json
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("study", choices=["fp32_vs_fp64", "half_storage"])
+    ap.add_argument("study", choices=["fp32_vs_fp64", "half_storage", "tgv_plateau"])
     ap.add_argument("--n", type=int)
     ap.add_argument("--steps", type=int)
     ap.add_argument("--every", type=int)
@@ -113,8 +172,11 @@ def main():
     ap.add_argument("--out")
     a = ap.parse_args()
     kw = {k: v for k, v in (("n", a.n), ("steps", a.steps), ("every", a.every)) if v}
-    fn = fp32_vs_fp64 if a.study == "fp32_vs_fp64" else half_storage
-    res = fn(nu=a.nu, **kw)
+    if a.study == "tgv_plateau":
+        res = tgv_plateau(**kw)
+    else:
+        fn = fp32_vs_fp64 if a.study == "fp32_vs_fp64" else half_storage
+        res = fn(nu=a.nu, **kw)
     txt = json.dumps(res, indent=1)
     if a.out:
         with open(a.out, "w") as f:

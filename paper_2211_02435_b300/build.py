@@ -33,7 +33,7 @@ def _deps():
 def _units():
     units = []
     for st in range(3):
-        for so in range(4):
+        for so in range(5):
             units.append((os.path.join(CSRC, "lbm_inst.cu"), f"inst_{st}_{so}.o",
                           [f"-DLBM_ST={st}", f"-DLBM_STORE={so}"]))
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):

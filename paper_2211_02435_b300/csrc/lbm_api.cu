@@ -19,21 +19,29 @@ using lbm::StepArgs;
 typedef void (*step_fn)(const StepArgs&);
 typedef void (*aux_fn)(const AuxArgs&);
 
-const step_fn kStep[3][4] = {
-    {lbm::launch_step_0_0, lbm::launch_step_0_1, lbm::launch_step_0_2, lbm::launch_step_0_3},
-    {lbm::launch_step_1_0, lbm::launch_step_1_1, lbm::launch_step_1_2, lbm::launch_step_1_3},
-    {lbm::launch_step_2_0, lbm::launch_step_2_1, lbm::launch_step_2_2, lbm::launch_step_2_3}};
-const aux_fn kAux[3][4] = {
-    {lbm::launch_aux_0_0, lbm::launch_aux_0_1, lbm::launch_aux_0_2, lbm::launch_aux_0_3},
-    {lbm::launch_aux_1_0, lbm::launch_aux_1_1, lbm::launch_aux_1_2, lbm::launch_aux_1_3},
-    {lbm::launch_aux_2_0, lbm::launch_aux_2_1, lbm::launch_aux_2_2, lbm::launch_aux_2_3}};
+const step_fn kStep[3][5] = {
+    {lbm::launch_step_0_0, lbm::launch_step_0_1, lbm::launch_step_0_2, lbm::launch_step_0_3,
+     lbm::launch_step_0_4},
+    {lbm::launch_step_1_0, lbm::launch_step_1_1, lbm::launch_step_1_2, lbm::launch_step_1_3,
+     lbm::launch_step_1_4},
+    {lbm::launch_step_2_0, lbm::launch_step_2_1, lbm::launch_step_2_2, lbm::launch_step_2_3,
+     lbm::launch_step_2_4}};
+const aux_fn kAux[3][5] = {
+    {lbm::launch_aux_0_0, lbm::launch_aux_0_1, lbm::launch_aux_0_2, lbm::launch_aux_0_3,
+     lbm::launch_aux_0_4},
+    {lbm::launch_aux_1_0, lbm::launch_aux_1_1, lbm::launch_aux_1_2, lbm::launch_aux_1_3,
+     lbm::launch_aux_1_4},
+    {lbm::launch_aux_2_0, lbm::launch_aux_2_1, lbm::launch_aux_2_2, lbm::launch_aux_2_3,
+     lbm::launch_aux_2_4}};
 
 constexpr int G_PULL = 0, G_LOCAL = 1, G_AAODD = 2;
 constexpr uint64_t kStateMagic = 0x4c424d3253544154ull;  // "LBM2STAT"
 
 int q_of(int st) { return st == LBM_D2Q9 ? 9 : (st == LBM_D3Q19 ? 19 : 27); }
 int elem_bytes(int storage) {
-  return storage == LBM_STORE_F64 ? 8 : (storage == LBM_STORE_F32 ? 4 : 2);
+  return (storage == LBM_STORE_F64 || storage == LBM_STORE_F64_ABSOLUTE)
+             ? 8
+             : (storage == LBM_STORE_F32 ? 4 : 2);
 }
 
 struct StateHeader {
@@ -62,8 +70,8 @@ void* state_buf(const lbm_ctx* c) {
 
 void set_effective_rates(lbm_ctx* c, const double* r) {
   for (int k = 0; k < 6; ++k) c->rates[k] = c->p.space == LBM_SPACE_POPULATIONS ? r[0] : r[k];
-  c->space = c->p.space == LBM_SPACE_POPULATIONS ? LBM_SPACE_RAW : c->p.space;
-  c->reg = 1;
+  c->space = c->p.space;  // POPULATIONS is the population-space SRT kernel
+  c->reg = c->p.space != LBM_SPACE_POPULATIONS;
   for (int k = 1; k < 6; ++k)
     if (c->rates[k] != 1.0) c->reg = 0;
 }
@@ -137,10 +145,10 @@ void dispatch_step(int stencil, int storage, const StepArgs& a) { kStep[stencil]
 void dispatch_aux(int stencil, int storage, const AuxArgs& a) { kAux[stencil][storage](a); }
 
 typedef void (*batch_fn)(const BatchArgs&);
-static const batch_fn kBatch[3][4] = {
-    {launch_batch_0_0, launch_batch_0_1, launch_batch_0_2, launch_batch_0_3},
-    {launch_batch_1_0, launch_batch_1_1, launch_batch_1_2, launch_batch_1_3},
-    {launch_batch_2_0, launch_batch_2_1, launch_batch_2_2, launch_batch_2_3}};
+static const batch_fn kBatch[3][5] = {
+    {launch_batch_0_0, launch_batch_0_1, launch_batch_0_2, launch_batch_0_3, launch_batch_0_4},
+    {launch_batch_1_0, launch_batch_1_1, launch_batch_1_2, launch_batch_1_3, launch_batch_1_4},
+    {launch_batch_2_0, launch_batch_2_1, launch_batch_2_2, launch_batch_2_3, launch_batch_2_4}};
 void dispatch_batch(int stencil, int storage, const BatchArgs& a) { kBatch[stencil][storage](a); }
 
 }  // namespace lbm
@@ -165,11 +173,19 @@ int lbm_create(lbm_ctx** out, const lbm_params* p) {
   if (!out || !p) return LBM_ERR_INVALID;
   *out = nullptr;
   if (p->stencil < 0 || p->stencil > 2 || p->space < 0 || p->space > 3 || p->storage < 0 ||
-      p->storage > 3 || p->streaming < 0 || p->streaming > 1 ||
-      (p->equilibrium != LBM_EQ_DELTA && p->equilibrium != LBM_EQ_ABSOLUTE))
+      p->storage > 4 || p->streaming < 0 || p->streaming > 1 ||
+      (p->equilibrium != LBM_EQ_DELTA && p->equilibrium != LBM_EQ_ABSOLUTE) ||
+      (p->arithmetic != LBM_ARITH_DEVIATION && p->arithmetic != LBM_ARITH_AS_WRITTEN))
     return LBM_ERR_INVALID;
+  // Sec. 3: no zero-centered cumulants; delta-equilibria need zero-centered storage
   if (p->space == LBM_SPACE_CUMULANT && p->equilibrium == LBM_EQ_DELTA)
     return LBM_ERR_INADMISSIBLE;
+  if (p->storage == LBM_STORE_F64_ABSOLUTE && p->equilibrium == LBM_EQ_DELTA)
+    return LBM_ERR_INADMISSIBLE;
+  if ((p->storage == LBM_STORE_F64_ABSOLUTE || p->arithmetic == LBM_ARITH_AS_WRITTEN) &&
+      (p->streaming != LBM_PULL ||
+       (p->storage != LBM_STORE_F64 && p->storage != LBM_STORE_F64_ABSOLUTE)))
+    return LBM_ERR_UNSUPPORTED;
   if (p->boundary != LBM_PERIODIC) return LBM_ERR_UNSUPPORTED;
   for (int k = 0; k < 3; ++k)
     if (p->dims[k] < 1) return LBM_ERR_INVALID;
@@ -309,6 +325,7 @@ int lbm_step(lbm_ctx* c, int64_t n) {
   a.space = c->space;
   a.reg = c->reg;
   a.storage = c->p.storage;
+  a.form = (c->p.arithmetic == LBM_ARITH_AS_WRITTEN && c->p.equilibrium == LBM_EQ_ABSOLUTE) ? 1 : 0;
   a.stream = c->stream;
   const step_fn fn = kStep[c->p.stencil][c->p.storage];
   for (int64_t s = 0; s < n; ++s) {

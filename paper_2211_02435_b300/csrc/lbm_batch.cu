@@ -43,7 +43,7 @@ int cuda_err(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
 int q_of(int st) { return st == LBM_D2Q9 ? 9 : (st == LBM_D3Q19 ? 19 : 27); }
 int elem_bytes(int storage) {
   return storage == LBM_STORE_F64 ? 8 : (storage == LBM_STORE_F32 ? 4 : 2);
-}
+}  // absolute storage is rejected at create
 
 void drop_graphs(lbm_batch* b) {
   for (int k = 0; k < 2; ++k)
@@ -159,11 +159,13 @@ int lbm_batch_create(lbm_batch** out, const lbm_params* p, int n, const int64_t*
   if (!out || !p || n < 1 || !dims) return LBM_ERR_INVALID;
   *out = nullptr;
   if (p->stencil < 0 || p->stencil > 2 || p->space < 0 || p->space > 3 || p->storage < 0 ||
-      p->storage > 3 || (p->equilibrium != LBM_EQ_DELTA && p->equilibrium != LBM_EQ_ABSOLUTE))
+      p->storage > 4 || (p->equilibrium != LBM_EQ_DELTA && p->equilibrium != LBM_EQ_ABSOLUTE))
     return LBM_ERR_INVALID;
   if (p->space == LBM_SPACE_CUMULANT && p->equilibrium == LBM_EQ_DELTA)
     return LBM_ERR_INADMISSIBLE;
-  if (p->boundary != LBM_PERIODIC || p->streaming != LBM_PULL) return LBM_ERR_UNSUPPORTED;
+  if (p->boundary != LBM_PERIODIC || p->streaming != LBM_PULL ||
+      p->storage == LBM_STORE_F64_ABSOLUTE || p->arithmetic != LBM_ARITH_DEVIATION)
+    return LBM_ERR_UNSUPPORTED;
   for (int k = 0; k < 6; ++k)
     if (!(p->rates[k] > 0.0 && p->rates[k] <= 2.0)) return LBM_ERR_INVALID;
   int ndev = 0;
@@ -179,9 +181,9 @@ int lbm_batch_create(lbm_batch** out, const lbm_params* p, int n, const int64_t*
   b->d = p->stencil == LBM_D2Q9 ? 2 : 3;
   b->eb = elem_bytes(p->storage);
   b->stream = (cudaStream_t)p->stream;
-  b->space = p->space == LBM_SPACE_POPULATIONS ? LBM_SPACE_RAW : p->space;
+  b->space = p->space;
   for (int k = 0; k < 6; ++k) b->rates[k] = p->space == LBM_SPACE_POPULATIONS ? p->rates[0] : p->rates[k];
-  b->reg = 1;
+  b->reg = p->space != LBM_SPACE_POPULATIONS;
   for (int k = 1; k < 6; ++k)
     if (b->rates[k] != 1.0) b->reg = 0;
   int64_t off = 0;

@@ -765,7 +765,7 @@ int lbm_trainer_snapshot_count(const lbm_trainer* t) { return t ? t->count : LBM
 int lbm_trainer_add_restricted(lbm_trainer* t, lbm_ctx* fine) {
   if (!t || !fine || t->count >= t->cap) return LBM_ERR_INVALID;
   if (fine->p.stencil != LBM_D3Q27 || fine->g.nx != 4 * t->g.nx || fine->g.ny != 4 * t->g.ny ||
-      fine->g.nz != 4 * t->g.nz)
+      fine->g.nz != 4 * t->g.nz || fine->p.storage > LBM_STORE_BF16_DELTA)
     return LBM_ERR_INVALID;
   const int mode = fine->p.streaming == LBM_PULL ? lbm::G_PULL
                                                  : (fine->parity ? lbm::G_AAODD : lbm::G_LOCAL);

@@ -34,7 +34,7 @@
 namespace lbm {
 
 enum { D2Q9 = 0, D3Q19 = 1, D3Q27 = 2 };
-enum { SP_RAW = 1, SP_CENTRAL = 2, SP_CUMULANT = 3 };
+enum { SP_SRT = 0, SP_RAW = 1, SP_CENTRAL = 2, SP_CUMULANT = 3 };
 
 // ---------------------------------------------------------------- helpers
 template <class F, int... Is>
@@ -79,6 +79,15 @@ LBM_HD constexpr int scale_exp(int st, int i) {
   if (st == D2Q9) return n2 == 0 ? 1 : (n2 == 1 ? 3 : 5);
   if (st == D3Q19) return n2 == 0 ? 2 : (n2 == 1 ? 4 : 5);
   return n2 == 0 ? 2 : (n2 == 1 ? 4 : (n2 == 2 ? 6 : 8));
+}
+
+// lattice weight w_i = f0_i (Sec. 2.4) by speed class |xi_i|^2
+LBM_HD constexpr double weight(int st, int i) {
+  int n2 = vel(st, i, 0) * vel(st, i, 0) + vel(st, i, 1) * vel(st, i, 1) +
+           vel(st, i, 2) * vel(st, i, 2);
+  if (st == D2Q9) return n2 == 0 ? 4.0 / 9.0 : (n2 == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
+  if (st == D3Q19) return n2 == 0 ? 1.0 / 3.0 : (n2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+  return n2 == 0 ? 8.0 / 27.0 : (n2 == 1 ? 2.0 / 27.0 : (n2 == 2 ? 1.0 / 54.0 : 1.0 / 216.0));
 }
 
 // rest-state background factor of one axis exponent: (1, 0, 1/3)
@@ -368,9 +377,11 @@ LBM_D void relax_order2(T (&X)[3][3][3], T ks, T kb) {
 // diagonal, 0 elsewhere) of orders 4-6 into C; orders 2-3 are identical.
 // Each order-n formula is the sum over the set partitions of the index
 // multiset into blocks of size >= 2 (central moments have no first order).
-template <int ST, class T>
+// ABS: K holds absolute normalised central moments and C receives absolute
+// cumulants (the same relations with the background constant A = 0).
+template <int ST, class T, bool ABS = false>
 LBM_D void cumulant_fwd(const T (&K)[3][3][3], T (&C)[3][3][3]) {
-  const T A = T(1.0 / 3.0);
+  const T A = T(ABS ? 0.0 : 1.0 / 3.0);
   const T a = K[2][0][0], b = K[0][2][0], c = K[0][0][2];
   const T k110 = K[1][1][0], k101 = K[1][0][1], k011 = K[0][1][1];
   C[2][2][0] = K[2][2][0] - A * (a + b) - a * b - T(2) * k110 * k110;
@@ -406,9 +417,9 @@ LBM_D void cumulant_fwd(const T (&K)[3][3][3], T (&C)[3][3][3]) {
 // cumulant deviations of orders 2..6; writes normalised central-moment
 // deviations of orders 4..6 into K.  REG: every cumulant of order >= 3 is
 // zero (rates 1), so only Gaussian products of second-order cumulants stay.
-template <int ST, class T, bool REG>
+template <int ST, class T, bool REG, bool ABS = false>
 LBM_D void cumulant_bwd(const T (&C)[3][3][3], T (&K)[3][3][3]) {
-  const T A = T(1.0 / 3.0);
+  const T A = T(ABS ? 0.0 : 1.0 / 3.0);
   const T a = C[2][0][0], b = C[0][2][0], c = C[0][0][2];
   const T c110 = C[1][1][0], c101 = C[1][0][1], c011 = C[0][1][1];
   const T g220 = A * (a + b) + a * b + T(2) * c110 * c110;
@@ -462,6 +473,9 @@ LBM_D void cumulant_bwd(const T (&C)[3][3][3], T (&K)[3][3][3]) {
   }
 }
 
+template <int ST, class T, int SPACE>
+LBM_D void equilibrium(T drho, const T (&u)[3], T (&f)[q_of(ST)]);
+
 // ------------------------------------------------------------ collision
 // In: zero-centered pre-collision populations f.  Out: zero-centered
 // post-collision populations f*.  keep.om[g] = 1 - omega_g.
@@ -476,7 +490,16 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep) {
   const T u[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
   const T u2[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
 
-  if constexpr (SPACE == SP_RAW) {
+  if constexpr (SPACE == SP_SRT) {
+    // single relaxation time in population space against f_eq = M^-1 m_eq
+    T feq[q_of(ST)];
+    equilibrium<ST, T, SP_RAW>(drho, u, feq);
+    sfor<q_of(ST)>([&](auto I) {
+      constexpr int i = CI(I);
+      f[i] = feq[i] + keep.om[0] * (f[i] - feq[i]);
+    });
+    return;
+  } else if constexpr (SPACE == SP_RAW) {
     // non-equilibrium parts in the orthogonal basis, relax, transform back
     T E[3][3][3], N[3][3][3];
     sfor<27>([&](auto K) {
@@ -606,6 +629,171 @@ LBM_D void equilibrium(T drho, const T (&u)[3], T (&f)[q_of(ST)]) {
     });
     binomial<ST, +1, T>(A, u, u2);
   }
+  bwd_raw<ST, T>(A, f);
+}
+
+// ----------------------------------------- collision in absolute arithmetic
+// The paper's Eq. 2.4 on absolute populations (used for absolute storage and,
+// from zero-centered storage, for Eq. 2.6): every moment, central moment and
+// cumulant is carried with its background, q* = q_eq + (1 - omega)(q - q_eq).
+// In / out: absolute populations f.  For round-off studies; FP64.
+template <int ST, class T, int SPACE, bool REG>
+LBM_D void collide_abs(T (&f)[q_of(ST)], const Rates<T>& keep) {
+  T A[3][3][3];
+  fwd_raw_chimera<ST, T>(f, A);
+  const T rho = A[0][0][0];
+  const T drho = rho - T(1);
+  const T inv = rcp(rho);
+  const T j[3] = {A[1][0][0], A[0][1][0], dim_of(ST) == 3 ? A[0][0][1] : T(0)};
+  const T u[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
+  const T u2[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
+  // absolute raw equilibrium moments (truncated Maxwellian, Sec. 4.2)
+  auto raw_eq_abs = [&](int a, int b, int c) -> T {
+    return raw_eq_dev<T>(a, b, c, drho, rho, u) + T(a + b + c == 0 ? 1.0 : bg3(a, b, c));
+  };
+  if constexpr (SPACE == SP_SRT) {
+    T Me[3][3][3];
+    sfor<27>([&](auto K) {
+      constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+      if constexpr (has_mono(ST, a, b, c)) {
+        if constexpr (a + b + c == 0) Me[a][b][c] = rho;
+        else if constexpr (a + b + c == 1) Me[a][b][c] = A[a][b][c];
+        else Me[a][b][c] = raw_eq_abs(a, b, c);
+      } else {
+        Me[a][b][c] = T(0);
+      }
+    });
+    T feq[q_of(ST)];
+    bwd_raw<ST, T>(Me, feq);
+    sfor<q_of(ST)>([&](auto I) {
+      constexpr int i = CI(I);
+      f[i] = feq[i] + keep.om[0] * (f[i] - feq[i]);
+    });
+    return;
+  } else if constexpr (SPACE == SP_RAW) {
+    T E[3][3][3], N[3][3][3];
+    sfor<27>([&](auto K) {
+      constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+      constexpr int o = a + b + c;
+      if constexpr (has_mono(ST, a, b, c) && o >= 2) {
+        E[a][b][c] = raw_eq_abs(a, b, c);
+        if constexpr (REG && o != 2) N[a][b][c] = T(0);
+        else N[a][b][c] = A[a][b][c] - E[a][b][c];
+      } else {
+        E[a][b][c] = T(0);
+        N[a][b][c] = T(0);
+      }
+    });
+    if constexpr (!REG) ortho_raw<ST, -1, T>(N);
+    relax_order2<ST, T, REG>(N, keep.om[0], keep.om[1]);
+    if constexpr (!REG) {
+      sfor<27>([&](auto K) {
+        constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+        constexpr int o = a + b + c;
+        if constexpr (has_mono(ST, a, b, c) && o >= 3) N[a][b][c] *= keep.om[o - 1];
+      });
+    }
+    ortho_raw<ST, +1, T>(N);
+    sfor<27>([&](auto K) {
+      constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+      if constexpr (has_mono(ST, a, b, c) && a + b + c >= 2) A[a][b][c] = E[a][b][c] + N[a][b][c];
+    });
+  } else {
+    // absolute central moments: the binomial passes without background
+    auto binom_abs = [&](auto sign_tag) {
+      constexpr int SIGN = decltype(sign_tag)::value;
+      if constexpr (dim_of(ST) == 3) {
+        sfor<9>([&](auto K) {
+          binom3<SIGN, T, 0>(A[CI(K) / 3][CI(K) % 3][0], A[CI(K) / 3][CI(K) % 3][1],
+                             A[CI(K) / 3][CI(K) % 3][2], u[2], u2[2], T(0));
+        });
+      }
+      sfor<9>([&](auto K) {
+        constexpr int a = CI(K) / 3, c = CI(K) % 3;
+        if constexpr (dim_of(ST) == 3 || c == 0)
+          binom3<SIGN, T, 0>(A[a][0][c], A[a][1][c], A[a][2][c], u[1], u2[1], T(0));
+      });
+      sfor<9>([&](auto K) {
+        constexpr int b = CI(K) / 3, c = CI(K) % 3;
+        if constexpr (dim_of(ST) == 3 || c == 0)
+          binom3<SIGN, T, 0>(A[0][b][c], A[1][b][c], A[2][b][c], u[0], u2[0], T(0));
+      });
+    };
+    binom_abs(std::integral_constant<int, -1>{});
+    T Kn[3][3][3];  // absolute normalised central moments kappa / rho
+    sfor<27>([&](auto K) {
+      constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+      if constexpr (has_mono(ST, a, b, c) && a + b + c >= 2) Kn[a][b][c] = A[a][b][c] * inv;
+      else Kn[a][b][c] = T(0);
+    });
+    // equilibrium: Gaussian moments bg3 (central) / 1/3 on the 2nd-order
+    // diagonal and 0 above (cumulants)
+    T X[3][3][3], Xeq[3][3][3];
+    if constexpr (SPACE == SP_CENTRAL) {
+      sfor<27>([&](auto K) {
+        constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+        X[a][b][c] = Kn[a][b][c];
+        Xeq[a][b][c] = T(bg3(a, b, c));
+      });
+    } else {
+      sfor<27>([&](auto K) {
+        constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+        constexpr int o = a + b + c;
+        X[a][b][c] = Kn[a][b][c];
+        Xeq[a][b][c] = T(o == 2 ? bg3(a, b, c) : 0.0);
+      });
+      cumulant_fwd<ST, T, true>(Kn, X);
+    }
+    T N[3][3][3];
+    sfor<27>([&](auto K) {
+      constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+      constexpr int o = a + b + c;
+      if constexpr (has_mono(ST, a, b, c) && o >= 2) N[a][b][c] = X[a][b][c] - Xeq[a][b][c];
+      else N[a][b][c] = T(0);
+    });
+    relax_order2<ST, T, REG>(N, keep.om[0], keep.om[1]);
+    sfor<27>([&](auto K) {
+      constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+      constexpr int o = a + b + c;
+      if constexpr (has_mono(ST, a, b, c) && o >= 2) {
+        if constexpr (o == 2) X[a][b][c] = Xeq[a][b][c] + N[a][b][c];
+        else if constexpr (REG) X[a][b][c] = Xeq[a][b][c];
+        else X[a][b][c] = Xeq[a][b][c] + keep.om[o - 1] * N[a][b][c];
+      }
+    });
+    if constexpr (SPACE == SP_CUMULANT) {
+      sfor<27>([&](auto K) {
+        constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+        constexpr int o = a + b + c;
+        Kn[a][b][c] = (o == 2 || o == 3) ? X[a][b][c] : T(0);
+      });
+      cumulant_bwd<ST, T, REG, true>(X, Kn);
+      if constexpr (REG) {
+        sfor<27>([&](auto K) {
+          constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+          if constexpr (a + b + c == 3) Kn[a][b][c] = T(0);
+        });
+      }
+    } else {
+      sfor<27>([&](auto K) {
+        constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+        Kn[a][b][c] = X[a][b][c];
+      });
+    }
+    sfor<27>([&](auto K) {
+      constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+      constexpr int o = a + b + c;
+      if constexpr (o == 0) A[a][b][c] = rho;
+      else if constexpr (o == 1) A[a][b][c] = T(0);
+      else if constexpr (has_mono(ST, a, b, c)) A[a][b][c] = rho * Kn[a][b][c];
+      else A[a][b][c] = T(0);
+    });
+    binom_abs(std::integral_constant<int, +1>{});
+  }
+  A[0][0][0] = rho;
+  A[1][0][0] = j[0];
+  A[0][1][0] = j[1];
+  if constexpr (dim_of(ST) == 3) A[0][0][1] = j[2];
   bwd_raw<ST, T>(A, f);
 }
 

@@ -21,9 +21,12 @@ using CompT = float;
 #elif LBM_STORE == 2
 using StoreT = __half;
 using CompT = float;
-#else
+#elif LBM_STORE == 3
 using StoreT = __nv_bfloat16;
 using CompT = float;
+#else
+using StoreT = AbsF64;
+using CompT = double;
 #endif
 
 #define LBM_CAT(a, b, c) a##b##_##c
@@ -35,8 +38,13 @@ void LBM_FN(launch_step_, LBM_ST, LBM_STORE)(const StepArgs& a) {
 void LBM_FN(launch_aux_, LBM_ST, LBM_STORE)(const AuxArgs& a) {
   launch_aux_typed<LBM_ST, StoreT, CompT>(a);
 }
+#if LBM_STORE == 4
+// the batched ensemble does not serve absolute storage (rejected at create)
+void LBM_FN(launch_batch_, LBM_ST, LBM_STORE)(const BatchArgs&) {}
+#else
 void LBM_FN(launch_batch_, LBM_ST, LBM_STORE)(const BatchArgs& a) {
   launch_batch_space<LBM_ST, StoreT, CompT>(a);
 }
+#endif
 
 }  // namespace lbm

@@ -15,7 +15,7 @@ struct Geo {
   int64_t N;  // nx * ny * nz (< 2^31)
 };
 
-enum { STORE_F64 = 0, STORE_F32 = 1, STORE_F16 = 2, STORE_BF16 = 3 };
+enum { STORE_F64 = 0, STORE_F32 = 1, STORE_F16 = 2, STORE_BF16 = 3, STORE_F64_ABS = 4 };
 enum { MODE_PULL = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2 };
 enum { AUX_GATHER = 0, AUX_SCATTER = 1, AUX_INVARIANTS = 2 };
 
@@ -28,6 +28,7 @@ struct StepArgs {
   int reg;    // bulk and orders >= 3 relaxed with rate 1 (compile-time)
   int storage;
   int mode;
+  int form;  // FORM_DEV / FORM_ABS_EQ (Eq. 2.6 arithmetic, FP64 storage)
   cudaStream_t stream;
 };
 
@@ -53,9 +54,9 @@ struct AuxArgs {
 #define LBM_DECL(ST, SO)                           \
   void launch_step_##ST##_##SO(const StepArgs& a); \
   void launch_aux_##ST##_##SO(const AuxArgs& a);
-LBM_DECL(0, 0) LBM_DECL(0, 1) LBM_DECL(0, 2) LBM_DECL(0, 3)
-LBM_DECL(1, 0) LBM_DECL(1, 1) LBM_DECL(1, 2) LBM_DECL(1, 3)
-LBM_DECL(2, 0) LBM_DECL(2, 1) LBM_DECL(2, 2) LBM_DECL(2, 3)
+LBM_DECL(0, 0) LBM_DECL(0, 1) LBM_DECL(0, 2) LBM_DECL(0, 3) LBM_DECL(0, 4)
+LBM_DECL(1, 0) LBM_DECL(1, 1) LBM_DECL(1, 2) LBM_DECL(1, 3) LBM_DECL(1, 4)
+LBM_DECL(2, 0) LBM_DECL(2, 1) LBM_DECL(2, 2) LBM_DECL(2, 3) LBM_DECL(2, 4)
 #undef LBM_DECL
 
 // ----- batched ensemble (lbm_batch.cu)
@@ -81,9 +82,9 @@ struct BatchArgs {
   cudaStream_t stream;
 };
 #define LBM_BDECL(ST, SO) void launch_batch_##ST##_##SO(const BatchArgs& a);
-LBM_BDECL(0, 0) LBM_BDECL(0, 1) LBM_BDECL(0, 2) LBM_BDECL(0, 3)
-LBM_BDECL(1, 0) LBM_BDECL(1, 1) LBM_BDECL(1, 2) LBM_BDECL(1, 3)
-LBM_BDECL(2, 0) LBM_BDECL(2, 1) LBM_BDECL(2, 2) LBM_BDECL(2, 3)
+LBM_BDECL(0, 0) LBM_BDECL(0, 1) LBM_BDECL(0, 2) LBM_BDECL(0, 3) LBM_BDECL(0, 4)
+LBM_BDECL(1, 0) LBM_BDECL(1, 1) LBM_BDECL(1, 2) LBM_BDECL(1, 3) LBM_BDECL(1, 4)
+LBM_BDECL(2, 0) LBM_BDECL(2, 1) LBM_BDECL(2, 2) LBM_BDECL(2, 3) LBM_BDECL(2, 4)
 #undef LBM_BDECL
 
 void launch_invariants_fold(const double* part, int nparts, double* out, cudaStream_t s);

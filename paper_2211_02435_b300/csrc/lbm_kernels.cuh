@@ -23,6 +23,28 @@ namespace lbm {
 // how a kernel reads the canonical populations f(n) of a cell
 enum { G_PULL = 0, G_LOCAL = 1, G_AAODD = 2 };
 
+// absolute FP64 storage element (LBM_STORE_F64_ABSOLUTE): holds f_i itself
+struct AbsF64 {
+  double v;
+};
+
+// storage element <-> zero-centered population i (every read-out and set-up
+// kernel works on df; absolute storage adds / removes the weight w_i)
+template <int ST, int i, class S, class T>
+LBM_D T dec_pop(S v) {
+  if constexpr (std::is_same<S, AbsF64>::value) return T(v.v - weight(ST, i));
+  else return Codec<S>::template dec<T>(v, scale_exp(ST, i));
+}
+template <int ST, int i, class S, class T>
+LBM_D S enc_pop(T f) {
+  if constexpr (std::is_same<S, AbsF64>::value) return AbsF64{double(f) + weight(ST, i)};
+  else return Codec<S>::template enc<T>(f, scale_exp(ST, i));
+}
+
+// arithmetic form of the step kernel: deviations (default), Eq. 2.6 from
+// zero-centered storage, Eq. 2.4 on absolute storage
+enum { FORM_DEV = 0, FORM_ABS_EQ = 1, FORM_ABS_STORE = 2 };
+
 struct Nbr {
   int x[3], y[3], z[3];  // coordinate of offset -1, 0, +1 (periodic)
 };
@@ -60,7 +82,7 @@ LBM_D void load_pops(const S* buf, const Geo& g, const Nbr& n, int c, T (&f)[q_o
     if constexpr (MODE != G_LOCAL) src_c = cell_at(n, g, -cx, -cy, -cz);
     if constexpr (MODE == G_AAODD) slot = opp(i);
     const S v = buf[(int64_t)slot * g.N + src_c];
-    f[i] = Codec<S>::template dec<T>(v, scale_exp(ST, i));
+    f[i] = dec_pop<ST, i, S, T>(v);
   });
 }
 
@@ -77,7 +99,7 @@ struct PullPtrs {
 };
 
 // pull: read f_i from x - xi_i of src, collide, write f*_i at x of dst
-template <int ST, class S, class T, int SPACE, bool REG>
+template <int ST, class S, class T, int SPACE, bool REG, int FORM = FORM_DEV>
 __global__ void __launch_bounds__(LBM_BX) k_pull(const __grid_constant__ PullPtrs<S> P, Geo g,
                                                  Rates<T> keep) {
   const int x = blockIdx.x * LBM_BX + threadIdx.x;
@@ -96,12 +118,20 @@ __global__ void __launch_bounds__(LBM_BX) k_pull(const __grid_constant__ PullPtr
     const int wyz = (cy > 0 ? wyp : (cy < 0 ? wym : 0)) + (cz > 0 ? wzp : (cz < 0 ? wzm : 0));
     const int wx = cx > 0 ? wxp : (cx < 0 ? wxm : 0);
     const S v = P.src[i][c + wx + wyz];
-    f[i] = Codec<S>::template dec<T>(v, scale_exp(ST, i));
+    if constexpr (FORM == FORM_ABS_STORE) {
+      f[i] = T(v.v);
+    } else {
+      f[i] = dec_pop<ST, i, S, T>(v);
+      if constexpr (FORM == FORM_ABS_EQ) f[i] += T(weight(ST, i));  // f = df + f0
+    }
   });
-  collide<ST, T, SPACE, REG>(f, keep);
+  if constexpr (FORM == FORM_DEV) collide<ST, T, SPACE, REG>(f, keep);
+  else collide_abs<ST, T, SPACE, REG>(f, keep);
   sfor<q_of(ST)>([&](auto I) {
     constexpr int i = CI(I);
-    P.dst[i][c] = Codec<S>::template enc<T>(f[i], scale_exp(ST, i));
+    if constexpr (FORM == FORM_ABS_STORE) P.dst[i][c] = S{double(f[i])};
+    else if constexpr (FORM == FORM_ABS_EQ) P.dst[i][c] = enc_pop<ST, i, S, T>(f[i] - T(weight(ST, i)));
+    else P.dst[i][c] = enc_pop<ST, i, S, T>(f[i]);
   });
 }
 
@@ -167,7 +197,7 @@ __global__ void __launch_bounds__(LBM_BX) k_aa(S* buf, Geo g, Rates<T> keep) {
       dc = cell_at(n, g, cx, cy, cz);
       slot = i;
     }
-    buf[(int64_t)slot * g.N + dc] = Codec<S>::template enc<T>(f[i], scale_exp(ST, i));
+    buf[(int64_t)slot * g.N + dc] = enc_pop<ST, i, S, T>(f[i]);
   });
 }
 
@@ -229,7 +259,7 @@ __global__ void __launch_bounds__(LBM_BX) k_scatter(S* buf, Geo g, const double*
     constexpr int i = CI(I);
     int dc = c;
     if constexpr (PULL) dc = cell_at(n, g, -vel(ST, i, 0), -vel(ST, i, 1), -vel(ST, i, 2));
-    buf[(int64_t)i * g.N + dc] = Codec<S>::template enc<T>(f[i], scale_exp(ST, i));
+    buf[(int64_t)i * g.N + dc] = enc_pop<ST, i, S, T>(f[i]);
   });
 }
 
@@ -321,7 +351,7 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS)
       collide<ST, T, SPACE, REG>(f, k);
       sfor<q_of(ST)>([&](auto I_) {
         constexpr int i = CI(I_);
-        d[(int64_t)i * g.N + c] = Codec<S>::template enc<T>(f[i], scale_exp(ST, i));
+        d[(int64_t)i * g.N + c] = enc_pop<ST, i, S, T>(f[i]);
       });
     }
   }
@@ -358,7 +388,7 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS)
       sfor<q_of(ST)>([&](auto I_) {
         constexpr int i = CI(I_);
         const int dc = cell_at(n, g, -vel(ST, i, 0), -vel(ST, i, 1), -vel(ST, i, 2));
-        b[(int64_t)i * g.N + dc] = Codec<S>::template enc<T>(f[i], scale_exp(ST, i));
+        b[(int64_t)i * g.N + dc] = enc_pop<ST, i, S, T>(f[i]);
       });
     }
   }
@@ -381,6 +411,15 @@ void launch_step_typed(const StepArgs& a) {
       P.dst[i] = (S*)a.dst + int64_t(i) * a.g.N;
     }
     for (int i = q_of(ST); i < 27; ++i) P.src[i] = nullptr, P.dst[i] = nullptr;
+    if constexpr (std::is_same<S, AbsF64>::value) {
+      k_pull<ST, S, T, SPACE, REG, FORM_ABS_STORE><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep);
+      return;
+    } else if constexpr (std::is_same<S, double>::value) {
+      if (a.form == FORM_ABS_EQ) {
+        k_pull<ST, S, T, SPACE, REG, FORM_ABS_EQ><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep);
+        return;
+      }
+    }
     constexpr bool half = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
     if constexpr (half) {
       if (a.g.nx % 2 == 0) {
@@ -402,6 +441,8 @@ void launch_step_typed(const StepArgs& a) {
 template <int ST, class S, class T>
 void launch_step_space(const StepArgs& a) {
   switch (a.space * 2 + (a.reg ? 1 : 0)) {
+    case SP_SRT * 2:
+    case SP_SRT * 2 + 1: launch_step_typed<ST, S, T, SP_SRT, false>(a); break;
     case SP_RAW * 2: launch_step_typed<ST, S, T, SP_RAW, false>(a); break;
     case SP_RAW * 2 + 1: launch_step_typed<ST, S, T, SP_RAW, true>(a); break;
     case SP_CENTRAL * 2: launch_step_typed<ST, S, T, SP_CENTRAL, false>(a); break;
@@ -426,7 +467,7 @@ void launch_aux_typed(const AuxArgs& a) {
       break;
     case AUX_SCATTER: {
       const bool pull = gm == G_PULL;
-      if (a.space == SP_RAW) {
+      if (a.space == SP_RAW || a.space == SP_SRT) {
         if (pull)
           k_scatter<ST, S, T, SP_RAW, true><<<grid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in);
         else
@@ -453,7 +494,7 @@ void launch_aux_typed(const AuxArgs& a) {
 template <int ST, class S, class T, int SPACE, bool REG>
 void launch_batch_typed(const BatchArgs& a) {
   if (a.op == BATCH_TGV) {
-    k_batch_tgv<ST, S, T, (SPACE == SP_RAW ? SP_RAW : SP_CENTRAL)>
+    k_batch_tgv<ST, S, T, (SPACE == SP_RAW || SPACE == SP_SRT ? SP_RAW : SP_CENTRAL)>
         <<<a.grid, a.threads, 0, a.stream>>>((S*)a.dst, a.inst, a.tiles, a.ntiles, a.cpt, a.u0);
     return;
   }
@@ -466,6 +507,8 @@ void launch_batch_typed(const BatchArgs& a) {
 template <int ST, class S, class T>
 void launch_batch_space(const BatchArgs& a) {
   switch (a.space * 2 + (a.reg ? 1 : 0)) {
+    case SP_SRT * 2:
+    case SP_SRT * 2 + 1: launch_batch_typed<ST, S, T, SP_SRT, false>(a); break;
     case SP_RAW * 2: launch_batch_typed<ST, S, T, SP_RAW, false>(a); break;
     case SP_RAW * 2 + 1: launch_batch_typed<ST, S, T, SP_RAW, true>(a); break;
     case SP_CENTRAL * 2: launch_batch_typed<ST, S, T, SP_CENTRAL, false>(a); break;

@@ -19,11 +19,13 @@ LIB_PATH = os.path.join(_HERE, "liblbm.so")
 D2Q9, D3Q19, D3Q27 = 0, 1, 2
 SPACE_POPULATIONS, SPACE_RAW, SPACE_CENTRAL, SPACE_CUMULANT = 0, 1, 2, 3
 EQ_DELTA, EQ_ABSOLUTE = 0, 1
-STORE_F64, STORE_F32, STORE_F16_DELTA, STORE_BF16_DELTA = 0, 1, 2, 3
+STORE_F64, STORE_F32, STORE_F16_DELTA, STORE_BF16_DELTA, STORE_F64_ABSOLUTE = 0, 1, 2, 3, 4
+ARITH_DEVIATION, ARITH_AS_WRITTEN = 0, 1
 PULL, AA = 0, 1
 PERIODIC = 0
 Q_OF = {D2Q9: 9, D3Q19: 19, D3Q27: 27}
-ELEM_BYTES = {STORE_F64: 8, STORE_F32: 4, STORE_F16_DELTA: 2, STORE_BF16_DELTA: 2}
+ELEM_BYTES = {STORE_F64: 8, STORE_F32: 4, STORE_F16_DELTA: 2, STORE_BF16_DELTA: 2,
+              STORE_F64_ABSOLUTE: 8}
 
 ERRORS = {0: "ok", -1: "invalid argument", -2: "unsupported", -3: "inadmissible",
           -4: "device out of memory", -5: "CUDA error", -6: "non-finite populations",
@@ -41,7 +43,7 @@ class Params(ctypes.Structure):
                 ("equilibrium", ctypes.c_int), ("storage", ctypes.c_int),
                 ("streaming", ctypes.c_int), ("rates", ctypes.c_double * 6),
                 ("dims", ctypes.c_int64 * 3), ("boundary", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("arithmetic", ctypes.c_int)]
 
 
 class Tuning(ctypes.Structure):
@@ -188,7 +190,7 @@ class Lattice:
     """One periodic domain advanced by the fused stream + collide step."""
 
     def __init__(self, stencil, space, equilibrium, storage, streaming, rates, dims,
-                 stream=None):
+                 stream=None, arithmetic=ARITH_DEVIATION):
         self.stencil, self.space, self.storage, self.streaming = stencil, space, storage, streaming
         self.equilibrium = equilibrium
         self.q = Q_OF[stencil]
@@ -198,7 +200,8 @@ class Lattice:
         self.N = self.dims[0] * self.dims[1] * self.dims[2]
         r = list(rates) + [1.0] * (6 - len(rates))
         p = Params(stencil, space, equilibrium, storage, streaming, (ctypes.c_double * 6)(*r),
-                   (ctypes.c_int64 * 3)(*self.dims), PERIODIC, stream_handle(stream))
+                   (ctypes.c_int64 * 3)(*self.dims), PERIODIC, stream_handle(stream),
+                   int(arithmetic))
         h = ctypes.c_void_p()
         _check(lib().lbm_create(ctypes.byref(h), ctypes.byref(p)), "lbm_create")
         self._h = h
@@ -319,7 +322,7 @@ class Batch:
         flat = (ctypes.c_int64 * (3 * n))(*[v for dm in self.dims for v in dm])
         r = list(rates) + [1.0] * (6 - len(rates))
         p = Params(stencil, space, equilibrium, storage, PULL, (ctypes.c_double * 6)(*r),
-                   (ctypes.c_int64 * 3)(1, 1, 1), PERIODIC, stream_handle(stream))
+                   (ctypes.c_int64 * 3)(1, 1, 1), PERIODIC, stream_handle(stream), 0)
         sr = None if shear_rates is None else (ctypes.c_double * n)(*[float(x) for x in shear_rates])
         h = ctypes.c_void_p()
         _check(lib().lbm_batch_create(ctypes.byref(h), ctypes.byref(p), n, flat, sr),

@@ -39,11 +39,11 @@ def test_every_declared_symbol_is_exported(lib):
 def _params(**kw):
     p = dict(stencil=L.D3Q27, space=L.SPACE_CUMULANT, equilibrium=L.EQ_ABSOLUTE,
              storage=L.STORE_F32, streaming=L.PULL, rates=[1.9] + [1.0] * 5,
-             dims=(8, 8, 8), boundary=L.PERIODIC)
+             dims=(8, 8, 8), boundary=L.PERIODIC, arithmetic=L.ARITH_DEVIATION)
     p.update(kw)
     return L.Params(p["stencil"], p["space"], p["equilibrium"], p["storage"], p["streaming"],
                     (ctypes.c_double * 6)(*p["rates"]), (ctypes.c_int64 * 3)(*p["dims"]),
-                    p["boundary"], None)
+                    p["boundary"], None, p["arithmetic"])
 
 
 @pytest.mark.parametrize("kw,code", [
@@ -60,6 +60,12 @@ def _params(**kw):
     (dict(rates=[0.0] + [1.0] * 5), -1),
     (dict(space=L.SPACE_CUMULANT, equilibrium=L.EQ_DELTA), -3),
     (dict(boundary=1), -2),
+    (dict(arithmetic=2), -1),
+    # absolute storage holds f itself: delta-equilibria (Eq. 2.5) need zero-centered storage
+    (dict(space=L.SPACE_RAW, equilibrium=L.EQ_DELTA, storage=L.STORE_F64_ABSOLUTE), -3),
+    (dict(storage=L.STORE_F64_ABSOLUTE, streaming=L.AA), -2),
+    (dict(arithmetic=L.ARITH_AS_WRITTEN, storage=L.STORE_F32), -2),
+    (dict(arithmetic=L.ARITH_AS_WRITTEN, storage=L.STORE_F64, streaming=L.AA), -2),
 ])
 def test_create_rejects_bad_parameters(lib, kw, code):
     h = ctypes.c_void_p()
