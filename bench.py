@@ -302,6 +302,8 @@ def run_cuda(args):
     def time_form(storage, steps, warmup, streaming=L.PULL):
         lat = L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, storage, streaming, rates,
                         (n, n, n), stream=stream)
+        if streaming == L.PULL:
+            lat.set_step_kernel(STEP_KERNELS[args.step_kernel])
         lat.init_velocity(rho_d, u_d)
         lat.step(warmup)
         torch.cuda.synchronize()
@@ -438,7 +440,8 @@ def run_cuda(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
                          "bytes_per_cell": BYTES_PER_CELL[main_key],
-                         "kernel": f"k_pull<D3Q27, {main_key} storage, cumulant, regularised>"},
+                         "kernel": f"k_pull<D3Q27, {main_key} storage, cumulant, regularised>",
+                         "step_kernel": args.step_kernel},
             "forms": forms, "batched": batched, "learned": learned, "clocks": clocks, "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": args.steps}
@@ -448,6 +451,9 @@ def run_cuda(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+STEP_KERNELS = {"auto": 0, "direct": 1, "staged": 2}  # LBM_STEP_* of include/lbm.h
 
 
 def main():
@@ -468,6 +474,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-fine", type=int, default=512)
     ap.add_argument("--batch-n", type=int, default=4096)
+    ap.add_argument("--step-kernel", choices=list(STEP_KERNELS), default="auto",
+                    help="pull step kernel of the D3Q27 forms (include/lbm.h)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "cuda":
         args.warmup = 3

@@ -63,6 +63,7 @@ extern "C" {
 #define LBM_ERR_CUDA -5           /* CUDA runtime error / no device          */
 #define LBM_ERR_DIVERGED -6       /* non-finite populations detected         */
 #define LBM_ERR_STATE_MISMATCH -7 /* checkpoint does not fit this context    */
+#define LBM_ERR_TIMEOUT -8        /* a kernel's bounded wait ran out         */
 
 /* ---- method specification (Sec. 3, Fig. 2) ---- */
 typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 } lbm_stencil;
@@ -105,8 +106,13 @@ typedef enum {
  * equilibrium format is chosen (algebraically Eq. 2.5 / 2.6).  AS_WRITTEN:
  * the arithmetic the paper writes, for round-off studies (Sec. 5.1):
  * LBM_EQ_DELTA relaxes deviations against the delta-equilibrium (Eq. 2.5),
- * LBM_EQ_ABSOLUTE adds f0 back and collides absolute populations (Eq. 2.6).
- * AS_WRITTEN is served for FP64 storage with pull streaming. */
+ * LBM_EQ_ABSOLUTE evaluates Eq. 2.6: q = T(df + f0) is formed as the
+ * nonlinear part of T (shift to central moments, cumulants) applied to the
+ * raw moments M df plus the constant background moments M f0, the collision
+ * runs on these absolute quantities, and T^-1(q*) - f0 is formed as M^-1 of
+ * the post-collision raw moments minus M f0 (M is linear).  Population-space
+ * SRT (T = identity) adds f0 = w to df and subtracts it again.  AS_WRITTEN
+ * is served for FP64 storage with pull streaming. */
 typedef enum { LBM_ARITH_DEVIATION = 0, LBM_ARITH_AS_WRITTEN = 1 } lbm_arithmetic;
 
 /* Streaming pattern (Sec. 4.3): pull with two buffers, or the in-place
@@ -230,6 +236,28 @@ int lbm_set_rates(lbm_ctx* ctx, const double rates[6]);
 
 /* Change the stream later work is enqueued on. */
 int lbm_set_stream(lbm_ctx* ctx, void* stream);
+
+/* Pull step kernel.  Both compute the same per-cell arithmetic and give
+ * bitwise-identical states; they differ in how the gather of Eq. 2.1b
+ * reaches the cell:
+ *   LBM_STEP_DIRECT: each thread loads its cells' q populations from
+ *     global memory (one grid of 128-thread CTAs over all cells).
+ *   LBM_STEP_STAGED: a persistent CTA copies, per x-row of cells, the q
+ *     source rows into shared memory with bulk asynchronous copies (two rows
+ *     in flight) and collides from there.  Needs pull streaming, deviation
+ *     arithmetic, Nx * element size a multiple of 16 bytes and
+ *     2 * q * Nx * element size <= 110 KiB (FP16/BF16: Nx <= 1024 for D3Q27;
+ *     FP32: Nx <= 512); otherwise LBM_ERR_UNSUPPORTED.
+ *   LBM_STEP_AUTO (default): the faster of the two for the context.
+ * The paper has no counterpart (its kernels are generated per platform).
+ * A staged kernel whose bounded wait ran out makes the next synchronising
+ * call (lbm_macroscopic / lbm_get_populations into host memory,
+ * lbm_invariants, lbm_get_state) return LBM_ERR_TIMEOUT.
+ * Errors: INVALID, UNSUPPORTED. */
+#define LBM_STEP_AUTO 0
+#define LBM_STEP_DIRECT 1
+#define LBM_STEP_STAGED 2
+int lbm_set_step_kernel(lbm_ctx* ctx, int kernel);
 
 /* Free the context and its device memory.  NULL is ignored. */
 void lbm_destroy(lbm_ctx* ctx);

@@ -165,6 +165,7 @@ const char* lbm_error_string(int code) {
     case LBM_ERR_CUDA: return "CUDA error";
     case LBM_ERR_DIVERGED: return "non-finite populations";
     case LBM_ERR_STATE_MISMATCH: return "state does not match this context";
+    case LBM_ERR_TIMEOUT: return "a kernel's bounded wait ran out";
     default: return "unknown error";
   }
 }
@@ -231,11 +232,17 @@ int lbm_create(lbm_ctx** out, const lbm_params* p) {
   }
   const int64_t np = (N + 255) / 256;
   c->nparts = int(np < 148 * 8 ? np : 148 * 8);
-  if (cudaMalloc((void**)&c->part, sizeof(double) * (size_t(c->nparts) * 8 + 8)) != cudaSuccess) {
+  // invariants scratch (nparts rows + 8 results) and one status word
+  if (cudaMalloc((void**)&c->part, sizeof(double) * (size_t(c->nparts) * 8 + 9)) != cudaSuccess) {
     cudaGetLastError();
     c->part = nullptr;
     lbm_destroy(c);
     return LBM_ERR_OOM;
+  }
+  c->status = reinterpret_cast<int*>(c->part + size_t(c->nparts) * 8 + 8);
+  if (cudaMemsetAsync(c->status, 0, sizeof(int), c->stream) != cudaSuccess) {
+    lbm_destroy(c);
+    return LBM_ERR_CUDA;
   }
   *out = c;
   return LBM_OK;
@@ -316,6 +323,38 @@ int lbm_set_populations(lbm_ctx* c, const double* df, int on_device) {
   return rc;
 }
 
+// Can this context run the shared-memory staged pull kernel?
+static bool staged_ok(const lbm_ctx* c) {
+  const int64_t row = int64_t(c->g.nx) * c->eb;
+  return c->p.streaming == LBM_PULL && c->p.storage != LBM_STORE_F64_ABSOLUTE &&
+         c->p.arithmetic == LBM_ARITH_DEVIATION && row % 16 == 0 &&
+         lbm::staged_smem_bytes(c->q, c->g.nx, c->eb) <= lbm::STG_MAX_SMEM;
+}
+
+// LBM_STEP_AUTO: measured on B300 (see the profiles of the staged kernel)
+static bool use_staged(const lbm_ctx* c) {
+  if (c->kernel == LBM_STEP_STAGED) return true;
+  if (c->kernel == LBM_STEP_DIRECT || c->closure) return false;
+  return false;
+}
+
+int lbm_set_step_kernel(lbm_ctx* c, int kernel) {
+  if (!c || kernel < LBM_STEP_AUTO || kernel > LBM_STEP_STAGED) return LBM_ERR_INVALID;
+  if (kernel == LBM_STEP_STAGED && !staged_ok(c)) return LBM_ERR_UNSUPPORTED;
+  c->kernel = kernel;
+  return LBM_OK;
+}
+
+// Nonzero status word: a staged kernel's bounded wait ran out (synchronises).
+static int read_status(lbm_ctx* c) {
+  int st = 0;
+  if (cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  return st ? LBM_ERR_TIMEOUT : LBM_OK;
+}
+
 int lbm_step(lbm_ctx* c, int64_t n) {
   if (!c || n < 0) return LBM_ERR_INVALID;
   StepArgs a;
@@ -326,6 +365,8 @@ int lbm_step(lbm_ctx* c, int64_t n) {
   a.reg = c->reg;
   a.storage = c->p.storage;
   a.form = (c->p.arithmetic == LBM_ARITH_AS_WRITTEN && c->p.equilibrium == LBM_EQ_ABSOLUTE) ? 1 : 0;
+  a.variant = use_staged(c) ? lbm::VARIANT_STAGED : lbm::VARIANT_DIRECT;
+  a.status = c->status;
   a.stream = c->stream;
   const step_fn fn = kStep[c->p.stencil][c->p.storage];
   for (int64_t s = 0; s < n; ++s) {
@@ -380,6 +421,7 @@ static int gather(lbm_ctx* c, double* df, double* rho, double* u, int on_device)
           cudaMemcpyAsync(u, tu, N * c->d * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
   }
+  if (rc == LBM_OK && !on_device) rc = read_status(c);
   if (tdf) cudaFree(tdf);
   if (trho) cudaFree(trho);
   if (tu) cudaFree(tu);
@@ -409,6 +451,7 @@ int lbm_invariants(lbm_ctx* c, double out[8]) {
     rc = cuda_err(cudaMemcpyAsync(out, c->part + size_t(c->nparts) * 8, 8 * sizeof(double),
                                   cudaMemcpyDeviceToHost, c->stream));
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+  if (rc == LBM_OK) rc = read_status(c);
   if (rc == LBM_OK && out[6] > 0) rc = LBM_ERR_DIVERGED;
   return rc;
 }
@@ -436,6 +479,7 @@ int lbm_get_state(lbm_ctx* c, void* buf, size_t bytes) {
   int rc = cuda_err(cudaMemcpyAsync((char*)buf + sizeof(h), state_buf(c), size_t(h.payload),
                                     cudaMemcpyDeviceToHost, c->stream));
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+  if (rc == LBM_OK) rc = read_status(c);
   return rc;
 }
 

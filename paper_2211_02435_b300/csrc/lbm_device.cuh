@@ -633,14 +633,32 @@ LBM_D void equilibrium(T drho, const T (&u)[3], T (&f)[q_of(ST)]) {
 }
 
 // ----------------------------------------- collision in absolute arithmetic
-// The paper's Eq. 2.4 on absolute populations (used for absolute storage and,
-// from zero-centered storage, for Eq. 2.6): every moment, central moment and
-// cumulant is carried with its background, q* = q_eq + (1 - omega)(q - q_eq).
-// In / out: absolute populations f.  For round-off studies; FP64.
-template <int ST, class T, int SPACE, bool REG>
+// The paper's Eq. 2.4 in absolute arithmetic: every moment, central moment
+// and cumulant is carried with its background, q* = q_eq + (1 - omega)(q -
+// q_eq).  For round-off studies; FP64.
+//   ZC = false: in / out absolute populations f (absolute storage).
+//   ZC = true : Eq. 2.6 on zero-centered storage, in / out df.  T(df + f0)
+//     is evaluated as the nonlinear part of T applied to M df + M f0, with
+//     the background raw moments M f0 = (1, 0, 1/3, ...) added as constants
+//     (M is linear), and T^-1(q*) - f0 as M^-1 (raw moments of q* - M f0);
+//     the conserved moments keep their deviation values.  Population-space
+//     SRT (T = identity) adds and subtracts f0 = w itself.
+template <int ST, class T, int SPACE, bool REG, bool ZC = false>
 LBM_D void collide_abs(T (&f)[q_of(ST)], const Rates<T>& keep) {
+  if constexpr (ZC && SPACE == SP_SRT) {
+    sfor<q_of(ST)>([&](auto I) { f[CI(I)] += T(weight(ST, CI(I))); });
+  }
   T A[3][3][3];
   fwd_raw_chimera<ST, T>(f, A);
+  T drho0 = T(0);  // ZC: the deviation density, kept through the collision
+  if constexpr (ZC && SPACE != SP_SRT) {
+    drho0 = A[0][0][0];
+    sfor<27>([&](auto K) {
+      constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+      if constexpr (has_mono(ST, a, b, c) && a + b + c != 1)
+        A[a][b][c] += T(a + b + c == 0 ? 1.0 : bg3(a, b, c));
+    });
+  }
   const T rho = A[0][0][0];
   const T drho = rho - T(1);
   const T inv = rcp(rho);
@@ -668,6 +686,7 @@ LBM_D void collide_abs(T (&f)[q_of(ST)], const Rates<T>& keep) {
     sfor<q_of(ST)>([&](auto I) {
       constexpr int i = CI(I);
       f[i] = feq[i] + keep.om[0] * (f[i] - feq[i]);
+      if constexpr (ZC) f[i] -= T(weight(ST, i));
     });
     return;
   } else if constexpr (SPACE == SP_RAW) {
@@ -794,6 +813,13 @@ LBM_D void collide_abs(T (&f)[q_of(ST)], const Rates<T>& keep) {
   A[1][0][0] = j[0];
   A[0][1][0] = j[1];
   if constexpr (dim_of(ST) == 3) A[0][0][1] = j[2];
+  if constexpr (ZC) {
+    A[0][0][0] = drho0;
+    sfor<27>([&](auto K) {
+      constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+      if constexpr (has_mono(ST, a, b, c) && a + b + c >= 2) A[a][b][c] -= T(bg3(a, b, c));
+    });
+  }
   bwd_raw<ST, T>(A, f);
 }
 

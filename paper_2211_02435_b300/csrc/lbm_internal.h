@@ -17,6 +17,14 @@ struct Geo {
 
 enum { STORE_F64 = 0, STORE_F32 = 1, STORE_F16 = 2, STORE_BF16 = 3, STORE_F64_ABS = 4 };
 enum { MODE_PULL = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2 };
+enum { VARIANT_DIRECT = 0, VARIANT_STAGED = 1 };
+
+// shared-memory staged pull kernel (lbm_staged.cuh)
+constexpr int STG_STAGES = 2;             // rows in flight per CTA
+constexpr int STG_MAX_SMEM = 110 * 1024;  // stage bytes per CTA: two CTAs per SM
+inline int64_t staged_smem_bytes(int q, int nx, int elem) {
+  return int64_t(STG_STAGES) * q * nx * elem;
+}
 enum { AUX_GATHER = 0, AUX_SCATTER = 1, AUX_INVARIANTS = 2 };
 
 struct StepArgs {
@@ -28,7 +36,9 @@ struct StepArgs {
   int reg;    // bulk and orders >= 3 relaxed with rate 1 (compile-time)
   int storage;
   int mode;
-  int form;  // FORM_DEV / FORM_ABS_EQ (Eq. 2.6 arithmetic, FP64 storage)
+  int form;     // FORM_DEV / FORM_ABS_EQ (Eq. 2.6 arithmetic, FP64 storage)
+  int variant;  // VARIANT_DIRECT / VARIANT_STAGED (pull only)
+  int* status;  // device word set by a kernel whose bounded wait ran out
   cudaStream_t stream;
 };
 
@@ -118,5 +128,7 @@ struct lbm_ctx {
   double rates[6];
   int reg;
   void* closure;  // device closure parameters (lbm_closure.cu), NULL = off
+  int* status;    // device word after the invariants scratch: nonzero = a bounded wait ran out
+  int kernel;     // requested step kernel (LBM_STEP_*)
 };
 

@@ -13,6 +13,7 @@
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 #include "lbm_packed.cuh"
+#include "lbm_staged.cuh"
 
 namespace lbm {
 
@@ -118,19 +119,14 @@ __global__ void __launch_bounds__(LBM_BX) k_pull(const __grid_constant__ PullPtr
     const int wyz = (cy > 0 ? wyp : (cy < 0 ? wym : 0)) + (cz > 0 ? wzp : (cz < 0 ? wzm : 0));
     const int wx = cx > 0 ? wxp : (cx < 0 ? wxm : 0);
     const S v = P.src[i][c + wx + wyz];
-    if constexpr (FORM == FORM_ABS_STORE) {
-      f[i] = T(v.v);
-    } else {
-      f[i] = dec_pop<ST, i, S, T>(v);
-      if constexpr (FORM == FORM_ABS_EQ) f[i] += T(weight(ST, i));  // f = df + f0
-    }
+    if constexpr (FORM == FORM_ABS_STORE) f[i] = T(v.v);
+    else f[i] = dec_pop<ST, i, S, T>(v);
   });
   if constexpr (FORM == FORM_DEV) collide<ST, T, SPACE, REG>(f, keep);
-  else collide_abs<ST, T, SPACE, REG>(f, keep);
+  else collide_abs<ST, T, SPACE, REG, FORM == FORM_ABS_EQ>(f, keep);
   sfor<q_of(ST)>([&](auto I) {
     constexpr int i = CI(I);
     if constexpr (FORM == FORM_ABS_STORE) P.dst[i][c] = S{double(f[i])};
-    else if constexpr (FORM == FORM_ABS_EQ) P.dst[i][c] = enc_pop<ST, i, S, T>(f[i] - T(weight(ST, i)));
     else P.dst[i][c] = enc_pop<ST, i, S, T>(f[i]);
   });
 }
@@ -411,6 +407,12 @@ void launch_step_typed(const StepArgs& a) {
       P.dst[i] = (S*)a.dst + int64_t(i) * a.g.N;
     }
     for (int i = q_of(ST); i < 27; ++i) P.src[i] = nullptr, P.dst[i] = nullptr;
+    if constexpr (!std::is_same<S, AbsF64>::value) {
+      if (a.variant == VARIANT_STAGED && a.form == FORM_DEV) {
+        launch_staged<ST, S, T, SPACE, REG>(a);
+        return;
+      }
+    }
     if constexpr (std::is_same<S, AbsF64>::value) {
       k_pull<ST, S, T, SPACE, REG, FORM_ABS_STORE><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep);
       return;

@@ -21,6 +21,7 @@ SPACE_POPULATIONS, SPACE_RAW, SPACE_CENTRAL, SPACE_CUMULANT = 0, 1, 2, 3
 EQ_DELTA, EQ_ABSOLUTE = 0, 1
 STORE_F64, STORE_F32, STORE_F16_DELTA, STORE_BF16_DELTA, STORE_F64_ABSOLUTE = 0, 1, 2, 3, 4
 ARITH_DEVIATION, ARITH_AS_WRITTEN = 0, 1
+STEP_AUTO, STEP_DIRECT, STEP_STAGED = 0, 1, 2
 PULL, AA = 0, 1
 PERIODIC = 0
 Q_OF = {D2Q9: 9, D3Q19: 19, D3Q27: 27}
@@ -88,6 +89,7 @@ def lib():
         L.lbm_get_time.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(c_int)]
         L.lbm_set_rates.argtypes = [vp, d]
         L.lbm_set_stream.argtypes = [vp, vp]
+        L.lbm_set_step_kernel.argtypes = [vp, c_int]
         L.lbm_destroy.argtypes = [vp]
         L.lbm_destroy.restype = None
         L.lbm_error_string.argtypes = [c_int]
@@ -301,6 +303,10 @@ class Lattice:
 
     def set_stream(self, stream):
         _check(lib().lbm_set_stream(self._h, stream_handle(stream)), "lbm_set_stream")
+
+    def set_step_kernel(self, kernel):
+        """STEP_AUTO, STEP_DIRECT or STEP_STAGED (include/lbm.h)."""
+        _check(lib().lbm_set_step_kernel(self._h, int(kernel)), "lbm_set_step_kernel")
 
     def set_closure(self, weights):
         """Enable the learned rates (a ClosureWeights) or disable them (None)."""

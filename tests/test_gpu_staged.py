@@ -1,0 +1,112 @@
+"""The shared-memory staged pull kernel (LBM_STEP_STAGED, bulk asynchronous
+copies of whole source rows) against the direct pull kernel: the same
+per-cell arithmetic, so the states must be bitwise equal, and both within
+the parity tolerance of the oracle.  Lattices have more rows than the
+persistent grid has CTAs in some cases and fewer in others, small Ny / Nz
+(periodic wrap of the source rows) and Nx a multiple of 8."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2211_02435_b300 import build as B
+from paper_2211_02435_b300 import inputs as I
+from paper_2211_02435_b300 import lbm as L
+
+pytestmark = pytest.mark.gpu
+
+RATES_GEN = [1.7, 1.2, 1.3, 1.4, 1.5, 1.6]
+RATES_REG = [1.9, 1.0, 1.0, 1.0, 1.0, 1.0]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    B.build()
+    O.build()
+
+
+def start(st, space, eq, rates, dims, seed):
+    d = 2 if st == 0 else 3
+    rho, u = I.taylor_green(dims, 0.05, d=d)
+    u = I.add_uniform_noise(u, 1e-3, seed=seed)
+    m = O.method(st, space, eq, rates)
+    df = O.init(m, dims, rho, u)
+    _, w, _ = O.lattice(st)
+    pert = I.random_deviations(len(w), int(np.prod(dims)), 2e-3, seed=seed + 1)
+    return m, df + (w[:, None] * pert).reshape(df.shape)
+
+
+def run(st, space, eq, storage, rates, dims, df0, kernel, n):
+    with L.Lattice(st, space, eq, storage, L.PULL, rates, dims) as lat:
+        lat.set_step_kernel(kernel)
+        lat.set_populations(df0)
+        lat.step(n)
+        out = lat.get_populations()
+        inv = lat.invariants()
+    return out, inv
+
+
+CASES = [  # (stencil, space, eq, rates, dims)
+    (2, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, RATES_REG, (64, 5, 4)),
+    (2, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, RATES_GEN, (32, 3, 3)),
+    (2, L.SPACE_CENTRAL, L.EQ_ABSOLUTE, RATES_REG, (48, 7, 2)),
+    (1, L.SPACE_RAW, L.EQ_DELTA, RATES_GEN, (40, 6, 5)),
+    (1, L.SPACE_CENTRAL, L.EQ_DELTA, RATES_REG, (64, 33, 31)),
+    (0, L.SPACE_RAW, L.EQ_DELTA, RATES_REG, (256, 37, 1)),
+    (0, L.SPACE_POPULATIONS, L.EQ_DELTA, [1.6] * 6, (24, 11, 1)),
+    (2, L.SPACE_POPULATIONS, L.EQ_DELTA, [1.6] * 6, (16, 2, 3)),
+]
+
+
+@pytest.mark.parametrize("storage", [L.STORE_F64, L.STORE_F32, L.STORE_F16_DELTA,
+                                     L.STORE_BF16_DELTA])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_staged_equals_direct(case, storage):
+    st, space, eq, rates, dims = CASES[case]
+    m, df0 = start(st, space, eq, rates, dims, seed=40 + case)
+    a, ia = run(st, space, eq, storage, rates, dims, df0, L.STEP_DIRECT, 5)
+    b, ib = run(st, space, eq, storage, rates, dims, df0, L.STEP_STAGED, 5)
+    assert np.array_equal(a, b)
+    assert ia == ib
+    if storage in (L.STORE_F64, L.STORE_F32):
+        ref = O.step(m, dims, df0, 5)
+        tol = 1e-12 if storage == L.STORE_F64 else 1e-5
+        assert np.abs(b - ref).max() / np.abs(ref).max() < tol
+
+
+def test_staged_large_rows_and_many_rows():
+    """Nx = 512 (the largest FP32 D3Q27 row the stage buffers take) and more
+    rows than the persistent grid has CTAs."""
+    st, space, eq, rates = 2, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, RATES_REG
+    dims = (512, 40, 30)
+    rho, u = I.taylor_green(dims, 0.05)
+    u = I.add_uniform_noise(u, 1e-3, seed=7)
+    out = {}
+    for storage in (L.STORE_F32, L.STORE_F16_DELTA):
+        for kernel in (L.STEP_DIRECT, L.STEP_STAGED):
+            with L.Lattice(st, space, eq, storage, L.PULL, rates, dims) as lat:
+                lat.set_step_kernel(kernel)
+                lat.init_velocity(rho.reshape(-1), u.reshape(-1))
+                lat.step(3)
+                out[storage, kernel] = lat.get_populations()
+        assert np.array_equal(out[storage, L.STEP_DIRECT], out[storage, L.STEP_STAGED])
+
+
+def test_staged_rejects_what_it_cannot_run():
+    bad = [  # (storage, streaming, dims, arithmetic)
+        (L.STORE_F32, L.AA, (64, 4, 4), 0),
+        (L.STORE_F16_DELTA, L.PULL, (36, 4, 4), 0),     # row 72 B, not a multiple of 16
+        (L.STORE_F32, L.PULL, (1024, 2, 2), 0),         # 2 x 27 x 4 KiB > 110 KiB
+        (L.STORE_F64, L.PULL, (64, 4, 4), L.ARITH_AS_WRITTEN),
+        (L.STORE_F64_ABSOLUTE, L.PULL, (64, 4, 4), 0),
+    ]
+    for storage, streaming, dims, arith in bad:
+        with L.Lattice(2, L.SPACE_CENTRAL, L.EQ_ABSOLUTE, storage, streaming, RATES_REG, dims,
+                       arithmetic=arith) as lat:
+            with pytest.raises(L.LBMError) as e:
+                lat.set_step_kernel(L.STEP_STAGED)
+            assert e.value.code == -2
+            lat.set_step_kernel(L.STEP_DIRECT)
+            lat.set_step_kernel(L.STEP_AUTO)
+            with pytest.raises(L.LBMError) as e:
+                lat.set_step_kernel(3)
+            assert e.value.code == -1
