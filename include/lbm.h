@@ -237,15 +237,16 @@ int lbm_set_rates(lbm_ctx* ctx, const double rates[6]);
 /* Change the stream later work is enqueued on. */
 int lbm_set_stream(lbm_ctx* ctx, void* stream);
 
-/* Pull step kernel.  Both compute the same per-cell arithmetic and give
- * bitwise-identical states; they differ in how the gather of Eq. 2.1b
- * reaches the cell:
+/* Pull step kernel.  Both compute the same per-cell arithmetic (FP16/BF16
+ * storage: bitwise-identical states; FP32/FP64: equal up to the compiler's
+ * choice of multiply-add contractions); they differ in how the gather of
+ * Eq. 2.1b reaches the cell:
  *   LBM_STEP_DIRECT: each thread loads its cells' q populations from
  *     global memory (one grid of 128-thread CTAs over all cells).
  *   LBM_STEP_STAGED: a persistent CTA copies, per x-row of cells, the q
- *     source rows into shared memory with bulk asynchronous copies (two rows
- *     in flight) and collides from there.  Needs pull streaming, deviation
- *     arithmetic, Nx * element size a multiple of 16 bytes and
+ *     source rows into shared memory with bulk asynchronous copies (two to
+ *     four rows in flight) and collides from there.  Needs pull streaming,
+ *     deviation arithmetic, Nx * element size a multiple of 16 bytes and
  *     2 * q * Nx * element size <= 110 KiB (FP16/BF16: Nx <= 1024 for D3Q27;
  *     FP32: Nx <= 512); otherwise LBM_ERR_UNSUPPORTED.
  *   LBM_STEP_AUTO (default): the faster of the two for the context.

@@ -328,7 +328,7 @@ static bool staged_ok(const lbm_ctx* c) {
   const int64_t row = int64_t(c->g.nx) * c->eb;
   return c->p.streaming == LBM_PULL && c->p.storage != LBM_STORE_F64_ABSOLUTE &&
          c->p.arithmetic == LBM_ARITH_DEVIATION && row % 16 == 0 &&
-         lbm::staged_smem_bytes(c->q, c->g.nx, c->eb) <= lbm::STG_MAX_SMEM;
+         lbm::staged_stages(c->q, c->g.nx, c->eb) >= lbm::STG_MIN_STAGES;
 }
 
 // LBM_STEP_AUTO: measured on B300 (see the profiles of the staged kernel)

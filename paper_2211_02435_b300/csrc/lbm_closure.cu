@@ -14,6 +14,7 @@
 #include "lbm.h"
 #include "lbm_closure.h"
 #include "lbm_kernels.cuh"
+#include "lbm_umma.cuh"
 
 namespace lbm {
 
@@ -285,6 +286,193 @@ __global__ void __launch_bounds__(128)
   });
 }
 
+// ------------------------------------------- tensor-core network (FP32)
+// The three layers run on the tensor cores for the 128 cells of a CTA at
+// once: layer l is D = A * B^T with A = [a_hi | a_lo] (128 x 2K, row = cell)
+// and B = [W | W] (N x 2K), where a_hi = bf16(a) and a_lo = bf16(a - a_hi)
+// split each FP32 activation into two BF16 values.  The weights are BF16
+// values, so each product is exact and the sum runs in FP32 in tensor
+// memory; the split leaves a relative residual below 2^-17 per activation,
+// which keeps the rates within ~1e-5 of the FP32 CUDA-core network (the
+// populations far closer).  Layer 1 pads the 7 inputs to 8 (K = 16), layer
+// 3 pads the 4 outputs to N = 16.
+constexpr int TC_K1 = 16, TC_K2 = 2 * NH, TC_N3 = 16;
+constexpr int TC_B1 = 0, TC_B2 = TC_B1 + NH * TC_K1, TC_B3 = TC_B2 + NH * TC_K2;
+constexpr int TC_BELEMS = TC_B3 + TC_N3 * TC_K2;
+constexpr int TC_BOFF_BYTES = ((NSMEM * 4 + 127) / 128) * 128;  // packed B after the floats
+constexpr int TC_TMEM_COLS = 32;
+
+// Pack the weights (FP32 values of BF16 numbers) into the three B operands.
+inline void pack_tc_weights(const float* P, uint16_t* out) {
+  auto bits = [](float v) {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    return uint16_t(u >> 16);  // exact: v is a BF16 value
+  };
+  for (int k = 0; k < TC_BELEMS; ++k) out[k] = 0;
+  for (int n = 0; n < NH; ++n)
+    for (int k = 0; k < NIN; ++k)
+      for (int h = 0; h < 2; ++h)
+        out[TC_B1 + umma::kmajor_offset(n, h * 8 + k, TC_K1)] = bits(P[OW1 + n * NIN + k]);
+  for (int n = 0; n < NH; ++n)
+    for (int k = 0; k < NH; ++k)
+      for (int h = 0; h < 2; ++h)
+        out[TC_B2 + umma::kmajor_offset(n, h * NH + k, TC_K2)] = bits(P[OW2 + n * NH + k]);
+  for (int n = 0; n < NOUT; ++n)
+    for (int k = 0; k < NH; ++k)
+      for (int h = 0; h < 2; ++h)
+        out[TC_B3 + umma::kmajor_offset(n, h * NH + k, TC_K2)] = bits(P[OW3 + n * NH + k]);
+}
+
+// row `r` of an A operand: hi parts in columns [0, KH), lo parts in [KH, 2 KH)
+template <int KH>
+__device__ __forceinline__ void write_split(__nv_bfloat16* A, int r, const float (&v)[KH]) {
+#pragma unroll
+  for (int kc = 0; kc < KH / 8; ++kc) {
+    __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      hi[e] = __float2bfloat16_rn(v[kc * 8 + e]);
+      lo[e] = __float2bfloat16_rn(v[kc * 8 + e] - __bfloat162float(hi[e]));
+    }
+    *reinterpret_cast<uint4*>(A + umma::kmajor_offset(r, kc * 8, 2 * KH)) =
+        *reinterpret_cast<const uint4*>(hi);
+    *reinterpret_cast<uint4*>(A + umma::kmajor_offset(r, KH + kc * 8, 2 * KH)) =
+        *reinterpret_cast<const uint4*>(lo);
+  }
+}
+
+// One layer: every thread has written its A row; thread 0 issues the K/16
+// MMAs into tensor-memory columns [0, N) and commits them to `bar`; every
+// thread waits (bounded) for the given phase.  Returns false on a timeout.
+template <int K, int N>
+__device__ __forceinline__ bool tc_layer(const __nv_bfloat16* A, const __nv_bfloat16* B,
+                                         uint32_t tmem, uint64_t* bar, uint32_t phase) {
+  umma::fence_proxy_async();
+  umma::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    umma::fence_after_sync();
+#pragma unroll
+    for (int kk = 0; kk < K / 16; ++kk) {
+      const uint64_t ad = umma::smem_desc(A + kk * 128, 128, (K / 8) * 128);
+      const uint64_t bd = umma::smem_desc(B + kk * 128, 128, (K / 8) * 128);
+      umma::mma_bf16(tmem, ad, bd, umma::idesc_bf16_f32(N), kk > 0);
+    }
+    umma::commit(bar);
+  }
+  const bool ok = tma::mbar_wait(bar, phase);
+  __syncwarp();  // reconverge after the wait loop for the .sync.aligned load
+  umma::fence_after_sync();
+  return ok;
+}
+
+// fused pull step with the learned rates, FP32, network on the tensor cores
+__global__ void __launch_bounds__(128)
+    k_closure_pull_tc(const float* __restrict__ src, float* __restrict__ dst, Geo g,
+                      Rates<float> keep, const float* __restrict__ params, int* status) {
+  __shared__ float sp[NSMEM];
+  __shared__ __align__(128) __nv_bfloat16 sB[TC_BELEMS];
+  __shared__ __align__(128) __nv_bfloat16 sA1[128 * TC_K1];
+  __shared__ __align__(128) __nv_bfloat16 sA2[128 * TC_K2];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int t = threadIdx.x, warp = t / 32;
+  for (int k = t; k < NSMEM; k += 128) sp[k] = params[k];
+  {
+    const uint4* gB =
+        reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(params) + TC_BOFF_BYTES);
+    uint4* sB4 = reinterpret_cast<uint4*>(sB);
+    for (int k = t; k < TC_BELEMS / 8; k += 128) sB4[k] = gB[k];
+  }
+  __syncwarp();  // the tcgen05 .sync.aligned forms need converged warps
+  if (warp == 0) umma::tmem_alloc(&tmem_base, TC_TMEM_COLS);
+  if (t == 0) {
+    tma::mbar_init(&bar, 1);
+    tma::fence_init();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t tlane = tmem + (uint32_t(warp * 32) << 16);
+
+  const int x = blockIdx.x * 128 + t;
+  const bool active = x < g.nx;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int c = (z * g.ny + y) * g.nx + (active ? x : 0);
+  float f[27];
+  CumState<float> s;
+  float xin[8];
+  bool ok = true;
+  if (active) {
+    const Nbr n = neighbours(x, y, z, g);
+    load_pops<D3Q27, float, float, G_PULL>(src, g, n, c, f);
+    cum_forward<float>(f, s);
+    float raw[NIN];
+    closure_features<float>(s.Kn, s.drho, 1.0f - keep.om[0], raw);
+#pragma unroll
+    for (int i = 0; i < NIN; ++i) {
+      xin[i] = (raw[i] - sp[NPARAM + i]) * sp[NPARAM + NIN + i];
+      ok = ok && isfinite(xin[i]);
+    }
+    xin[7] = 0.0f;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) xin[i] = 0.0f;
+  }
+  bool waited = true;
+  float acc[32], h[32];
+  write_split<8>(sA1, t, xin);
+  waited &= tc_layer<TC_K1, NH>(sA1, sB + TC_B1, tmem, &bar, 0);
+  umma::tmem_ld32(tlane, acc);
+#pragma unroll
+  for (int j = 0; j < NH; ++j) h[j] = tanhf(acc[j] + sp[OB1 + j]);
+  write_split<NH>(sA2, t, h);
+  waited &= tc_layer<TC_K2, NH>(sA2, sB + TC_B2, tmem, &bar, 1);
+  umma::tmem_ld32(tlane, acc);
+#pragma unroll
+  for (int j = 0; j < NH; ++j) h[j] = tanhf(acc[j] + sp[OB2 + j]);
+  write_split<NH>(sA2, t, h);
+  waited &= tc_layer<TC_K2, TC_N3>(sA2, sB + TC_B3, tmem, &bar, 0);
+  float z16[16];
+  umma::tmem_ld16(tlane, z16);
+  Rates<float> k = keep;
+#pragma unroll
+  for (int o = 0; o < NOUT; ++o) {
+    const float zz = z16[o] + sp[OB3 + o];
+    const float sg = 1.0f / (1.0f + expf(-zz));
+    float om = 2.0f * sg;
+    if (om < 1e-3f) om = 1e-3f;
+    if (om > 1.999f) om = 1.999f;
+    ok = ok && isfinite(om);
+    k.om[2 + o] = 1.0f - om;
+  }
+  if (!ok) {
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) k.om[2 + o] = 0.0f;  // rates 1
+  }
+  if (active) {
+    float Cs[3][3][3];
+    cum_backward<float>(s, k, Cs, f);
+    sfor<27>([&](auto I) {
+      constexpr int i = CI(I);
+      dst[(int64_t)i * g.N + c] = f[i];
+    });
+  }
+  umma::fence_before_sync();
+  if (__syncthreads_or(!waited)) {
+    // a bounded wait ran out: record it and let the last MMAs finish
+    if (t == 0) {
+      atomicExch(status, 1);
+      tma::mbar_wait(&bar, 0);
+    }
+    __syncthreads();
+  }
+  __syncwarp();
+  if (warp == 0) umma::tmem_dealloc(tmem, TC_TMEM_COLS);
+}
+
 // 4^3 block average of the canonical populations of a fine lattice
 template <class S, class T, int MODE>
 __global__ void __launch_bounds__(128)
@@ -553,8 +741,8 @@ void launch_closure_step(const StepArgs& a, const void* closure) {
   } else {
     Rates<float> keep;
     for (int k = 0; k < 6; ++k) keep.om[k] = float(1.0 - a.rates[k]);
-    k_closure_pull<float, float><<<grid, 128, 0, a.stream>>>((const float*)a.src, (float*)a.dst,
-                                                             a.g, keep, (const float*)closure);
+    k_closure_pull_tc<<<grid, 128, 0, a.stream>>>((const float*)a.src, (float*)a.dst, a.g, keep,
+                                                   (const float*)closure, a.status);
   }
 }
 
@@ -632,7 +820,9 @@ int lbm_set_closure(lbm_ctx* c, const lbm_closure_weights* w) {
     hd[NPARAM + k] = w->shift[k];
     hd[NPARAM + NIN + k] = w->scale[k];
   }
-  const size_t bytes = lbm::NSMEM * (dbl ? sizeof(double) : sizeof(float));
+  // FP32: the float parameters, then the packed tensor-core B operands
+  const size_t bytes = dbl ? lbm::NSMEM * sizeof(double)
+                           : size_t(lbm::TC_BOFF_BYTES) + lbm::TC_BELEMS * sizeof(uint16_t);
   void* dev = nullptr;
   if (cudaMalloc(&dev, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -642,8 +832,12 @@ int lbm_set_closure(lbm_ctx* c, const lbm_closure_weights* w) {
   if (dbl) {
     rc = cuda_err(cudaMemcpy(dev, hd.data(), bytes, cudaMemcpyHostToDevice));
   } else {
+    std::vector<unsigned char> img(bytes, 0);
     std::vector<float> hf(hd.begin(), hd.end());
-    rc = cuda_err(cudaMemcpy(dev, hf.data(), bytes, cudaMemcpyHostToDevice));
+    std::memcpy(img.data(), hf.data(), hf.size() * sizeof(float));
+    lbm::pack_tc_weights(hf.data(),
+                         reinterpret_cast<uint16_t*>(img.data() + lbm::TC_BOFF_BYTES));
+    rc = cuda_err(cudaMemcpy(dev, img.data(), bytes, cudaMemcpyHostToDevice));
   }
   if (rc != LBM_OK) {
     cudaFree(dev);

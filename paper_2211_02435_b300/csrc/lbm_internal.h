@@ -19,11 +19,22 @@ enum { STORE_F64 = 0, STORE_F32 = 1, STORE_F16 = 2, STORE_BF16 = 3, STORE_F64_AB
 enum { MODE_PULL = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2 };
 enum { VARIANT_DIRECT = 0, VARIANT_STAGED = 1 };
 
-// shared-memory staged pull kernel (lbm_staged.cuh)
-constexpr int STG_STAGES = 2;             // rows in flight per CTA
-constexpr int STG_MAX_SMEM = 110 * 1024;  // stage bytes per CTA: two CTAs per SM
+// shared-memory staged pull kernel (lbm_staged.cuh); the stage cap is a
+// compile-time tuning knob
+#ifndef LBM_STG_MAX_STAGES
+#define LBM_STG_MAX_STAGES 4
+#endif
+constexpr int STG_MIN_STAGES = 2, STG_MAX_STAGES = LBM_STG_MAX_STAGES;  // rows in flight per CTA
+constexpr int STG_MAX_SMEM = 110 * 1024;               // stage bytes per CTA: two CTAs per SM
+// as many stages as fit the budget (0 when not even two fit)
+inline int staged_stages(int q, int nx, int elem) {
+  const int64_t row = int64_t(q) * nx * elem;
+  int s = int(STG_MAX_SMEM / row);
+  if (s > STG_MAX_STAGES) s = STG_MAX_STAGES;
+  return s < STG_MIN_STAGES ? 0 : s;
+}
 inline int64_t staged_smem_bytes(int q, int nx, int elem) {
-  return int64_t(STG_STAGES) * q * nx * elem;
+  return int64_t(staged_stages(q, nx, elem)) * q * nx * elem;
 }
 enum { AUX_GATHER = 0, AUX_SCATTER = 1, AUX_INVARIANTS = 2 };
 

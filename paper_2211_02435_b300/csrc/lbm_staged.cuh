@@ -6,8 +6,8 @@
 // persistent CTA owns rows r = blockIdx.x + k * gridDim.x; for each it
 // issues q one-dimensional bulk copies global -> shared (one per direction,
 // the full row, so the x wrap is resolved by indexing in shared memory) that
-// complete on one mbarrier, and keeps STG_STAGES rows in flight while it
-// collides the current one.  The copies need no registers and no warps, so
+// complete on one mbarrier, and keeps `stages` rows (2 to 4, as many as fit
+// the shared-memory budget) in flight while it collides the current one.  The copies need no registers and no warps, so
 // the bytes in flight per SM no longer depend on the occupancy of the
 // (register-heavy) collision.  Stores go straight from registers to global
 // memory, coalesced along x.
@@ -94,11 +94,11 @@ constexpr int STG_NT = 256;  // threads per CTA
 // The row pipeline: calls body(rows_of_stage, r) for every row r of this
 // CTA, with rows_of_stage[i * nx + x] = plane i of row (y - xi_iy, z - xi_iz).
 template <int ST, class S, class Body>
-__device__ __forceinline__ void staged_rows(const RowPtrs<S>& P, const Geo& g, int* status,
-                                            Body&& body) {
+__device__ __forceinline__ void staged_rows(const RowPtrs<S>& P, const Geo& g, int stages,
+                                            int* status, Body&& body) {
   constexpr int Q = q_of(ST);
   extern __shared__ __align__(128) unsigned char stg_raw[];
-  __shared__ __align__(8) uint64_t bar[STG_STAGES];
+  __shared__ __align__(8) uint64_t bar[STG_MAX_STAGES];
   __shared__ int abort_all;
   S* const stage = reinterpret_cast<S*>(stg_raw);
   const int nx = g.nx;
@@ -108,7 +108,7 @@ __device__ __forceinline__ void staged_rows(const RowPtrs<S>& P, const Geo& g, i
   const int K = b < rows ? (rows - 1 - b) / G + 1 : 0;
   const uint32_t row_bytes = uint32_t(nx) * uint32_t(sizeof(S));
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STG_STAGES; ++s) tma::mbar_init(&bar[s], 1);
+    for (int s = 0; s < stages; ++s) tma::mbar_init(&bar[s], 1);
     tma::fence_init();
     abort_all = 0;
   }
@@ -127,23 +127,23 @@ __device__ __forceinline__ void staged_rows(const RowPtrs<S>& P, const Geo& g, i
     });
   };
   if (threadIdx.x == 0)
-    for (int s = 0; s < STG_STAGES && s < K; ++s) issue(s, b + s * G);
+    for (int s = 0; s < stages && s < K; ++s) issue(s, b + s * G);
   int k = 0;
   for (; k < K; ++k) {
-    const int s = k % STG_STAGES;
+    const int s = k % stages;
     const int r = b + k * G;
-    if (!tma::mbar_wait(&bar[s], uint32_t(k / STG_STAGES) & 1u)) abort_all = 1;
+    if (!tma::mbar_wait(&bar[s], uint32_t(k / stages) & 1u)) abort_all = 1;
     __syncthreads();
     if (abort_all) break;
     body(static_cast<const S*>(stage + int64_t(s) * Q * nx), r);
     __syncthreads();  // every thread is done reading stage s
-    if (threadIdx.x == 0 && k + STG_STAGES < K) issue(s, r + STG_STAGES * G);
+    if (threadIdx.x == 0 && k + stages < K) issue(s, r + stages * G);
   }
   if (abort_all && threadIdx.x == 0) {
     atomicExch(status, 1);
-    // rows k .. k + STG_STAGES - 1 were issued: let them land before exit
-    for (int j = k; j < K && j < k + STG_STAGES; ++j)
-      tma::mbar_wait(&bar[j % STG_STAGES], uint32_t(j / STG_STAGES) & 1u);
+    // rows k .. k + stages - 1 were issued: let them land before exit
+    for (int j = k; j < K && j < k + stages; ++j)
+      tma::mbar_wait(&bar[j % stages], uint32_t(j / stages) & 1u);
   }
 }
 
@@ -151,9 +151,10 @@ __device__ __forceinline__ void staged_rows(const RowPtrs<S>& P, const Geo& g, i
 // same per-cell arithmetic as k_pull2, so the results are bitwise equal.
 template <int ST, class S, int SPACE, bool REG>
 __global__ void __launch_bounds__(STG_NT, 3) k_pull2_staged(const __grid_constant__ RowPtrs<S> P,
-                                                          Geo g, Rates<P2> keep, int* status) {
+                                                          Geo g, Rates<P2> keep, int stages,
+                                                          int* status) {
   constexpr int Q = q_of(ST);
-  staged_rows<ST, S>(P, g, status, [&](const S* row, int r) {
+  staged_rows<ST, S>(P, g, stages, status, [&](const S* row, int r) {
     const int nx = g.nx;
     const int cbase = r * nx;
 #pragma unroll 1
@@ -186,9 +187,10 @@ __global__ void __launch_bounds__(STG_NT, 3) k_pull2_staged(const __grid_constan
 // per-cell arithmetic as k_pull.
 template <int ST, class S, class T, int SPACE, bool REG>
 __global__ void __launch_bounds__(STG_NT, 2) k_pull_staged(const __grid_constant__ RowPtrs<S> P,
-                                                         Geo g, Rates<T> keep, int* status) {
+                                                         Geo g, Rates<T> keep, int stages,
+                                                         int* status) {
   constexpr int Q = q_of(ST);
-  staged_rows<ST, S>(P, g, status, [&](const S* row, int r) {
+  staged_rows<ST, S>(P, g, stages, status, [&](const S* row, int r) {
     const int nx = g.nx;
     const int cbase = r * nx;
 #pragma unroll 1
@@ -239,6 +241,7 @@ void launch_staged(const StepArgs& a) {
     P.src[i] = i < Q ? (const S*)a.src + int64_t(i) * a.g.N : nullptr;
     P.dst[i] = i < Q ? (S*)a.dst + int64_t(i) * a.g.N : nullptr;
   }
+  const int stages = staged_stages(Q, a.g.nx, sizeof(S));
   const int smem = int(staged_smem_bytes(Q, a.g.nx, sizeof(S)));
   const int rows = a.g.ny * a.g.nz;
   constexpr bool half = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
@@ -251,7 +254,7 @@ void launch_staged(const StepArgs& a) {
     }
     Rates<P2> k2;
     for (int k = 0; k < 6; ++k) k2.om[k] = P2(1.0 - a.rates[k]);
-    kern<<<staged_grid(kern, smem, rows), STG_NT, smem, a.stream>>>(P, a.g, k2, a.status);
+    kern<<<staged_grid(kern, smem, rows), STG_NT, smem, a.stream>>>(P, a.g, k2, stages, a.status);
   } else {
     auto kern = k_pull_staged<ST, S, T, SPACE, REG>;
     static bool attr = false;
@@ -261,7 +264,8 @@ void launch_staged(const StepArgs& a) {
     }
     Rates<T> keep;
     for (int k = 0; k < 6; ++k) keep.om[k] = T(1.0 - a.rates[k]);
-    kern<<<staged_grid(kern, smem, rows), STG_NT, smem, a.stream>>>(P, a.g, keep, a.status);
+    kern<<<staged_grid(kern, smem, rows), STG_NT, smem, a.stream>>>(P, a.g, keep, stages,
+                                                                    a.status);
   }
 }
 
