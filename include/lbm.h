@@ -244,8 +244,9 @@ int lbm_set_stream(lbm_ctx* ctx, void* stream);
  *   LBM_STEP_DIRECT: each thread loads its cells' q populations from
  *     global memory (one grid of 128-thread CTAs over all cells).
  *   LBM_STEP_STAGED: a persistent CTA copies, per x-row of cells, the q
- *     source rows into shared memory with bulk asynchronous copies (two to
- *     four rows in flight) and collides from there.  Needs pull streaming,
+ *     source rows into shared memory with bulk asynchronous copies (two
+ *     rows in flight) and collides from there.  Measured slower than
+ *     LBM_STEP_DIRECT on B300, so AUTO does not choose it.  Needs pull streaming,
  *     deviation arithmetic, Nx * element size a multiple of 16 bytes and
  *     2 * q * Nx * element size <= 110 KiB (FP16/BF16: Nx <= 1024 for D3Q27;
  *     FP32: Nx <= 512); otherwise LBM_ERR_UNSUPPORTED.

@@ -288,15 +288,15 @@ __global__ void __launch_bounds__(128)
 
 // ------------------------------------------- tensor-core network (FP32)
 // The three layers run on the tensor cores for the 128 cells of a CTA at
-// once: layer l is D = A * B^T with A = [a_hi | a_lo] (128 x 2K, row = cell)
-// and B = [W | W] (N x 2K), where a_hi = bf16(a) and a_lo = bf16(a - a_hi)
-// split each FP32 activation into two BF16 values.  The weights are BF16
-// values, so each product is exact and the sum runs in FP32 in tensor
-// memory; the split leaves a relative residual below 2^-17 per activation,
-// which keeps the rates within ~1e-5 of the FP32 CUDA-core network (the
-// populations far closer).  Layer 1 pads the 7 inputs to 8 (K = 16), layer
-// 3 pads the 4 outputs to N = 16.
-constexpr int TC_K1 = 16, TC_K2 = 2 * NH, TC_N3 = 16;
+// once: layer l is D = A * B^T with A = [a_0 | a_1 | a_2] (128 x 3K, row =
+// cell) and B = [W | W | W] (N x 3K), where a_0 = bf16(a), a_1 = bf16(a -
+// a_0), a_2 = bf16(a - a_0 - a_1) split each FP32 activation into three
+// BF16 values.  The weights are BF16 values, so every product is exact and
+// the sum runs in FP32 in tensor memory; the split leaves a relative
+// residual below 2^-26 per activation, under FP32's own rounding.  Layer 1
+// pads the 7 inputs to 8 and its K = 24 to 32 (zero columns), layer 3 pads
+// the 4 outputs to N = 16.
+constexpr int TC_K1 = 32, TC_K2 = 3 * NH, TC_N3 = 16;
 constexpr int TC_B1 = 0, TC_B2 = TC_B1 + NH * TC_K1, TC_B3 = TC_B2 + NH * TC_K2;
 constexpr int TC_BELEMS = TC_B3 + TC_N3 * TC_K2;
 constexpr int TC_BOFF_BYTES = ((NSMEM * 4 + 127) / 128) * 128;  // packed B after the floats
@@ -312,34 +312,43 @@ inline void pack_tc_weights(const float* P, uint16_t* out) {
   for (int k = 0; k < TC_BELEMS; ++k) out[k] = 0;
   for (int n = 0; n < NH; ++n)
     for (int k = 0; k < NIN; ++k)
-      for (int h = 0; h < 2; ++h)
+      for (int h = 0; h < 3; ++h)
         out[TC_B1 + umma::kmajor_offset(n, h * 8 + k, TC_K1)] = bits(P[OW1 + n * NIN + k]);
   for (int n = 0; n < NH; ++n)
     for (int k = 0; k < NH; ++k)
-      for (int h = 0; h < 2; ++h)
+      for (int h = 0; h < 3; ++h)
         out[TC_B2 + umma::kmajor_offset(n, h * NH + k, TC_K2)] = bits(P[OW2 + n * NH + k]);
   for (int n = 0; n < NOUT; ++n)
     for (int k = 0; k < NH; ++k)
-      for (int h = 0; h < 2; ++h)
+      for (int h = 0; h < 3; ++h)
         out[TC_B3 + umma::kmajor_offset(n, h * NH + k, TC_K2)] = bits(P[OW3 + n * NH + k]);
 }
 
-// row `r` of an A operand: hi parts in columns [0, KH), lo parts in [KH, 2 KH)
-template <int KH>
+// row `r` of an A operand with K columns: the three BF16 parts of v in
+// columns [0, KH), [KH, 2 KH), [2 KH, 3 KH); columns from 3 KH on are zero
+template <int KH, int K>
 __device__ __forceinline__ void write_split(__nv_bfloat16* A, int r, const float (&v)[KH]) {
 #pragma unroll
   for (int kc = 0; kc < KH / 8; ++kc) {
-    __align__(16) __nv_bfloat16 hi[8], lo[8];
+    __align__(16) __nv_bfloat16 p0[8], p1[8], p2[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      hi[e] = __float2bfloat16_rn(v[kc * 8 + e]);
-      lo[e] = __float2bfloat16_rn(v[kc * 8 + e] - __bfloat162float(hi[e]));
+      const float a = v[kc * 8 + e];
+      p0[e] = __float2bfloat16_rn(a);
+      const float r1 = a - __bfloat162float(p0[e]);  // exact
+      p1[e] = __float2bfloat16_rn(r1);
+      p2[e] = __float2bfloat16_rn(r1 - __bfloat162float(p1[e]));
     }
-    *reinterpret_cast<uint4*>(A + umma::kmajor_offset(r, kc * 8, 2 * KH)) =
-        *reinterpret_cast<const uint4*>(hi);
-    *reinterpret_cast<uint4*>(A + umma::kmajor_offset(r, KH + kc * 8, 2 * KH)) =
-        *reinterpret_cast<const uint4*>(lo);
+    *reinterpret_cast<uint4*>(A + umma::kmajor_offset(r, kc * 8, K)) =
+        *reinterpret_cast<const uint4*>(p0);
+    *reinterpret_cast<uint4*>(A + umma::kmajor_offset(r, KH + kc * 8, K)) =
+        *reinterpret_cast<const uint4*>(p1);
+    *reinterpret_cast<uint4*>(A + umma::kmajor_offset(r, 2 * KH + kc * 8, K)) =
+        *reinterpret_cast<const uint4*>(p2);
   }
+#pragma unroll
+  for (int kc = 3 * KH / 8; kc < K / 8; ++kc)
+    *reinterpret_cast<uint4*>(A + umma::kmajor_offset(r, kc * 8, K)) = make_uint4(0, 0, 0, 0);
 }
 
 // One layer: every thread has written its A row; thread 0 issues the K/16
@@ -373,8 +382,7 @@ __global__ void __launch_bounds__(128)
                       Rates<float> keep, const float* __restrict__ params, int* status) {
   __shared__ float sp[NSMEM];
   __shared__ __align__(128) __nv_bfloat16 sB[TC_BELEMS];
-  __shared__ __align__(128) __nv_bfloat16 sA1[128 * TC_K1];
-  __shared__ __align__(128) __nv_bfloat16 sA2[128 * TC_K2];
+  __shared__ __align__(128) __nv_bfloat16 sA[128 * TC_K2];  // A of every layer
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_base;
   const int t = threadIdx.x, warp = t / 32;
@@ -423,18 +431,18 @@ __global__ void __launch_bounds__(128)
   }
   bool waited = true;
   float acc[32], h[32];
-  write_split<8>(sA1, t, xin);
-  waited &= tc_layer<TC_K1, NH>(sA1, sB + TC_B1, tmem, &bar, 0);
+  write_split<8, TC_K1>(sA, t, xin);
+  waited &= tc_layer<TC_K1, NH>(sA, sB + TC_B1, tmem, &bar, 0);
   umma::tmem_ld32(tlane, acc);
 #pragma unroll
   for (int j = 0; j < NH; ++j) h[j] = tanhf(acc[j] + sp[OB1 + j]);
-  write_split<NH>(sA2, t, h);
-  waited &= tc_layer<TC_K2, NH>(sA2, sB + TC_B2, tmem, &bar, 1);
+  write_split<NH, TC_K2>(sA, t, h);
+  waited &= tc_layer<TC_K2, NH>(sA, sB + TC_B2, tmem, &bar, 1);
   umma::tmem_ld32(tlane, acc);
 #pragma unroll
   for (int j = 0; j < NH; ++j) h[j] = tanhf(acc[j] + sp[OB2 + j]);
-  write_split<NH>(sA2, t, h);
-  waited &= tc_layer<TC_K2, TC_N3>(sA2, sB + TC_B3, tmem, &bar, 0);
+  write_split<NH, TC_K2>(sA, t, h);
+  waited &= tc_layer<TC_K2, TC_N3>(sA, sB + TC_B3, tmem, &bar, 0);
   float z16[16];
   umma::tmem_ld16(tlane, z16);
   Rates<float> k = keep;

@@ -22,7 +22,7 @@ enum { VARIANT_DIRECT = 0, VARIANT_STAGED = 1 };
 // shared-memory staged pull kernel (lbm_staged.cuh); the stage cap is a
 // compile-time tuning knob
 #ifndef LBM_STG_MAX_STAGES
-#define LBM_STG_MAX_STAGES 4
+#define LBM_STG_MAX_STAGES 2  // measured on B300: more stages cost CTAs per SM
 #endif
 constexpr int STG_MIN_STAGES = 2, STG_MAX_STAGES = LBM_STG_MAX_STAGES;  // rows in flight per CTA
 constexpr int STG_MAX_SMEM = 110 * 1024;               // stage bytes per CTA: two CTAs per SM

@@ -6,8 +6,9 @@
 // persistent CTA owns rows r = blockIdx.x + k * gridDim.x; for each it
 // issues q one-dimensional bulk copies global -> shared (one per direction,
 // the full row, so the x wrap is resolved by indexing in shared memory) that
-// complete on one mbarrier, and keeps `stages` rows (2 to 4, as many as fit
-// the shared-memory budget) in flight while it collides the current one.  The copies need no registers and no warps, so
+// complete on one mbarrier, and keeps `stages` rows (up to the compile-time
+// cap, as many as fit the shared-memory budget) in flight while it collides
+// the current one.  The copies need no registers and no warps, so
 // the bytes in flight per SM no longer depend on the occupancy of the
 // (register-heavy) collision.  Stores go straight from registers to global
 // memory, coalesced along x.

@@ -52,3 +52,36 @@ def test_tgv_plateau_short():
     # than Eq. 2.6 as written
     for m in ("R-O-MRT", "R-CM", "R-K"):
         assert end[f"{m}/zc_feq_deviation"] <= 10 * end[f"{m}/zc_feq"], (m, end)
+
+
+def _table3():
+    """Table 3 values from tests/golden/table3_tgv_plateaus.txt."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table3_tgv_plateaus.txt")
+    cols = ("absolute", "zc_feq", "zc_dfeq")
+    out = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, *vals = line.split()
+        for c, v in zip(cols, vals):
+            if v != "-":
+                out[f"{name}/{c}"] = float(v)
+    return out
+
+
+@pytest.mark.slow
+def test_tgv_plateau_table3_orders_of_magnitude():
+    """The full Table 3 case (L = 256, 200 000 steps) for SRT and R-K, the
+    two methods where the paper finds storage matters most: every plateau
+    the paper prints for them within 1.5 decades of ours."""
+    B.build()
+    paper = _table3()
+    res = A.tgv_plateau(n=256, steps=200_000, every=50_000, methods=["SRT", "R-K"],
+                        forms=["absolute", "zc_feq", "zc_dfeq"])
+    checked = 0
+    for key, ours in ((k, v[-1]) for k, v in res["runs"].items()):
+        if key in paper:
+            assert abs(np.log10(ours / paper[key])) < 1.5, (key, ours, paper[key])
+            checked += 1
+    assert checked == 4
