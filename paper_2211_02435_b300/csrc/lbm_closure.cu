@@ -18,6 +18,12 @@
 
 namespace lbm {
 
+// FP32 inference network: tensor cores (1) or CUDA cores (0); a compile-time
+// choice, measured on B300
+#ifndef LBM_CLOSURE_TC
+#define LBM_CLOSURE_TC 0
+#endif
+
 constexpr int NIN = LBM_CLOSURE_NIN, NH = LBM_CLOSURE_NHIDDEN, NOUT = LBM_CLOSURE_NOUT;
 constexpr int NPARAM = LBM_CLOSURE_NPARAM;
 constexpr int OW1 = 0, OB1 = OW1 + NH * NIN, OW2 = OB1 + NH, OB2 = OW2 + NH * NH;
@@ -25,10 +31,25 @@ constexpr int OW3 = OB2 + NH, OB3 = OW3 + NOUT * NH;
 static_assert(OB3 + NOUT == NPARAM, "parameter layout");
 constexpr int NSMEM = NPARAM + 2 * NIN;  // parameters, shift, scale
 
+// FP32 tanh from the identity tanh|x| = (1 - t) / (1 + t), t = e^(-2|x|) in
+// (0, 1], with the sign of x restored: the fast exponential never overflows
+// and the quotient's denominator stays in [1, 2].  Absolute error a few 1e-8
+// on the whole line (near 0 the relative error grows while the absolute error
+// stays at the rounding of 1), exactly +-1 once t underflows, NaN for NaN.
+// A third of the instructions of the library tanhf, which was a large part
+// of the network's cost.  FP64 keeps tanh.
 template <class T>
 LBM_D T tanh_t(T x) {
-  if constexpr (std::is_same<T, float>::value) return tanhf(x);
-  else return tanh(x);
+  if constexpr (std::is_same<T, float>::value) {
+#ifdef __CUDA_ARCH__
+    const float t = __expf(-2.0f * fabsf(x));
+    return copysignf(__fdividef(1.0f - t, 1.0f + t), x);
+#else
+    return tanhf(x);
+#endif
+  } else {
+    return tanh(x);
+  }
 }
 template <class T>
 LBM_D T exp_t(T x) {
@@ -56,19 +77,47 @@ LBM_D void mlp_forward(const T* P, const T (&raw)[NIN], T (&x)[NIN], T (&h1)[NH]
     x[i] = (raw[i] - shift[i]) * scale[i];
     ok = ok && isfinite(x[i]);
   }
+  if constexpr (std::is_same<T, float>::value) {
 #pragma unroll
-  for (int r = 0; r < NH; ++r) {
-    T a = P[OB1 + r];
+    for (int r = 0; r < NH; r += 2) {
+      float2 a = make_float2(P[OB1 + r], P[OB1 + r + 1]);
 #pragma unroll
-    for (int c = 0; c < NIN; ++c) a += P[OW1 + r * NIN + c] * x[c];
-    h1[r] = tanh_t(a);
+      for (int c = 0; c < NIN; ++c)
+        a = ffma2(make_float2(P[OW1 + r * NIN + c], P[OW1 + (r + 1) * NIN + c]),
+                  make_float2(x[c], x[c]), a);
+      h1[r] = tanh_t(a.x);
+      h1[r + 1] = tanh_t(a.y);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < NH; ++r) {
+      T a = P[OB1 + r];
+#pragma unroll
+      for (int c = 0; c < NIN; ++c) a += P[OW1 + r * NIN + c] * x[c];
+      h1[r] = tanh_t(a);
+    }
   }
+  if constexpr (std::is_same<T, float>::value) {
+    // two rows per packed fused multiply-add: each lane runs the same FP32
+    // chain as the scalar loop, so the results are bitwise equal
 #pragma unroll
-  for (int r = 0; r < NH; ++r) {
-    T a = P[OB2 + r];
+    for (int r = 0; r < NH; r += 2) {
+      float2 a = make_float2(P[OB2 + r], P[OB2 + r + 1]);
 #pragma unroll
-    for (int c = 0; c < NH; ++c) a += P[OW2 + r * NH + c] * h1[c];
-    h2[r] = tanh_t(a);
+      for (int c = 0; c < NH; ++c)
+        a = ffma2(make_float2(P[OW2 + r * NH + c], P[OW2 + (r + 1) * NH + c]),
+                  make_float2(h1[c], h1[c]), a);
+      h2[r] = tanh_t(a.x);
+      h2[r + 1] = tanh_t(a.y);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < NH; ++r) {
+      T a = P[OB2 + r];
+#pragma unroll
+      for (int c = 0; c < NH; ++c) a += P[OW2 + r * NH + c] * h1[c];
+      h2[r] = tanh_t(a);
+    }
   }
 #pragma unroll
   for (int k = 0; k < NOUT; ++k) {
@@ -435,12 +484,12 @@ __global__ void __launch_bounds__(128)
   waited &= tc_layer<TC_K1, NH>(sA, sB + TC_B1, tmem, &bar, 0);
   umma::tmem_ld32(tlane, acc);
 #pragma unroll
-  for (int j = 0; j < NH; ++j) h[j] = tanhf(acc[j] + sp[OB1 + j]);
+  for (int j = 0; j < NH; ++j) h[j] = tanh_t(acc[j] + sp[OB1 + j]);
   write_split<NH, TC_K2>(sA, t, h);
   waited &= tc_layer<TC_K2, NH>(sA, sB + TC_B2, tmem, &bar, 1);
   umma::tmem_ld32(tlane, acc);
 #pragma unroll
-  for (int j = 0; j < NH; ++j) h[j] = tanhf(acc[j] + sp[OB2 + j]);
+  for (int j = 0; j < NH; ++j) h[j] = tanh_t(acc[j] + sp[OB2 + j]);
   write_split<NH, TC_K2>(sA, t, h);
   waited &= tc_layer<TC_K2, TC_N3>(sA, sB + TC_B3, tmem, &bar, 0);
   float z16[16];
@@ -749,8 +798,13 @@ void launch_closure_step(const StepArgs& a, const void* closure) {
   } else {
     Rates<float> keep;
     for (int k = 0; k < 6; ++k) keep.om[k] = float(1.0 - a.rates[k]);
+#if LBM_CLOSURE_TC
     k_closure_pull_tc<<<grid, 128, 0, a.stream>>>((const float*)a.src, (float*)a.dst, a.g, keep,
                                                    (const float*)closure, a.status);
+#else
+    k_closure_pull<float, float><<<grid, 128, 0, a.stream>>>((const float*)a.src, (float*)a.dst,
+                                                             a.g, keep, (const float*)closure);
+#endif
   }
 }
 
