@@ -83,6 +83,9 @@ def lib():
         L.lbm_oracle_init.argtypes = [m, i64, d, d, d]
         L.lbm_oracle_step.argtypes = [m, i64, d, ctypes.c_int64, ctypes.c_int]
         L.lbm_oracle_macroscopic.argtypes = [m, i64, d, d, d]
+        L.lbm_oracle_collide_forced.argtypes = [m, ctypes.c_int64, d, d, d]
+        L.lbm_oracle_step_forced.argtypes = [m, i64, d, d, ctypes.c_int64, ctypes.c_int]
+        L.lbm_oracle_macroscopic_forced.argtypes = [m, i64, d, d, d, d]
         L.lbm_oracle_closure_features.argtypes = [ctypes.c_int, d, ctypes.c_double, d]
         L.lbm_oracle_closure_mlp.argtypes = [d, d, d, d, d]
         L.lbm_oracle_closure_step.argtypes = [m, i64, d, d, d, d, ctypes.c_int]
@@ -165,6 +168,19 @@ def collide(m, df):
     return out.reshape(df.shape)
 
 
+def collide_forced(m, df, force):
+    """Collide cells under a body force (Guo; see lbm_oracle.h): df [ncells, q],
+    force [ncells, 3] (or [3] for one cell)."""
+    df = _f64(df)
+    flat = df.reshape(-1, Q_OF[m.stencil])
+    F = _f64(np.broadcast_to(np.asarray(force, dtype=np.float64).reshape(-1, 3),
+                             (flat.shape[0], 3))).copy()
+    out = np.empty_like(flat)
+    _check(lib().lbm_oracle_collide_forced(ctypes.byref(m), flat.shape[0], _dp(flat), _dp(F),
+                                           _dp(out)))
+    return out.reshape(df.shape)
+
+
 def equilibrium(m, rho, u):
     """Method equilibrium deviations for rho[n], u[n,3] -> [n, q]."""
     rho = _f64(np.atleast_1d(rho))
@@ -200,6 +216,43 @@ def step(m, dims, df, nsteps, nthreads=0):
     _check(lib().lbm_oracle_step(ctypes.byref(m), dm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                  _dp(out), int(nsteps), int(nthreads)))
     return out
+
+
+def _force_field(m, dims, force):
+    """Force as SoA [D, N] (D = 2 for D2Q9); force may be a constant vector."""
+    dm = _dims(dims)
+    N = int(np.prod(dm))
+    d = 2 if m.stencil == D2Q9 else 3
+    F = np.asarray(force, dtype=np.float64)
+    if F.size == 3 or F.size == d:
+        F = np.repeat(F.reshape(-1)[:d, None], N, axis=1)
+    return np.ascontiguousarray(F.reshape(d, N))
+
+
+def step_forced(m, dims, df, force, nsteps, nthreads=0):
+    """step() under a time-constant body force (a vector or a [D, ...] field)."""
+    dm = _dims(dims)
+    out = _f64(df).copy()
+    F = _force_field(m, dims, force)
+    _check(lib().lbm_oracle_step_forced(ctypes.byref(m),
+                                        dm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                        _dp(out), _dp(F), int(nsteps), int(nthreads)))
+    return out
+
+
+def macroscopic_forced(m, dims, df, force):
+    """(rho, u) with the fluid velocity u = (j + F/2) / rho of a forced state."""
+    dm = _dims(dims)
+    N = int(np.prod(dm))
+    d = 2 if m.stencil == D2Q9 else 3
+    rho = np.empty(N)
+    u = np.zeros((d, N))
+    F = _force_field(m, dims, force)
+    _check(lib().lbm_oracle_macroscopic_forced(
+        ctypes.byref(m), dm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(_f64(df)),
+        _dp(F), _dp(rho), _dp(u)))
+    shp = (dm[2], dm[1], dm[0])
+    return rho.reshape(shp), u.reshape((d,) + shp)
 
 
 def macroscopic(m, dims, df):

@@ -371,8 +371,61 @@ static void central_matrix(const lattice_t* L, const double* u,
                 ipow(L->xi[i][2] - u[2], L->expo[k][2]);
 }
 
-static int collide_cell(const lattice_t* L, const lbm_oracle_method* m,
-                        const double* df, double* out) {
+/* Guo's discrete source term of a body force F at velocity u:
+ * S_i = w_i [ (xi_i - u).F / c_s^2 + (xi_i.u)(xi_i.F) / c_s^4 ],  c_s^2 = 1/3.
+ * Its zeroth moment is 0 and its first moment F. */
+static void guo_source(const lattice_t* L, const double* u, const double* F,
+                       double* S) {
+  for (int i = 0; i < L->q; ++i) {
+    double cu = 0.0, cf = 0.0, uf = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      cu += L->xi[i][d] * u[d];
+      cf += L->xi[i][d] * F[d];
+      uf += u[d] * F[d];
+    }
+    S[i] = L->w[i] * (3.0 * (cf - uf) + 9.0 * cu * cf);
+  }
+}
+
+/* relax() plus the collision-space source of Eq. 2.4:
+ * q* = q + S (q_eq - q) + (I - S/2) P sF, with sF the monomial moments of the
+ * population source (conserved rows: rate 0, factor 1) */
+static void relax_forced(const lattice_t* L, const lbm_oracle_method* m,
+                         const double P[QMAX][QMAX],
+                         const double Pinv[QMAX][QMAX], const double* v,
+                         const double* veq, const double* sF, double* vout) {
+  double qv[QMAX], qe[QMAX], qf[QMAX], qs[QMAX];
+  matvec(L->q, P, v, qv);
+  matvec(L->q, P, veq, qe);
+  matvec(L->q, P, sF, qf);
+  for (int r = 0; r < L->q; ++r) {
+    const double om = rate_of(m, L->group[r]);
+    qs[r] = qv[r] + om * (qe[r] - qv[r]) + (1.0 - 0.5 * om) * qf[r];
+  }
+  matvec(L->q, Pinv, qs, vout);
+}
+
+/* central-moment force (first-order rows only): v_k += F_d for the
+ * monomial x_d of degree 1 */
+static void add_first_order(const lattice_t* L, const double* F, double* v) {
+  for (int k = 0; k < L->q; ++k)
+    if (L->deg[k] == 1) {
+      const int* e = L->expo[k];
+      v[k] += F[e[0] ? 0 : (e[1] ? 1 : 2)];
+    }
+}
+
+/* One cell.  F = NULL: no force.  With a body force F (Eq. 2.1a source term,
+ * Eq. 2.4 q^F), the equilibrium velocity is u = (j + F/2) / rho and
+ *   populations (SRT): f* = f + w (f_eq - f) + (1 - w/2) S      (Guo)
+ *   raw moments:       q^F = (I - S/2) P M S                   (Guo, MRT)
+ *   central moments:   moments about u; q^F = F on the first-order rows
+ *                      only (kappa_1 = -F/2 before, +F/2 after, Sec. 4.2)
+ *   cumulants:         orders >= 2 are translation invariant and relax as
+ *                      without force; the first-order cumulant (the mean
+ *                      velocity) leaves the collision as (j + F) / rho. */
+static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
+                          const double* df, const double* F, double* out) {
   const int q = L->q;
   /* conserved quantities from the deviations, Eq. 2.3, rho0 = 1 */
   double drho = 0.0, j[3] = {0, 0, 0}, u[3];
@@ -381,7 +434,16 @@ static int collide_cell(const lattice_t* L, const lbm_oracle_method* m,
     for (int d = 0; d < 3; ++d) j[d] += L->xi[i][d] * df[i];
   }
   const double rho = 1.0 + drho;
-  for (int d = 0; d < 3; ++d) u[d] = j[d] / rho;
+  static const double zero_F[3] = {0, 0, 0};
+  const int forced = F != NULL;
+  if (!forced) F = zero_F;
+  const int shift = forced && m->space != LBM_ORACLE_SPACE_CUMULANT;
+  for (int d = 0; d < 3; ++d) u[d] = (j[d] + (shift ? 0.5 * F[d] : 0.0)) / rho;
+  double S[QMAX] = {0}, sF[QMAX] = {0};
+  if (forced) {
+    guo_source(L, u, F, S);
+    matvec(q, L->M, S, sF);
+  }
   const int delta = m->equilibrium == LBM_ORACLE_EQ_DELTA;
   double f[QMAX] = {0}, tmp[QMAX] = {0}, tmp2[QMAX] = {0}, veq[QMAX] = {0},
          vout[QMAX] = {0};
@@ -405,6 +467,7 @@ static int collide_cell(const lattice_t* L, const lbm_oracle_method* m,
           double fi = df[i] + L->w[i];
           out[i] = fi + om * (tmp[i] - fi) - L->w[i];
         }
+        if (forced) out[i] += (1.0 - 0.5 * om) * S[i];
       }
       return 0;
     }
@@ -414,14 +477,14 @@ static int collide_cell(const lattice_t* L, const lbm_oracle_method* m,
         for (int k = 0; k < q; ++k)
           veq[k] = maxwell_raw_moment(L->expo[k], rho, u, 1) -
                    maxwell_raw_moment(L->expo[k], 1.0, zero_u, 1);
-        relax(L, m, L->Praw, L->Prawinv, tmp, veq, vout);
+        relax_forced(L, m, L->Praw, L->Prawinv, tmp, veq, sF, vout);
         matvec(q, L->Minv, vout, out);
       } else { /* Eq. 2.6 */
         for (int i = 0; i < q; ++i) f[i] = df[i] + L->w[i];
         matvec(q, L->M, f, tmp);
         for (int k = 0; k < q; ++k)
           veq[k] = maxwell_raw_moment(L->expo[k], rho, u, 1);
-        relax(L, m, L->Praw, L->Prawinv, tmp, veq, vout);
+        relax_forced(L, m, L->Praw, L->Prawinv, tmp, veq, sF, vout);
         matvec(q, L->Minv, vout, tmp2);
         for (int i = 0; i < q; ++i) out[i] = tmp2[i] - L->w[i];
       }
@@ -438,6 +501,7 @@ static int collide_cell(const lattice_t* L, const lbm_oracle_method* m,
         for (int k = 0; k < q; ++k)
           veq[k] = maxwell_central_moment(L->expo[k], rho) - k0[k];
         relax(L, m, L->Pcm, L->Pcminv, tmp, veq, vout);
+        add_first_order(L, F, vout);
         matvec(q, Kinv, vout, out);
       } else { /* Eq. 2.6 */
         for (int i = 0; i < q; ++i) f[i] = df[i] + L->w[i];
@@ -445,6 +509,7 @@ static int collide_cell(const lattice_t* L, const lbm_oracle_method* m,
         for (int k = 0; k < q; ++k)
           veq[k] = maxwell_central_moment(L->expo[k], rho);
         relax(L, m, L->Pcm, L->Pcminv, tmp, veq, vout);
+        add_first_order(L, F, vout);
         matvec(q, Kinv, vout, tmp2);
         for (int i = 0; i < q; ++i) out[i] = tmp2[i] - L->w[i];
       }
@@ -482,8 +547,11 @@ static int collide_cell(const lattice_t* L, const lbm_oracle_method* m,
       relax(L, m, L->Pcm, L->Pcminv, v, veq, vout);
       for (int k = 0; k < q; ++k) {
         const int* e = L->expo[k];
+        double mean = 0.0; /* post-collision mean velocity (j + F) / rho */
+        if (L->deg[k] == 1)
+          mean = forced ? v[k] + F[e[0] ? 0 : (e[1] ? 1 : 2)] / rho_a : v[k];
         c[e[0]][e[1]][e[2]] =
-            L->deg[k] >= 2 ? vout[k] / rho_a : (L->deg[k] == 1 ? v[k] : 1.0);
+            L->deg[k] >= 2 ? vout[k] / rho_a : (L->deg[k] == 1 ? mean : 1.0);
       }
       for (int k = 0; k < q; ++k) {
         tmp2[k] = L->deg[k] == 0
@@ -496,6 +564,11 @@ static int collide_cell(const lattice_t* L, const lbm_oracle_method* m,
     }
   }
   return -1;
+}
+
+static int collide_cell(const lattice_t* L, const lbm_oracle_method* m,
+                        const double* df, double* out) {
+  return collide_cell_f(L, m, df, NULL, out);
 }
 
 static int check_method(const lbm_oracle_method* m) {
@@ -620,6 +693,23 @@ int lbm_oracle_collide(const lbm_oracle_method* m, int64_t ncells,
   return 0;
 }
 
+int lbm_oracle_collide_forced(const lbm_oracle_method* m, int64_t ncells,
+                              const double* df_in, const double* force,
+                              double* df_out) {
+  int rc = check_method(m);
+  if (rc) return rc;
+  if (!force || m->space == LBM_ORACLE_SPACE_NONE) return -1;
+  const lattice_t* L = &g_lat[m->stencil];
+  for (int64_t c = 0; c < ncells; ++c) {
+    double tmp[QMAX], F[3] = {0, 0, 0};
+    for (int d = 0; d < L->d; ++d) F[d] = force[c * 3 + d];
+    rc = collide_cell_f(L, m, df_in + c * L->q, F, tmp);
+    if (rc) return rc;
+    memcpy(df_out + c * L->q, tmp, sizeof(double) * L->q);
+  }
+  return 0;
+}
+
 static void equilibrium_cell(const lattice_t* L, const lbm_oracle_method* m,
                              double rho, const double* u, double* out) {
   /* raw-moment methods relax to the truncated equilibrium; central-moment
@@ -662,8 +752,15 @@ int lbm_oracle_init(const lbm_oracle_method* m, const int64_t* dims,
 
 int lbm_oracle_step(const lbm_oracle_method* m, const int64_t* dims,
                     double* df, int64_t nsteps, int nthreads) {
+  return lbm_oracle_step_forced(m, dims, df, NULL, nsteps, nthreads);
+}
+
+int lbm_oracle_step_forced(const lbm_oracle_method* m, const int64_t* dims,
+                           double* df, const double* force, int64_t nsteps,
+                           int nthreads) {
   int rc = check_method(m);
   if (rc) return rc;
+  if (force && m->space == LBM_ORACLE_SPACE_NONE) return -1;
   const lattice_t* L = &g_lat[m->stencil];
   const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
   if (nx <= 0 || ny <= 0 || nz <= 0) return -1;
@@ -682,9 +779,11 @@ int lbm_oracle_step(const lbm_oracle_method* m, const int64_t* dims,
 #pragma omp parallel for schedule(static) reduction(| : err)
     for (int64_t c = 0; c < N; ++c) {
       const int64_t x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
-      double in[QMAX], post[QMAX];
+      double in[QMAX], post[QMAX], F[3] = {0, 0, 0};
       for (int i = 0; i < q; ++i) in[i] = df[i * N + c];
-      if (collide_cell(L, m, in, post)) err |= 1;
+      if (force)
+        for (int d = 0; d < L->d; ++d) F[d] = force[d * N + c];
+      if (collide_cell_f(L, m, in, force ? F : NULL, post)) err |= 1;
       /* Eq. 2.1b: f_i(x + xi_i, t + 1) = f*_i(x, t), periodic */
       for (int i = 0; i < q; ++i) {
         int64_t xd = (x + L->xi[i][0] + nx) % nx;
@@ -701,6 +800,12 @@ int lbm_oracle_step(const lbm_oracle_method* m, const int64_t* dims,
 
 int lbm_oracle_macroscopic(const lbm_oracle_method* m, const int64_t* dims,
                            const double* df, double* rho, double* u) {
+  return lbm_oracle_macroscopic_forced(m, dims, df, NULL, rho, u);
+}
+
+int lbm_oracle_macroscopic_forced(const lbm_oracle_method* m,
+                                  const int64_t* dims, const double* df,
+                                  const double* force, double* rho, double* u) {
   if (!m || build_lattice(m->stencil)) return -1;
   const lattice_t* L = &g_lat[m->stencil];
   const int64_t N = dims[0] * dims[1] * dims[2];
@@ -711,7 +816,9 @@ int lbm_oracle_macroscopic(const lbm_oracle_method* m, const int64_t* dims,
       for (int d = 0; d < 3; ++d) j[d] += L->xi[i][d] * df[i * N + c];
     }
     rho[c] = 1.0 + drho;
-    for (int d = 0; d < L->d; ++d) u[d * N + c] = j[d] / rho[c];
+    /* with a body force the fluid velocity is (j + F/2) / rho (Guo) */
+    for (int d = 0; d < L->d; ++d)
+      u[d * N + c] = (j[d] + (force ? 0.5 * force[d * N + c] : 0.0)) / rho[c];
   }
   return 0;
 }

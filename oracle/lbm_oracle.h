@@ -123,6 +123,29 @@ int lbm_oracle_step(const lbm_oracle_method* m, const int64_t* dims,
 int lbm_oracle_macroscopic(const lbm_oracle_method* m, const int64_t* dims,
                            const double* df, double* rho, double* u);
 
+/* Body force (source term f^F of Eq. 2.1a, q^F of Eq. 2.4).  The paper
+ * names Guo's and He's models without writing them out; this oracle follows
+ * Guo: equilibrium velocity u = (j + F/2) / rho and the population source
+ * S_i = w_i [(xi_i - u).F / c_s^2 + (xi_i.u)(xi_i.F) / c_s^4], entering as
+ *   SRT:        f* = f + w (f_eq - f) + (1 - w/2) S
+ *   raw MRT:    q^F = (I - S/2) P M S   (conserved rows: factor 1)
+ *   central:    moments about u, q^F = F on the first-order rows only
+ *               (kappa_1 = -F/2 before and +F/2 after the collision)
+ *   cumulant:   cumulants of order >= 2 relax as without force; the
+ *               first-order cumulant (mean velocity) leaves as (j + F)/rho.
+ * collide: force[ncells][3] cell-major (z ignored for D2Q9).  step /
+ * macroscopic: force SoA [D][N] (D = 2 for D2Q9, else 3), constant in time,
+ * NULL = none; macroscopic then returns the fluid velocity (j + F/2)/rho. */
+int lbm_oracle_collide_forced(const lbm_oracle_method* m, int64_t ncells,
+                              const double* df_in, const double* force,
+                              double* df_out);
+int lbm_oracle_step_forced(const lbm_oracle_method* m, const int64_t* dims,
+                           double* df, const double* force, int64_t nsteps,
+                           int nthreads);
+int lbm_oracle_macroscopic_forced(const lbm_oracle_method* m,
+                                  const int64_t* dims, const double* df,
+                                  const double* force, double* rho, double* u);
+
 /* ------------------------------------------------------------------ */
 /* Learned closure (not in the paper): a per-cell MLP 7 -> 32 -> 32 -> 4 */
 /* sets the relaxation rates of orders 3..6 of the cumulant collision.    */

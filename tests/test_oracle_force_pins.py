@@ -1,0 +1,119 @@
+"""Pins of the oracle's body-force collision (source term of Eq. 2.1a, q^F of
+Eq. 2.4; Guo's model, see oracle/lbm_oracle.h) against what the physics
+fixes independently of the formulas typed in the oracle:
+
+* a body force changes the momentum of every cell by exactly F per step and
+  leaves its mass unchanged (any force model);
+* with F = 0 the forced collision is the plain one;
+* for cumulants with every rate 1 the collision lands on the method's own
+  equilibrium at the advanced velocity (j + F) / rho;
+* Kolmogorov flow: the steady state of a periodic shear force
+  F_x = F0 sin(k y) is u_x = F0 / (rho nu k^2) sin(k y) for the
+  incompressible Navier-Stokes equations, nu = (1/omega - 1/2) / 3; every
+  collision space reaches it within the lattice's O(k^2) error;
+* total momentum of a periodic lattice grows by N F per step.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+SPACES = [O.SPACE_POPULATIONS, O.SPACE_RAW, O.SPACE_CENTRAL, O.SPACE_CUMULANT]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    O.build()
+
+
+def random_cells(st, n, seed):
+    rng = np.random.default_rng(seed)
+    _, w, _ = O.lattice(st)
+    m = O.method(st, O.SPACE_RAW, O.EQ_DELTA, [1.0] * 6)
+    rho = 1.0 + 0.02 * rng.standard_normal(n)
+    u = 0.05 * rng.standard_normal((n, 3))
+    if st == O.D2Q9:
+        u[:, 2] = 0
+    df = O.equilibrium(m, rho, u)
+    return df + w[None, :] * 3e-3 * rng.standard_normal(df.shape)
+
+
+def moments(st, df):
+    xi = O.lattice(st)[0]
+    return df.sum(1), df @ xi
+
+
+@pytest.mark.parametrize("eq", [O.EQ_DELTA, O.EQ_ABSOLUTE])
+@pytest.mark.parametrize("space", SPACES)
+@pytest.mark.parametrize("st", [O.D2Q9, O.D3Q19, O.D3Q27])
+def test_force_adds_exactly_F_to_the_momentum(st, space, eq):
+    if space == O.SPACE_CUMULANT and eq == O.EQ_DELTA:
+        pytest.skip("inadmissible")
+    df = random_cells(st, 16, seed=st * 10 + space)
+    rng = np.random.default_rng(7)
+    F = 1e-3 * rng.standard_normal((16, 3))
+    if st == O.D2Q9:
+        F[:, 2] = 0
+    m = O.method(st, space, eq, [1.3, 1.1, 1.2, 1.4, 1.5, 1.6])
+    out = O.collide_forced(m, df, F)
+    rho0, j0 = moments(st, df)
+    rho1, j1 = moments(st, out)
+    assert np.abs(rho1 - rho0).max() < 1e-15
+    assert np.abs(j1 - (j0 + F)).max() < 1e-15
+    # no force: the plain collision
+    assert np.abs(O.collide_forced(m, df, np.zeros((16, 3))) - O.collide(m, df)).max() < 1e-16
+
+
+@pytest.mark.parametrize("st", [O.D3Q19, O.D3Q27])
+def test_cumulant_with_unit_rates_lands_on_the_shifted_equilibrium(st):
+    df = random_cells(st, 12, seed=3)
+    F = np.tile([2e-3, -1e-3, 5e-4], (12, 1))
+    m = O.method(st, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [1.0] * 6)
+    out = O.collide_forced(m, df, F)
+    rho, j = moments(st, df)
+    rho = 1.0 + rho
+    ref = O.equilibrium(m, rho, (j + F) / rho[:, None])
+    assert np.abs(out - ref).max() < 1e-15
+
+
+@pytest.mark.parametrize("space", SPACES)
+@pytest.mark.parametrize("st", [O.D2Q9, O.D3Q19, O.D3Q27])
+def test_kolmogorov_flow_steady_state(st, space):
+    ny = 32
+    dims = (1, ny, 1)
+    k = 2 * np.pi / ny
+    omega = 1.6
+    nu = (1.0 / omega - 0.5) / 3.0
+    F0 = 1e-6
+    y = np.arange(ny)
+    d = 2 if st == O.D2Q9 else 3
+    force = np.zeros((d, 1, ny, 1))
+    force[0, 0, :, 0] = F0 * np.sin(k * y)
+    eq = O.EQ_ABSOLUTE
+    m = O.method(st, space, eq, [omega] + [1.0] * 5)
+    rho0 = np.ones((1, ny, 1))
+    u0 = np.zeros((d, 1, ny, 1))
+    df = O.init(m, dims, rho0, u0)
+    steps = int(12 / (nu * k * k))  # e^-12 of the start-up transient left
+    df = O.step_forced(m, dims, df, force, steps)
+    _, u = O.macroscopic_forced(m, dims, df, force)
+    amp = F0 / (nu * k * k)
+    want = amp * np.sin(k * y)
+    err = np.abs(u[0, 0, :, 0] - want).max() / amp
+    assert err < 0.01, err  # O(k^2) lattice error: 0.4 - 0.6 % at L = 32
+    assert np.abs(u[1]).max() < 1e-6 * amp
+
+
+def test_total_momentum_grows_by_N_F_per_step():
+    st, dims = O.D3Q27, (6, 5, 4)
+    N = 6 * 5 * 4
+    F = np.array([1e-4, -2e-4, 3e-4])
+    for space in SPACES:
+        m = O.method(st, space, O.EQ_ABSOLUTE, [1.7, 1.0, 1.2, 1.1, 1.0, 1.3])
+        rng = np.random.default_rng(1)
+        u = 0.02 * rng.standard_normal((3, 4, 5, 6))
+        df = O.init(m, dims, np.ones((4, 5, 6)), u)
+        j0 = np.einsum("iz,id->d", df.reshape(27, -1), O.lattice(st)[0].astype(float))
+        out = O.step_forced(m, dims, df, F, 5)
+        j5 = np.einsum("iz,id->d", out.reshape(27, -1), O.lattice(st)[0].astype(float))
+        assert np.abs(j5 - (j0 + 5 * N * F)).max() < 1e-13, space
