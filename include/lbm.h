@@ -237,6 +237,30 @@ int lbm_set_rates(lbm_ctx* ctx, const double rates[6]);
 /* Change the stream later work is enqueued on. */
 int lbm_set_stream(lbm_ctx* ctx, void* stream);
 
+/* Body force: the source term f^F of Eq. 2.1a / q^F of Eq. 2.4.  The paper
+ * names Guo's and He's models without writing them out; this library
+ * implements Guo's: the equilibrium velocity is u = (j + F/2) / rho and,
+ * with S_i = w_i [(xi_i - u).F / c_s^2 + (xi_i.u)(xi_i.F) / c_s^4],
+ *   POPULATIONS (SRT): f* = f + w (f_eq - f) + (1 - w/2) S
+ *   RAW:      q^F = (I - S/2) P M S in the orthogonal basis
+ *   CENTRAL:  central moments about u; the first-order central moments
+ *             leave the collision as +F/2 (they enter as -F/2, Sec. 4.2)
+ *   CUMULANT: cumulants of order >= 2 (shift invariant) relax as without
+ *             force; the mean velocity leaves as (j + F) / rho.
+ * The total force on a cell is the uniform part plus the field's entry.
+ *   lbm_set_force: uniform F[D] (D = 2 for D2Q9, else 3); NULL = none.
+ *   lbm_set_force_field: per-cell F[d*N + c], d < D, FP64, host memory or
+ *     (on_device = 1) device memory; copied (FP32 storage: rounded to FP32)
+ *     into a device array the context owns; NULL removes it.
+ * Under a force, lbm_macroscopic returns the fluid velocity (j + F/2) / rho;
+ * lbm_invariants keeps reporting sums of rho - 1 and j = sum xi_i f_i.
+ * Served for LBM_STORE_F64 / LBM_STORE_F32 with deviation arithmetic, pull
+ * or AA, without a learned closure (then LBM_STEP_DIRECT runs); otherwise
+ * LBM_ERR_UNSUPPORTED.  Errors: INVALID (non-finite F), UNSUPPORTED, OOM,
+ * CUDA. */
+int lbm_set_force(lbm_ctx* ctx, const double* F);
+int lbm_set_force_field(lbm_ctx* ctx, const double* F, int on_device);
+
 /* Pull step kernel.  Both compute the same per-cell arithmetic (FP16/BF16
  * storage: bitwise-identical states; FP32/FP64: equal up to the compiler's
  * choice of multiply-add contractions); they differ in how the gather of

@@ -91,6 +91,9 @@ AuxArgs aux_base(const lbm_ctx* c, int op) {
   a.storage = c->p.storage;
   a.space = c->space;
   a.gather_mode = gather_mode(c);
+  a.force_mode = c->force_mode;
+  for (int d = 0; d < 3; ++d) a.force[d] = c->force[d];
+  a.force_field = c->force_field;
   a.stream = c->stream;
   return a;
 }
@@ -256,7 +259,88 @@ void lbm_destroy(lbm_ctx* c) {
     if (c->buf[b]) cudaFree(c->buf[b]);
   if (c->part) cudaFree(c->part);
   if (c->closure) lbm::free_closure(c->closure);
+  if (c->force_field) cudaFree(c->force_field);
   delete c;
+}
+
+// ------------------------------------------------------------ body force
+namespace {
+
+__global__ void k_f64_to_f32(const double* in, float* out, int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = float(in[k]);
+}
+
+bool force_served(const lbm_ctx* c) {
+  return (c->p.storage == LBM_STORE_F64 || c->p.storage == LBM_STORE_F32) &&
+         c->p.arithmetic == LBM_ARITH_DEVIATION && !c->closure;
+}
+
+void update_force_mode(lbm_ctx* c) {
+  const bool uni = c->force[0] != 0.0 || c->force[1] != 0.0 || c->force[2] != 0.0;
+  c->force_mode = c->force_field ? lbm::FORCE_FIELD : (uni ? lbm::FORCE_UNIFORM : lbm::FORCE_NONE);
+}
+
+}  // namespace
+
+int lbm_set_force(lbm_ctx* c, const double* F) {
+  if (!c) return LBM_ERR_INVALID;
+  if (F) {
+    for (int d = 0; d < c->d; ++d)
+      if (!std::isfinite(F[d])) return LBM_ERR_INVALID;
+    if (!force_served(c)) return LBM_ERR_UNSUPPORTED;
+  }
+  for (int d = 0; d < 3; ++d) c->force[d] = (F && d < c->d) ? F[d] : 0.0;
+  update_force_mode(c);
+  return LBM_OK;
+}
+
+int lbm_set_force_field(lbm_ctx* c, const double* F, int on_device) {
+  if (!c) return LBM_ERR_INVALID;
+  if (!F) {
+    if (c->force_field) {
+      cudaStreamSynchronize(c->stream);
+      cudaFree(c->force_field);
+      c->force_field = nullptr;
+    }
+    update_force_mode(c);
+    return LBM_OK;
+  }
+  if (!force_served(c)) return LBM_ERR_UNSUPPORTED;
+  const int64_t n = int64_t(c->d) * c->g.N;
+  const size_t eb = c->p.storage == LBM_STORE_F64 ? sizeof(double) : sizeof(float);
+  void* dev = nullptr;
+  if (cudaMalloc(&dev, size_t(n) * eb) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ERR_OOM;
+  }
+  int rc = LBM_OK;
+  if (eb == sizeof(double)) {
+    rc = cuda_err(cudaMemcpyAsync(dev, F, size_t(n) * eb,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  c->stream));
+  } else if (on_device) {
+    k_f64_to_f32<<<unsigned((n + 255) / 256), 256, 0, c->stream>>>(F, (float*)dev, n);
+    rc = cuda_err(cudaGetLastError());
+  } else {
+    float* h = new (std::nothrow) float[size_t(n)];
+    if (!h) rc = LBM_ERR_OOM;
+    else {
+      for (int64_t k = 0; k < n; ++k) h[k] = float(F[k]);
+      rc = cuda_err(cudaMemcpyAsync(dev, h, size_t(n) * eb, cudaMemcpyHostToDevice, c->stream));
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess && rc == LBM_OK) rc = LBM_ERR_CUDA;
+      delete[] h;
+    }
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess && rc == LBM_OK) rc = LBM_ERR_CUDA;
+  if (rc != LBM_OK) {
+    cudaFree(dev);
+    return rc;
+  }
+  if (c->force_field) cudaFree(c->force_field);
+  c->force_field = dev;
+  update_force_mode(c);
+  return LBM_OK;
 }
 
 int lbm_set_stream(lbm_ctx* c, void* stream) {
@@ -327,7 +411,7 @@ int lbm_set_populations(lbm_ctx* c, const double* df, int on_device) {
 static bool staged_ok(const lbm_ctx* c) {
   const int64_t row = int64_t(c->g.nx) * c->eb;
   return c->p.streaming == LBM_PULL && c->p.storage != LBM_STORE_F64_ABSOLUTE &&
-         c->p.arithmetic == LBM_ARITH_DEVIATION && row % 16 == 0 &&
+         c->p.arithmetic == LBM_ARITH_DEVIATION && !c->force_mode && row % 16 == 0 &&
          lbm::staged_stages(c->q, c->g.nx, c->eb) >= lbm::STG_MIN_STAGES;
 }
 
@@ -367,6 +451,10 @@ int lbm_step(lbm_ctx* c, int64_t n) {
   a.form = (c->p.arithmetic == LBM_ARITH_AS_WRITTEN && c->p.equilibrium == LBM_EQ_ABSOLUTE) ? 1 : 0;
   a.variant = use_staged(c) ? lbm::VARIANT_STAGED : lbm::VARIANT_DIRECT;
   a.status = c->status;
+  a.force_mode = c->force_mode;
+  for (int d = 0; d < 3; ++d) a.force[d] = c->force[d];
+  a.force_field = c->force_field;
+  if (c->force_mode) a.reg = 0;  // forced kernels: the general instantiation
   a.stream = c->stream;
   const step_fn fn = kStep[c->p.stencil][c->p.storage];
   for (int64_t s = 0; s < n; ++s) {

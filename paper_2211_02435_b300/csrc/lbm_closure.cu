@@ -873,7 +873,8 @@ int lbm_set_closure(lbm_ctx* c, const lbm_closure_weights* w) {
   }
   if (c->p.stencil != LBM_D3Q27 || c->p.space != LBM_SPACE_CUMULANT ||
       c->p.streaming != LBM_PULL ||
-      (c->p.storage != LBM_STORE_F32 && c->p.storage != LBM_STORE_F64))
+      (c->p.storage != LBM_STORE_F32 && c->p.storage != LBM_STORE_F64) ||
+      c->p.arithmetic != LBM_ARITH_DEVIATION || c->force_mode != lbm::FORCE_NONE)
     return LBM_ERR_UNSUPPORTED;
   const bool dbl = c->p.storage == LBM_STORE_F64;
   std::vector<double> hd(lbm::NSMEM);

@@ -479,25 +479,68 @@ LBM_D void equilibrium(T drho, const T (&u)[3], T (&f)[q_of(ST)]);
 // ------------------------------------------------------------ collision
 // In: zero-centered pre-collision populations f.  Out: zero-centered
 // post-collision populations f*.  keep.om[g] = 1 - omega_g.
-template <int ST, class T, int SPACE, bool REG, bool DEFER = false>
-LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep) {
+// Guo's population source of a body force F at velocity u (c_s^2 = 1/3):
+// S_i = w_i [3 (xi_i.F - u.F) + 9 (xi_i.u)(xi_i.F)]
+template <int ST, class T>
+LBM_D void guo_source(const T (&u)[3], const T (&F)[3], T (&S)[q_of(ST)]) {
+  const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1), cz = vel(ST, i, 2);
+    T cu = T(0), cf = T(0);
+    if constexpr (cx != 0) cu += T(cx) * u[0], cf += T(cx) * F[0];
+    if constexpr (cy != 0) cu += T(cy) * u[1], cf += T(cy) * F[1];
+    if constexpr (cz != 0) cu += T(cz) * u[2], cf += T(cz) * F[2];
+    S[i] = T(weight(ST, i)) * (T(3) * (cf - uF) + T(9) * cu * cf);
+  });
+}
+
+// FORCED: a body force F per cell (source term of Eq. 2.1a, q^F of Eq. 2.4,
+// Guo's model).  The equilibrium velocity is u = (j + F/2) / rho and
+//   SRT: f* = f + w (f_eq - f) + (1 - w/2) S
+//   raw: q^F = (I - S/2) P M S in the orthogonal basis (general path only)
+//   central: moments about u, first-order central moments leave as +F/2
+//   cumulant: cumulants relax about the mean j / rho; the mean leaves as
+//             (j + F) / rho (cumulants of order >= 2 are shift invariant).
+template <int ST, class T, int SPACE, bool REG, bool DEFER = false, bool FORCED = false>
+LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr) {
+  static_assert(!(FORCED && REG && SPACE == SP_RAW), "forced raw moments use the general path");
   T A[3][3][3];
   fwd_raw_chimera<ST, T>(f, A);
   const T drho = A[0][0][0];
   const T rho = T(1) + drho;
   const T inv = rcp(rho);
   const T j[3] = {A[1][0][0], A[0][1][0], dim_of(ST) == 3 ? A[0][0][1] : T(0)};
-  const T u[3] = {j[0] * inv, j[1] * inv, j[2] * inv};
+  T Fv[3] = {T(0), T(0), T(0)};
+  if constexpr (FORCED) {
+    Fv[0] = F[0];
+    Fv[1] = F[1];
+    if constexpr (dim_of(ST) == 3) Fv[2] = F[2];
+  }
+  constexpr bool SHIFT = FORCED && SPACE != SP_CUMULANT;
+  const T u[3] = {SHIFT ? (j[0] + T(0.5) * Fv[0]) * inv : j[0] * inv,
+                  SHIFT ? (j[1] + T(0.5) * Fv[1]) * inv : j[1] * inv,
+                  SHIFT ? (j[2] + T(0.5) * Fv[2]) * inv : j[2] * inv};
   const T u2[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
 
   if constexpr (SPACE == SP_SRT) {
     // single relaxation time in population space against f_eq = M^-1 m_eq
     T feq[q_of(ST)];
     equilibrium<ST, T, SP_RAW>(drho, u, feq);
-    sfor<q_of(ST)>([&](auto I) {
-      constexpr int i = CI(I);
-      f[i] = feq[i] + keep.om[0] * (f[i] - feq[i]);
-    });
+    if constexpr (FORCED) {
+      T S[q_of(ST)];
+      guo_source<ST, T>(u, Fv, S);
+      const T half = T(0.5) * (T(1) + keep.om[0]);  // 1 - w/2
+      sfor<q_of(ST)>([&](auto I) {
+        constexpr int i = CI(I);
+        f[i] = feq[i] + keep.om[0] * (f[i] - feq[i]) + half * S[i];
+      });
+    } else {
+      sfor<q_of(ST)>([&](auto I) {
+        constexpr int i = CI(I);
+        f[i] = feq[i] + keep.om[0] * (f[i] - feq[i]);
+      });
+    }
     return;
   } else if constexpr (SPACE == SP_RAW) {
     // non-equilibrium parts in the orthogonal basis, relax, transform back
@@ -507,7 +550,8 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep) {
       constexpr int o = a + b + c;
       if constexpr (has_mono(ST, a, b, c)) {
         E[a][b][c] = raw_eq_dev<T>(a, b, c, drho, rho, u);
-        if constexpr (o <= 1 || (REG && o != 2)) N[a][b][c] = T(0);
+        // forced: the first-order non-equilibrium part is -F/2
+        if constexpr (o == 0 || (o == 1 && !FORCED) || (REG && o != 2)) N[a][b][c] = T(0);
         else N[a][b][c] = A[a][b][c] - E[a][b][c];
       } else {
         E[a][b][c] = T(0);
@@ -521,6 +565,24 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep) {
         constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
         constexpr int o = a + b + c;
         if constexpr (has_mono(ST, a, b, c) && o >= 3) N[a][b][c] *= keep.om[o - 1];
+      });
+    }
+    if constexpr (FORCED) {
+      // q^F = (I - S/2) P M S: the source's raw moments in the orthogonal
+      // basis, each rate group scaled by 1 - w/2 (conserved rows by 1)
+      T S[q_of(ST)], G[3][3][3];
+      guo_source<ST, T>(u, Fv, S);
+      fwd_raw_chimera<ST, T>(S, G);
+      G[0][0][0] = T(0);
+      ortho_raw<ST, -1, T>(G);
+      relax_order2<ST, T, false>(G, T(0.5) * (T(1) + keep.om[0]), T(0.5) * (T(1) + keep.om[1]));
+      sfor<27>([&](auto K) {
+        constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+        constexpr int o = a + b + c;
+        if constexpr (has_mono(ST, a, b, c) && o >= 1) {
+          if constexpr (o >= 3) N[a][b][c] += T(0.5) * (T(1) + keep.om[o - 1]) * G[a][b][c];
+          else N[a][b][c] += G[a][b][c];
+        }
       });
     }
     ortho_raw<ST, +1, T>(N);
@@ -586,7 +648,12 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep) {
       if constexpr (o == 0) {
         A[a][b][c] = drho;
       } else if constexpr (o == 1) {
-        A[a][b][c] = T(0);
+        // central moments about u leave as F/2; cumulants rebuild about the
+        // advanced mean, where the first-order central moments are 0
+        if constexpr (FORCED && SPACE == SP_CENTRAL)
+          A[a][b][c] = T(0.5) * Fv[a == 1 ? 0 : (b == 1 ? 1 : 2)];
+        else
+          A[a][b][c] = T(0);
       } else if constexpr (has_mono(ST, a, b, c)) {
         if constexpr (B != 0.0) A[a][b][c] = drho * T(B) + rho * Kn[a][b][c];
         else A[a][b][c] = rho * Kn[a][b][c];
@@ -594,13 +661,25 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep) {
         A[a][b][c] = T(0);
       }
     });
-    binomial<ST, +1, T>(A, u, u2);
+    if constexpr (FORCED && SPACE == SP_CUMULANT) {
+      const T v[3] = {(j[0] + Fv[0]) * inv, (j[1] + Fv[1]) * inv, (j[2] + Fv[2]) * inv};
+      const T v2[3] = {v[0] * v[0], v[1] * v[1], v[2] * v[2]};
+      binomial<ST, +1, T>(A, v, v2);
+    } else {
+      binomial<ST, +1, T>(A, u, u2);
+    }
   }
-  // conserved moments pass through exactly
+  // conserved moments pass through exactly (plus the force's momentum)
   A[0][0][0] = drho;
-  A[1][0][0] = j[0];
-  A[0][1][0] = j[1];
-  if constexpr (dim_of(ST) == 3) A[0][0][1] = j[2];
+  if constexpr (FORCED) {
+    A[1][0][0] = j[0] + Fv[0];
+    A[0][1][0] = j[1] + Fv[1];
+    if constexpr (dim_of(ST) == 3) A[0][0][1] = j[2] + Fv[2];
+  } else {
+    A[1][0][0] = j[0];
+    A[0][1][0] = j[1];
+    if constexpr (dim_of(ST) == 3) A[0][0][1] = j[2];
+  }
   bwd_raw<ST, T, DEFER>(A, f);
 }
 

@@ -18,6 +18,7 @@ struct Geo {
 enum { STORE_F64 = 0, STORE_F32 = 1, STORE_F16 = 2, STORE_BF16 = 3, STORE_F64_ABS = 4 };
 enum { MODE_PULL = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2 };
 enum { VARIANT_DIRECT = 0, VARIANT_STAGED = 1 };
+enum { FORCE_NONE = 0, FORCE_UNIFORM = 1, FORCE_FIELD = 2 };
 
 // shared-memory staged pull kernel (lbm_staged.cuh); the stage cap is a
 // compile-time tuning knob
@@ -50,6 +51,9 @@ struct StepArgs {
   int form;     // FORM_DEV / FORM_ABS_EQ (Eq. 2.6 arithmetic, FP64 storage)
   int variant;  // VARIANT_DIRECT / VARIANT_STAGED (pull only)
   int* status;  // device word set by a kernel whose bounded wait ran out
+  int force_mode;           // FORCE_NONE / FORCE_UNIFORM / FORCE_FIELD
+  double force[3];          // uniform body force
+  const void* force_field;  // per-cell force [D][N] in the compute type (FORCE_FIELD)
   cudaStream_t stream;
 };
 
@@ -68,6 +72,9 @@ struct AuxArgs {
   const double* u_in;
   double* part;  // invariants partials [nparts][8]
   int nparts;
+  int force_mode;           // gather: fluid velocity (j + F/2) / rho under a force
+  double force[3];
+  const void* force_field;
   cudaStream_t stream;
 };
 
@@ -141,5 +148,8 @@ struct lbm_ctx {
   void* closure;  // device closure parameters (lbm_closure.cu), NULL = off
   int* status;    // device word after the invariants scratch: nonzero = a bounded wait ran out
   int kernel;     // requested step kernel (LBM_STEP_*)
+  int force_mode;     // lbm::FORCE_*
+  double force[3];    // uniform body force (zeros when unset)
+  void* force_field;  // device [D][N] in the compute type, or NULL
 };
 

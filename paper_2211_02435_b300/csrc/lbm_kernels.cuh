@@ -46,6 +46,22 @@ LBM_D S enc_pop(T f) {
 // zero-centered storage, Eq. 2.4 on absolute storage
 enum { FORM_DEV = 0, FORM_ABS_EQ = 1, FORM_ABS_STORE = 2 };
 
+// body force of a step: the uniform part F plus, for FORCE_FIELD, the cell's
+// entry of a per-cell field field[d * N + c] in the compute type
+template <class T>
+struct ForceArg {
+  T F[3];
+  const T* field;
+};
+template <int ST, int FORCE, class T>
+LBM_D void cell_force(const ForceArg<T>& fa, const Geo& g, int c, T (&Fc)[3]) {
+  for (int d = 0; d < 3; ++d) {
+    Fc[d] = d < dim_of(ST) ? fa.F[d] : T(0);
+    if constexpr (FORCE == FORCE_FIELD)
+      if (d < dim_of(ST)) Fc[d] += fa.field[(int64_t)d * g.N + c];
+  }
+}
+
 struct Nbr {
   int x[3], y[3], z[3];  // coordinate of offset -1, 0, +1 (periodic)
 };
@@ -100,9 +116,9 @@ struct PullPtrs {
 };
 
 // pull: read f_i from x - xi_i of src, collide, write f*_i at x of dst
-template <int ST, class S, class T, int SPACE, bool REG, int FORM = FORM_DEV>
+template <int ST, class S, class T, int SPACE, bool REG, int FORM = FORM_DEV, int FORCE = FORCE_NONE>
 __global__ void __launch_bounds__(LBM_BX) k_pull(const __grid_constant__ PullPtrs<S> P, Geo g,
-                                                 Rates<T> keep) {
+                                                 Rates<T> keep, ForceArg<T> fa = {}) {
   const int x = blockIdx.x * LBM_BX + threadIdx.x;
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
@@ -122,8 +138,15 @@ __global__ void __launch_bounds__(LBM_BX) k_pull(const __grid_constant__ PullPtr
     if constexpr (FORM == FORM_ABS_STORE) f[i] = T(v.v);
     else f[i] = dec_pop<ST, i, S, T>(v);
   });
-  if constexpr (FORM == FORM_DEV) collide<ST, T, SPACE, REG>(f, keep);
-  else collide_abs<ST, T, SPACE, REG, FORM == FORM_ABS_EQ>(f, keep);
+  if constexpr (FORM == FORM_DEV && FORCE != FORCE_NONE) {
+    T Fc[3];
+    cell_force<ST, FORCE>(fa, g, c, Fc);
+    collide<ST, T, SPACE, REG, false, true>(f, keep, Fc);
+  } else if constexpr (FORM == FORM_DEV) {
+    collide<ST, T, SPACE, REG>(f, keep);
+  } else {
+    collide_abs<ST, T, SPACE, REG, FORM == FORM_ABS_EQ>(f, keep);
+  }
   sfor<q_of(ST)>([&](auto I) {
     constexpr int i = CI(I);
     if constexpr (FORM == FORM_ABS_STORE) P.dst[i][c] = S{double(f[i])};
@@ -175,8 +198,9 @@ __global__ void __launch_bounds__(LBM_BX) k_pull2(const __grid_constant__ PullPt
 // kernels read slot ibar at x - xi_i and write f*_i into slot i at
 // x + xi_i.  Each cell reads and writes the same set of addresses, so no
 // two threads touch one element.
-template <int ST, class S, class T, int SPACE, bool REG, bool ODD>
-__global__ void __launch_bounds__(LBM_BX) k_aa(S* buf, Geo g, Rates<T> keep) {
+template <int ST, class S, class T, int SPACE, bool REG, bool ODD, int FORCE = FORCE_NONE>
+__global__ void __launch_bounds__(LBM_BX) k_aa(S* buf, Geo g, Rates<T> keep,
+                                               ForceArg<T> fa = {}) {
   const int x = blockIdx.x * LBM_BX + threadIdx.x;
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
@@ -184,7 +208,13 @@ __global__ void __launch_bounds__(LBM_BX) k_aa(S* buf, Geo g, Rates<T> keep) {
   const int c = (z * g.ny + y) * g.nx + x;
   T f[q_of(ST)];
   load_pops<ST, S, T, ODD ? G_AAODD : G_LOCAL>(buf, g, n, c, f);
-  collide<ST, T, SPACE, REG>(f, keep);
+  if constexpr (FORCE != FORCE_NONE) {
+    T Fc[3];
+    cell_force<ST, FORCE>(fa, g, c, Fc);
+    collide<ST, T, SPACE, REG, false, true>(f, keep, Fc);
+  } else {
+    collide<ST, T, SPACE, REG>(f, keep);
+  }
   sfor<q_of(ST)>([&](auto I) {
     constexpr int i = CI(I);
     constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1), cz = vel(ST, i, 2);
@@ -201,7 +231,7 @@ __global__ void __launch_bounds__(LBM_BX) k_aa(S* buf, Geo g, Rates<T> keep) {
 // canonical populations -> FP64 SoA df[i * N + c] and / or macroscopic
 template <int ST, class S, class T, int MODE>
 __global__ void __launch_bounds__(LBM_BX) k_gather(const S* buf, Geo g, double* df, double* rho,
-                                                   double* u) {
+                                                   double* u, ForceArg<T> fa = {}) {
   const int x = blockIdx.x * LBM_BX + threadIdx.x;
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
@@ -225,7 +255,12 @@ __global__ void __launch_bounds__(LBM_BX) k_gather(const S* buf, Geo g, double* 
     const double r = 1.0 + dr;
     if (rho) rho[c] = r;
     if (u) {
-      for (int d = 0; d < dim_of(ST); ++d) u[(int64_t)d * g.N + c] = j[d] / r;
+      // under a body force the fluid velocity is (j + F/2) / rho
+      for (int d = 0; d < dim_of(ST); ++d) {
+        double Fd = double(fa.F[d]);
+        if (fa.field) Fd += double(fa.field[(int64_t)d * g.N + c]);
+        u[(int64_t)d * g.N + c] = (j[d] + 0.5 * Fd) / r;
+      }
     }
   }
 }
@@ -393,11 +428,51 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS)
 // --------------------------------------------------------------- launchers
 inline dim3 step_grid(const Geo& g) { return dim3((g.nx + LBM_BX - 1) / LBM_BX, g.ny, g.nz); }
 
+// forced steps (FP32 / FP64 storage, deviation arithmetic): the general
+// (non-regularised) instantiation, which is the same method for unit rates
+template <int ST, class S, class T, int SPACE>
+void launch_forced(const StepArgs& a, const Rates<T>& keep, const dim3& grid) {
+  ForceArg<T> fa;
+  for (int d = 0; d < 3; ++d) fa.F[d] = T(a.force[d]);
+  fa.field = (const T*)a.force_field;
+  const bool field = a.force_mode == FORCE_FIELD;
+  if (a.mode == MODE_PULL) {
+    PullPtrs<S> P;
+    const int64_t nx = a.g.nx, nxy = int64_t(a.g.nx) * a.g.ny;
+    for (int i = 0; i < 27; ++i) {
+      const int64_t delta =
+          i < q_of(ST) ? -(vel(ST, i, 2) * nxy + vel(ST, i, 1) * nx + vel(ST, i, 0)) : 0;
+      P.src[i] = i < q_of(ST) ? (const S*)a.src + (int64_t(i) * a.g.N + delta) : nullptr;
+      P.dst[i] = i < q_of(ST) ? (S*)a.dst + int64_t(i) * a.g.N : nullptr;
+    }
+    if (field)
+      k_pull<ST, S, T, SPACE, false, FORM_DEV, FORCE_FIELD><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep, fa);
+    else
+      k_pull<ST, S, T, SPACE, false, FORM_DEV, FORCE_UNIFORM><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep, fa);
+  } else if (a.mode == MODE_AA_EVEN) {
+    if (field)
+      k_aa<ST, S, T, SPACE, false, false, FORCE_FIELD><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
+    else
+      k_aa<ST, S, T, SPACE, false, false, FORCE_UNIFORM><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
+  } else {
+    if (field)
+      k_aa<ST, S, T, SPACE, false, true, FORCE_FIELD><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
+    else
+      k_aa<ST, S, T, SPACE, false, true, FORCE_UNIFORM><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
+  }
+}
+
 template <int ST, class S, class T, int SPACE, bool REG>
 void launch_step_typed(const StepArgs& a) {
   Rates<T> keep;
   for (int k = 0; k < 6; ++k) keep.om[k] = T(1.0 - a.rates[k]);
   const dim3 grid = step_grid(a.g);
+  if constexpr ((std::is_same<S, float>::value || std::is_same<S, double>::value) && !REG) {
+    if (a.force_mode != FORCE_NONE) {
+      launch_forced<ST, S, T, SPACE>(a, keep, grid);
+      return;
+    }
+  }
   if (a.mode == MODE_PULL) {
     PullPtrs<S> P;
     const int64_t nx = a.g.nx, nxy = int64_t(a.g.nx) * a.g.ny;
@@ -459,14 +534,18 @@ void launch_aux_typed(const AuxArgs& a) {
   const dim3 grid = step_grid(a.g);
   const int gm = a.gather_mode;
   switch (a.op) {
-    case AUX_GATHER:
+    case AUX_GATHER: {
+      ForceArg<T> fa;
+      for (int d = 0; d < 3; ++d) fa.F[d] = T(a.force_mode != FORCE_NONE ? a.force[d] : 0.0);
+      fa.field = a.force_mode == FORCE_FIELD ? (const T*)a.force_field : nullptr;
       if (gm == G_PULL)
-        k_gather<ST, S, T, G_PULL><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u);
+        k_gather<ST, S, T, G_PULL><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
       else if (gm == G_LOCAL)
-        k_gather<ST, S, T, G_LOCAL><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u);
+        k_gather<ST, S, T, G_LOCAL><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
       else
-        k_gather<ST, S, T, G_AAODD><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u);
+        k_gather<ST, S, T, G_AAODD><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
       break;
+    }
     case AUX_SCATTER: {
       const bool pull = gm == G_PULL;
       if (a.space == SP_RAW || a.space == SP_SRT) {

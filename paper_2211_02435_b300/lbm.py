@@ -90,6 +90,8 @@ def lib():
         L.lbm_set_rates.argtypes = [vp, d]
         L.lbm_set_stream.argtypes = [vp, vp]
         L.lbm_set_step_kernel.argtypes = [vp, c_int]
+        L.lbm_set_force.argtypes = [vp, vp]
+        L.lbm_set_force_field.argtypes = [vp, vp, c_int]
         L.lbm_destroy.argtypes = [vp]
         L.lbm_destroy.restype = None
         L.lbm_error_string.argtypes = [c_int]
@@ -303,6 +305,24 @@ class Lattice:
 
     def set_stream(self, stream):
         _check(lib().lbm_set_stream(self._h, stream_handle(stream)), "lbm_set_stream")
+
+    def set_force(self, F):
+        """Uniform body force F[D] (None removes it); Guo's model, include/lbm.h."""
+        if F is None:
+            _check(lib().lbm_set_force(self._h, None), "lbm_set_force")
+            return
+        arr = (ctypes.c_double * 3)(*[float(v) for v in list(F)[:3]])
+        _check(lib().lbm_set_force(self._h, ctypes.cast(arr, ctypes.c_void_p)), "lbm_set_force")
+
+    def set_force_field(self, F):
+        """Per-cell body force [D, N] (numpy FP64 or a CUDA tensor); None removes it."""
+        if F is None:
+            _check(lib().lbm_set_force_field(self._h, None, 0), "lbm_set_force_field")
+            return
+        if isinstance(F, np.ndarray):
+            F = np.ascontiguousarray(F, dtype=np.float64)
+        p, dev = _ptr(F, self.d * self.N)
+        _check(lib().lbm_set_force_field(self._h, p, dev), "lbm_set_force_field")
 
     def set_step_kernel(self, kernel):
         """STEP_AUTO, STEP_DIRECT or STEP_STAGED (include/lbm.h)."""
