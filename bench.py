@@ -299,11 +299,16 @@ def run_cuda(args):
     u_d = torch.from_numpy(u_h.reshape(-1)).cuda()
     peak, peak_kind = measured_peaks()
 
-    def time_form(storage, steps, warmup, streaming=L.PULL):
+    def time_form(storage, steps, warmup, streaming=L.PULL, force=None):
         lat = L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, storage, streaming, rates,
                         (n, n, n), stream=stream)
         if streaming == L.PULL:
             lat.set_step_kernel(STEP_KERNELS[args.step_kernel])
+        if force is not None:
+            if force.ndim == 1:
+                lat.set_force(force)
+            else:
+                lat.set_force_field(force)
         lat.init_velocity(rho_d, u_d)
         lat.step(warmup)
         torch.cuda.synchronize()
@@ -374,6 +379,20 @@ def run_cuda(args):
         forms["f32_aa"] = {"mlups": N * st_aa / (ms / 1e3) / 1e6, "achieved_gbs": ach,
                            "roofline_frac": ach / peak, "buffers": 1,
                            "note": "same per-cell arithmetic as pull (bitwise equal states)"}
+        # body force (Guo): uniform, and a per-cell field (+12 B/cell of reads)
+        for name, force, bpc in (
+                ("f32_force_uniform", np.array([1e-6, 0.0, 0.0]), BYTES_PER_CELL["f32"]),
+                ("f32_force_field", torch.full((3 * N,), 1e-6, dtype=torch.float64,
+                                               device="cuda"), BYTES_PER_CELL["f32"] + 12)):
+            if not isinstance(force, np.ndarray):
+                force = force.view(3, -1)
+            lat, ms = time_form(L.STORE_F32, args.steps, args.warmup, force=force)
+            lat.close()
+            del lat
+            ach = bpc * N / (ms / 1e3 / args.steps) / 1e9
+            forms[name] = {"mlups": N * args.steps / (ms / 1e3) / 1e6, "achieved_gbs": ach,
+                           "roofline_frac": ach / peak, "bytes_per_cell": bpc}
+            del force
         del u64
     del u32
 
