@@ -75,7 +75,15 @@ typedef enum {
   LBM_SPACE_POPULATIONS = 0,
   LBM_SPACE_RAW = 1,      /* orthogonal raw moments, unweighted (O-MRT)  */
   LBM_SPACE_CENTRAL = 2,  /* polynomial central moments (CM)             */
-  LBM_SPACE_CUMULANT = 3  /* polynomial cumulants (K)                    */
+  LBM_SPACE_CUMULANT = 3, /* polynomial cumulants (K)                    */
+  LBM_SPACE_TRT = 4       /* two relaxation times in population space:
+                             per opposite pair the even part
+                             (f_i + f_ibar)/2 relaxes with rates[0], the
+                             odd part with rates[2]; the same method as
+                             LBM_SPACE_RAW with even orders at rates[0] and
+                             odd orders at rates[2].  Deviation arithmetic
+                             only (not with LBM_STORE_F64_ABSOLUTE or
+                             LBM_ARITH_AS_WRITTEN: UNSUPPORTED) */
 } lbm_space;
 
 /* Equilibrium format (Sec. 2.2): relax deviations against the
@@ -115,9 +123,13 @@ typedef enum {
  * is served for FP64 storage with pull streaming. */
 typedef enum { LBM_ARITH_DEVIATION = 0, LBM_ARITH_AS_WRITTEN = 1 } lbm_arithmetic;
 
-/* Streaming pattern (Sec. 4.3): pull with two buffers, or the in-place
- * AA pattern with one buffer. */
-typedef enum { LBM_PULL = 0, LBM_AA = 1 } lbm_streaming;
+/* Streaming pattern (Sec. 4.3): pull with two buffers, or one of the
+ * in-place patterns with one buffer: AA (even steps local, odd steps across
+ * all neighbours) or Esoteric Twist (every step reads and writes the cell
+ * and its positive neighbours: population i of cell x lives at node
+ * x + max(-xi_i, 0), slot i at even and slot ibar at odd times).  All give
+ * identical states f(n); lbm_get_time reports the in-place parity. */
+typedef enum { LBM_PULL = 0, LBM_AA = 1, LBM_ESOTERIC_TWIST = 2 } lbm_streaming;
 
 #define LBM_PERIODIC 0 /* the only boundary; others -> LBM_ERR_UNSUPPORTED */
 

@@ -23,7 +23,7 @@ _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liblbm_oracle.so")
 
 D2Q9, D3Q19, D3Q27 = 0, 1, 2
-SPACE_POPULATIONS, SPACE_RAW, SPACE_CENTRAL, SPACE_CUMULANT, SPACE_NONE = 0, 1, 2, 3, 4
+SPACE_POPULATIONS, SPACE_RAW, SPACE_CENTRAL, SPACE_CUMULANT, SPACE_TRT, SPACE_NONE = 0, 1, 2, 3, 4, 5
 EQ_DELTA, EQ_ABSOLUTE = 0, 1
 GROUP_CONSERVED, GROUP_SHEAR, GROUP_BULK = -1, 0, 1
 Q_OF = {D2Q9: 9, D3Q19: 19, D3Q27: 27}

@@ -25,6 +25,7 @@ typedef struct {
   int ready;
   int q, d;
   int xi[QMAX][3];
+  int opp[QMAX]; /* index of -xi_i */
   int expo[QMAX][3];
   int deg[QMAX];
   int mono[3][3][3]; /* exponent -> monomial index, -1 if not in the set */
@@ -198,6 +199,11 @@ static int build_lattice(int stencil) {
   for (int i = 0; i < L->q; ++i)
     for (int d = 0; d < 3; ++d)
       L->xi[i][d] = stencil == LBM_ORACLE_D2Q9 ? V2[i][d] : V3[i][d];
+  for (int i = 0; i < L->q; ++i)
+    for (int k = 0; k < L->q; ++k)
+      if (L->xi[k][0] == -L->xi[i][0] && L->xi[k][1] == -L->xi[i][1] &&
+          L->xi[k][2] == -L->xi[i][2])
+        L->opp[i] = k;
   /* monomial exponent set, ordered by total degree then lexicographically */
   int n = 0;
   for (int a = 0; a < 3; ++a)
@@ -453,6 +459,29 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
     case LBM_ORACLE_SPACE_NONE:
       for (int i = 0; i < q; ++i) out[i] = df[i];
       return 0;
+    case LBM_ORACLE_SPACE_TRT: {
+      /* two relaxation times: the even part f+_i = (f_i + f_ibar)/2 relaxes
+       * with w+ = rates[0], the odd part f-_i = (f_i - f_ibar)/2 with
+       * w- = rates[2]; equilibrium and Guo source split the same way */
+      for (int k = 0; k < q; ++k)
+        veq[k] = maxwell_raw_moment(L->expo[k], rho, u, 1) -
+                 (delta ? maxwell_raw_moment(L->expo[k], 1.0, zero_u, 1) : 0.0);
+      matvec(q, L->Minv, veq, tmp); /* delta: df_eq ; absolute: f_eq */
+      const double wp = m->rates[0], wm = m->rates[2];
+      for (int i = 0; i < q; ++i) {
+        const int ib = L->opp[i];
+        const double fi = df[i] + (delta ? 0.0 : L->w[i]);
+        const double fb = df[ib] + (delta ? 0.0 : L->w[ib]);
+        const double fp = 0.5 * (fi + fb), fm = 0.5 * (fi - fb);
+        const double ep = 0.5 * (tmp[i] + tmp[ib]), em = 0.5 * (tmp[i] - tmp[ib]);
+        double o = fi - wp * (fp - ep) - wm * (fm - em);
+        if (forced)
+          o += (1.0 - 0.5 * wp) * 0.5 * (S[i] + S[ib]) +
+               (1.0 - 0.5 * wm) * 0.5 * (S[i] - S[ib]);
+        out[i] = o - (delta ? 0.0 : L->w[i]);
+      }
+      return 0;
+    }
     case LBM_ORACLE_SPACE_POPULATIONS: {
       /* SRT: f* = f + w (f_eq - f), f_eq = M^-1 m_eq (truncated) */
       for (int k = 0; k < q; ++k)
@@ -573,7 +602,7 @@ static int collide_cell(const lattice_t* L, const lbm_oracle_method* m,
 
 static int check_method(const lbm_oracle_method* m) {
   if (!m || build_lattice(m->stencil)) return -1;
-  if (m->space < 0 || m->space > 4) return -1;
+  if (m->space < 0 || m->space > 5) return -1;
   if (m->equilibrium != LBM_ORACLE_EQ_DELTA &&
       m->equilibrium != LBM_ORACLE_EQ_ABSOLUTE)
     return -1;
@@ -718,6 +747,7 @@ static void equilibrium_cell(const lattice_t* L, const lbm_oracle_method* m,
   static const double zero_u[3] = {0, 0, 0};
   const int trunc = m->space == LBM_ORACLE_SPACE_RAW ||
                     m->space == LBM_ORACLE_SPACE_POPULATIONS ||
+                    m->space == LBM_ORACLE_SPACE_TRT ||
                     m->space == LBM_ORACLE_SPACE_NONE;
   double dm[QMAX];
   for (int k = 0; k < L->q; ++k)

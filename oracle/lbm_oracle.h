@@ -51,7 +51,10 @@ extern "C" {
 #define LBM_ORACLE_SPACE_RAW 1
 #define LBM_ORACLE_SPACE_CENTRAL 2
 #define LBM_ORACLE_SPACE_CUMULANT 3
-#define LBM_ORACLE_SPACE_NONE 4
+/* two-relaxation-time collision in population space: even part with
+ * rates[0], odd part with rates[2] (the order-3 slot) */
+#define LBM_ORACLE_SPACE_TRT 4
+#define LBM_ORACLE_SPACE_NONE 5
 /* equilibrium format: deviation-only (Eq. 2.5) or absolute (Eq. 2.6) */
 #define LBM_ORACLE_EQ_DELTA 0
 #define LBM_ORACLE_EQ_ABSOLUTE 1

@@ -34,7 +34,7 @@ const aux_fn kAux[3][5] = {
     {lbm::launch_aux_2_0, lbm::launch_aux_2_1, lbm::launch_aux_2_2, lbm::launch_aux_2_3,
      lbm::launch_aux_2_4}};
 
-constexpr int G_PULL = 0, G_LOCAL = 1, G_AAODD = 2;
+constexpr int G_PULL = 0, G_LOCAL = 1, G_AAODD = 2, G_ET_EVEN = 3, G_ET_ODD = 4;
 constexpr uint64_t kStateMagic = 0x4c424d3253544154ull;  // "LBM2STAT"
 
 int q_of(int st) { return st == LBM_D2Q9 ? 9 : (st == LBM_D3Q19 ? 19 : 27); }
@@ -62,6 +62,7 @@ int cuda_err(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
 
 int gather_mode(const lbm_ctx* c) {
   if (c->p.streaming == LBM_PULL) return G_PULL;
+  if (c->p.streaming == LBM_ESOTERIC_TWIST) return c->parity ? G_ET_ODD : G_ET_EVEN;
   return c->parity ? G_AAODD : G_LOCAL;
 }
 void* state_buf(const lbm_ctx* c) {
@@ -70,8 +71,8 @@ void* state_buf(const lbm_ctx* c) {
 
 void set_effective_rates(lbm_ctx* c, const double* r) {
   for (int k = 0; k < 6; ++k) c->rates[k] = c->p.space == LBM_SPACE_POPULATIONS ? r[0] : r[k];
-  c->space = c->p.space;  // POPULATIONS is the population-space SRT kernel
-  c->reg = c->p.space != LBM_SPACE_POPULATIONS;
+  c->space = c->p.space;  // POPULATIONS / TRT: population-space kernels
+  c->reg = c->p.space != LBM_SPACE_POPULATIONS && c->p.space != LBM_SPACE_TRT;
   for (int k = 1; k < 6; ++k)
     if (c->rates[k] != 1.0) c->reg = 0;
 }
@@ -176,8 +177,8 @@ const char* lbm_error_string(int code) {
 int lbm_create(lbm_ctx** out, const lbm_params* p) {
   if (!out || !p) return LBM_ERR_INVALID;
   *out = nullptr;
-  if (p->stencil < 0 || p->stencil > 2 || p->space < 0 || p->space > 3 || p->storage < 0 ||
-      p->storage > 4 || p->streaming < 0 || p->streaming > 1 ||
+  if (p->stencil < 0 || p->stencil > 2 || p->space < 0 || p->space > 4 || p->storage < 0 ||
+      p->storage > 4 || p->streaming < 0 || p->streaming > 2 ||
       (p->equilibrium != LBM_EQ_DELTA && p->equilibrium != LBM_EQ_ABSOLUTE) ||
       (p->arithmetic != LBM_ARITH_DEVIATION && p->arithmetic != LBM_ARITH_AS_WRITTEN))
     return LBM_ERR_INVALID;
@@ -187,7 +188,7 @@ int lbm_create(lbm_ctx** out, const lbm_params* p) {
   if (p->storage == LBM_STORE_F64_ABSOLUTE && p->equilibrium == LBM_EQ_DELTA)
     return LBM_ERR_INADMISSIBLE;
   if ((p->storage == LBM_STORE_F64_ABSOLUTE || p->arithmetic == LBM_ARITH_AS_WRITTEN) &&
-      (p->streaming != LBM_PULL ||
+      (p->streaming != LBM_PULL || p->space == LBM_SPACE_TRT ||
        (p->storage != LBM_STORE_F64 && p->storage != LBM_STORE_F64_ABSOLUTE)))
     return LBM_ERR_UNSUPPORTED;
   if (p->boundary != LBM_PERIODIC) return LBM_ERR_UNSUPPORTED;
@@ -365,9 +366,11 @@ int lbm_get_time(const lbm_ctx* c, int64_t* step, int* parity) {
 }
 
 static int scatter(lbm_ctx* c, const double* df, const double* rho, const double* u) {
-  if (c->p.streaming == LBM_AA) c->parity = 0;
+  if (c->p.streaming != LBM_PULL) c->parity = 0;
   AuxArgs a = aux_base(c, lbm::AUX_SCATTER);
-  a.gather_mode = c->p.streaming == LBM_PULL ? G_PULL : G_LOCAL;
+  a.gather_mode = c->p.streaming == LBM_PULL
+                      ? G_PULL
+                      : (c->p.streaming == LBM_ESOTERIC_TWIST ? G_ET_EVEN : G_LOCAL);
   a.df_in = df;
   a.rho_in = rho;
   a.u_in = u;
@@ -468,7 +471,10 @@ int lbm_step(lbm_ctx* c, int64_t n) {
         fn(a);
       c->cur = 1 - c->cur;
     } else {
-      a.mode = c->parity ? lbm::MODE_AA_ODD : lbm::MODE_AA_EVEN;
+      if (c->p.streaming == LBM_ESOTERIC_TWIST)
+        a.mode = c->parity ? lbm::MODE_ET_ODD : lbm::MODE_ET_EVEN;
+      else
+        a.mode = c->parity ? lbm::MODE_AA_ODD : lbm::MODE_AA_EVEN;
       a.src = c->buf[0];
       a.dst = c->buf[0];
       fn(a);

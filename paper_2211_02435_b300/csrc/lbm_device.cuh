@@ -34,7 +34,7 @@
 namespace lbm {
 
 enum { D2Q9 = 0, D3Q19 = 1, D3Q27 = 2 };
-enum { SP_SRT = 0, SP_RAW = 1, SP_CENTRAL = 2, SP_CUMULANT = 3 };
+enum { SP_SRT = 0, SP_RAW = 1, SP_CENTRAL = 2, SP_CUMULANT = 3, SP_TRT = 4 };
 
 // ---------------------------------------------------------------- helpers
 template <class F, int... Is>
@@ -479,6 +479,18 @@ LBM_D void equilibrium(T drho, const T (&u)[3], T (&f)[q_of(ST)]);
 // ------------------------------------------------------------ collision
 // In: zero-centered pre-collision populations f.  Out: zero-centered
 // post-collision populations f*.  keep.om[g] = 1 - omega_g.
+// population-space collisions under DEFER: scale population i by
+// 2^(|xi_i|^2) as the deferred backward transform would have left it
+template <int ST, class T>
+LBM_D void defer_scale(T (&f)[q_of(ST)]) {
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    constexpr int k = vel(ST, i, 0) * vel(ST, i, 0) + vel(ST, i, 1) * vel(ST, i, 1) +
+                      vel(ST, i, 2) * vel(ST, i, 2);
+    if constexpr (k > 0) f[i] = f[i] * T(float(1 << k));
+  });
+}
+
 // Guo's population source of a body force F at velocity u (c_s^2 = 1/3):
 // S_i = w_i [3 (xi_i.F - u.F) + 9 (xi_i.u)(xi_i.F)]
 template <int ST, class T>
@@ -541,6 +553,38 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
         f[i] = feq[i] + keep.om[0] * (f[i] - feq[i]);
       });
     }
+    if constexpr (DEFER) defer_scale<ST, T>(f);
+    return;
+  } else if constexpr (SPACE == SP_TRT) {
+    // two relaxation times: per opposite pair the even part relaxes with
+    // keep.om[0] = 1 - w+, the odd part with keep.om[2] = 1 - w-
+    T feq[q_of(ST)], S[q_of(ST)];
+    equilibrium<ST, T, SP_RAW>(drho, u, feq);
+    if constexpr (FORCED) guo_source<ST, T>(u, Fv, S);
+    const T kp = keep.om[0], km = keep.om[2];
+    sfor<q_of(ST)>([&](auto I) {
+      constexpr int i = CI(I);
+      constexpr int b = opp(i);
+      if constexpr (i == b) {
+        f[i] = feq[i] + kp * (f[i] - feq[i]);
+        if constexpr (FORCED) f[i] += T(0.5) * (T(1) + kp) * S[i];
+      } else if constexpr (i < b) {
+        const T np = (f[i] + f[b]) - (feq[i] + feq[b]);
+        const T nm = (f[i] - f[b]) - (feq[i] - feq[b]);
+        const T ep = T(0.5) * (feq[i] + feq[b]), em = T(0.5) * (feq[i] - feq[b]);
+        const T rp = T(0.5) * (kp * np), rm = T(0.5) * (km * nm);
+        T fi = ep + em + rp + rm, fb = ep - em + rp - rm;
+        if constexpr (FORCED) {
+          const T sp = T(0.25) * (T(1) + kp) * (S[i] + S[b]);
+          const T sm = T(0.25) * (T(1) + km) * (S[i] - S[b]);
+          fi += sp + sm;
+          fb += sp - sm;
+        }
+        f[i] = fi;
+        f[b] = fb;
+      }
+    });
+    if constexpr (DEFER) defer_scale<ST, T>(f);
     return;
   } else if constexpr (SPACE == SP_RAW) {
     // non-equilibrium parts in the orthogonal basis, relax, transform back

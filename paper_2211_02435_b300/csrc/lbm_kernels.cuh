@@ -22,7 +22,15 @@ namespace lbm {
 #endif
 
 // how a kernel reads the canonical populations f(n) of a cell
-enum { G_PULL = 0, G_LOCAL = 1, G_AAODD = 2 };
+enum { G_PULL = 0, G_LOCAL = 1, G_AAODD = 2, G_ET_EVEN = 3, G_ET_ODD = 4 };
+
+// Esoteric Twist offset of direction i: a_i = max(-xi_i, 0) per component.
+// Population i of cell x lives at node x + a_i (slot i at even times, slot
+// ibar at odd times), so a cell touches itself and its positive neighbours.
+template <int ST, int i, int d>
+LBM_HD constexpr int et_off() {
+  return vel(ST, i, d) < 0 ? 1 : 0;
+}
 
 // absolute FP64 storage element (LBM_STORE_F64_ABSOLUTE): holds f_i itself
 struct AbsF64 {
@@ -96,8 +104,10 @@ LBM_D void load_pops(const S* buf, const Geo& g, const Nbr& n, int c, T (&f)[q_o
     constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1), cz = vel(ST, i, 2);
     int src_c = c;
     int slot = i;
-    if constexpr (MODE != G_LOCAL) src_c = cell_at(n, g, -cx, -cy, -cz);
-    if constexpr (MODE == G_AAODD) slot = opp(i);
+    if constexpr (MODE == G_PULL || MODE == G_AAODD) src_c = cell_at(n, g, -cx, -cy, -cz);
+    if constexpr (MODE == G_ET_EVEN || MODE == G_ET_ODD)
+      src_c = cell_at(n, g, et_off<ST, i, 0>(), et_off<ST, i, 1>(), et_off<ST, i, 2>());
+    if constexpr (MODE == G_AAODD || MODE == G_ET_ODD) slot = opp(i);
     const S v = buf[(int64_t)slot * g.N + src_c];
     f[i] = dec_pop<ST, i, S, T>(v);
   });
@@ -227,6 +237,41 @@ __global__ void __launch_bounds__(LBM_BX) k_aa(S* buf, Geo g, Rates<T> keep,
   });
 }
 
+// Esoteric Twist, in place on one buffer (Sec. 4.3).  With a_i = max(-xi_i, 0)
+// per component, cell x reads population i from node x + a_i (slot i at even
+// times, slot ibar at odd times) and writes f*_i to node x + a_ibar (slot
+// ibar at even times, slot i at odd times).  Node x + a_ibar, slot ibar (even)
+// is one the cell has just read, so each cell writes exactly the elements it
+// read and no two cells touch one element; at the next time the population
+// sits at x + xi_i + a_i, the same rule with the slots swapped.  Even and odd
+// steps differ only in the slot labels; every step reaches the cell and its
+// positive neighbours.
+template <int ST, class S, class T, int SPACE, bool REG, bool ODD, int FORCE = FORCE_NONE>
+__global__ void __launch_bounds__(LBM_BX) k_et(S* buf, Geo g, Rates<T> keep,
+                                               ForceArg<T> fa = {}) {
+  const int x = blockIdx.x * LBM_BX + threadIdx.x;
+  if (x >= g.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const Nbr n = neighbours(x, y, z, g);
+  const int c = (z * g.ny + y) * g.nx + x;
+  T f[q_of(ST)];
+  load_pops<ST, S, T, ODD ? G_ET_ODD : G_ET_EVEN>(buf, g, n, c, f);
+  if constexpr (FORCE != FORCE_NONE) {
+    T Fc[3];
+    cell_force<ST, FORCE>(fa, g, c, Fc);
+    collide<ST, T, SPACE, REG, false, true>(f, keep, Fc);
+  } else {
+    collide<ST, T, SPACE, REG>(f, keep);
+  }
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    constexpr int b = opp(i);
+    const int dc = cell_at(n, g, et_off<ST, b, 0>(), et_off<ST, b, 1>(), et_off<ST, b, 2>());
+    const int slot = ODD ? i : b;
+    buf[(int64_t)slot * g.N + dc] = enc_pop<ST, i, S, T>(f[i]);
+  });
+}
+
 // ------------------------------------------------------ read-out kernels
 // canonical populations -> FP64 SoA df[i * N + c] and / or macroscopic
 template <int ST, class S, class T, int MODE>
@@ -269,7 +314,7 @@ __global__ void __launch_bounds__(LBM_BX) k_gather(const S* buf, Geo g, double* 
 // rho / u when df is NULL) into the storage so that the next gather returns
 // them: pull -> buf[i][x - xi_i] (moved back upstream, where the pull
 // gather of cell x looks), AA -> buf[i][x] (even parity).
-template <int ST, class S, class T, int SPACE, bool PULL>
+template <int ST, class S, class T, int SPACE, int LAYOUT>
 __global__ void __launch_bounds__(LBM_BX) k_scatter(S* buf, Geo g, const double* df,
                                                     const double* rho, const double* u) {
   const int x = blockIdx.x * LBM_BX + threadIdx.x;
@@ -289,7 +334,9 @@ __global__ void __launch_bounds__(LBM_BX) k_scatter(S* buf, Geo g, const double*
   sfor<q_of(ST)>([&](auto I) {
     constexpr int i = CI(I);
     int dc = c;
-    if constexpr (PULL) dc = cell_at(n, g, -vel(ST, i, 0), -vel(ST, i, 1), -vel(ST, i, 2));
+    if constexpr (LAYOUT == G_PULL) dc = cell_at(n, g, -vel(ST, i, 0), -vel(ST, i, 1), -vel(ST, i, 2));
+    if constexpr (LAYOUT == G_ET_EVEN)
+      dc = cell_at(n, g, et_off<ST, i, 0>(), et_off<ST, i, 1>(), et_off<ST, i, 2>());
     buf[(int64_t)i * g.N + dc] = enc_pop<ST, i, S, T>(f[i]);
   });
 }
@@ -449,6 +496,16 @@ void launch_forced(const StepArgs& a, const Rates<T>& keep, const dim3& grid) {
       k_pull<ST, S, T, SPACE, false, FORM_DEV, FORCE_FIELD><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep, fa);
     else
       k_pull<ST, S, T, SPACE, false, FORM_DEV, FORCE_UNIFORM><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep, fa);
+  } else if (a.mode == MODE_ET_EVEN || a.mode == MODE_ET_ODD) {
+    const bool odd = a.mode == MODE_ET_ODD;
+    if (field && odd)
+      k_et<ST, S, T, SPACE, false, true, FORCE_FIELD><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
+    else if (field)
+      k_et<ST, S, T, SPACE, false, false, FORCE_FIELD><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
+    else if (odd)
+      k_et<ST, S, T, SPACE, false, true, FORCE_UNIFORM><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
+    else
+      k_et<ST, S, T, SPACE, false, false, FORCE_UNIFORM><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
   } else if (a.mode == MODE_AA_EVEN) {
     if (field)
       k_aa<ST, S, T, SPACE, false, false, FORCE_FIELD><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
@@ -489,9 +546,11 @@ void launch_step_typed(const StepArgs& a) {
       }
     }
     if constexpr (std::is_same<S, AbsF64>::value) {
-      k_pull<ST, S, T, SPACE, REG, FORM_ABS_STORE><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep);
+      // absolute forms serve SRT and the moment spaces (TRT is refused at create)
+      if constexpr (SPACE != SP_TRT)
+        k_pull<ST, S, T, SPACE, REG, FORM_ABS_STORE><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep);
       return;
-    } else if constexpr (std::is_same<S, double>::value) {
+    } else if constexpr (std::is_same<S, double>::value && SPACE != SP_TRT) {
       if (a.form == FORM_ABS_EQ) {
         k_pull<ST, S, T, SPACE, REG, FORM_ABS_EQ><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep);
         return;
@@ -509,6 +568,10 @@ void launch_step_typed(const StepArgs& a) {
     }
     k_pull<ST, S, T, SPACE, REG><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep);
   }
+  else if (a.mode == MODE_ET_EVEN)
+    k_et<ST, S, T, SPACE, REG, false><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep);
+  else if (a.mode == MODE_ET_ODD)
+    k_et<ST, S, T, SPACE, REG, true><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep);
   else if (a.mode == MODE_AA_EVEN)
     k_aa<ST, S, T, SPACE, REG, false><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep);
   else
@@ -525,7 +588,8 @@ void launch_step_space(const StepArgs& a) {
     case SP_CENTRAL * 2: launch_step_typed<ST, S, T, SP_CENTRAL, false>(a); break;
     case SP_CENTRAL * 2 + 1: launch_step_typed<ST, S, T, SP_CENTRAL, true>(a); break;
     case SP_CUMULANT * 2: launch_step_typed<ST, S, T, SP_CUMULANT, false>(a); break;
-    default: launch_step_typed<ST, S, T, SP_CUMULANT, true>(a); break;
+    case SP_CUMULANT * 2 + 1: launch_step_typed<ST, S, T, SP_CUMULANT, true>(a); break;
+    default: launch_step_typed<ST, S, T, SP_TRT, false>(a); break;
   }
 }
 
@@ -542,23 +606,26 @@ void launch_aux_typed(const AuxArgs& a) {
         k_gather<ST, S, T, G_PULL><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
       else if (gm == G_LOCAL)
         k_gather<ST, S, T, G_LOCAL><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
-      else
+      else if (gm == G_AAODD)
         k_gather<ST, S, T, G_AAODD><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
+      else if (gm == G_ET_EVEN)
+        k_gather<ST, S, T, G_ET_EVEN><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
+      else
+        k_gather<ST, S, T, G_ET_ODD><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
       break;
     }
     case AUX_SCATTER: {
-      const bool pull = gm == G_PULL;
-      if (a.space == SP_RAW || a.space == SP_SRT) {
-        if (pull)
-          k_scatter<ST, S, T, SP_RAW, true><<<grid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in);
+      const bool raw = a.space == SP_RAW || a.space == SP_SRT || a.space == SP_TRT;
+      auto go = [&](auto layout) {
+        constexpr int LY = decltype(layout)::value;
+        if (raw)
+          k_scatter<ST, S, T, SP_RAW, LY><<<grid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in);
         else
-          k_scatter<ST, S, T, SP_RAW, false><<<grid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in);
-      } else {
-        if (pull)
-          k_scatter<ST, S, T, SP_CENTRAL, true><<<grid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in);
-        else
-          k_scatter<ST, S, T, SP_CENTRAL, false><<<grid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in);
-      }
+          k_scatter<ST, S, T, SP_CENTRAL, LY><<<grid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in);
+      };
+      if (gm == G_PULL) go(std::integral_constant<int, G_PULL>{});
+      else if (gm == G_ET_EVEN) go(std::integral_constant<int, G_ET_EVEN>{});
+      else go(std::integral_constant<int, G_LOCAL>{});
       break;
     }
     case AUX_INVARIANTS:
@@ -566,8 +633,12 @@ void launch_aux_typed(const AuxArgs& a) {
         k_invariants<ST, S, T, G_PULL><<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
       else if (gm == G_LOCAL)
         k_invariants<ST, S, T, G_LOCAL><<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
-      else
+      else if (gm == G_AAODD)
         k_invariants<ST, S, T, G_AAODD><<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
+      else if (gm == G_ET_EVEN)
+        k_invariants<ST, S, T, G_ET_EVEN><<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
+      else
+        k_invariants<ST, S, T, G_ET_ODD><<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
       break;
   }
 }
@@ -575,7 +646,7 @@ void launch_aux_typed(const AuxArgs& a) {
 template <int ST, class S, class T, int SPACE, bool REG>
 void launch_batch_typed(const BatchArgs& a) {
   if (a.op == BATCH_TGV) {
-    k_batch_tgv<ST, S, T, (SPACE == SP_RAW || SPACE == SP_SRT ? SP_RAW : SP_CENTRAL)>
+    k_batch_tgv<ST, S, T, (SPACE == SP_RAW || SPACE == SP_SRT || SPACE == SP_TRT ? SP_RAW : SP_CENTRAL)>
         <<<a.grid, a.threads, 0, a.stream>>>((S*)a.dst, a.inst, a.tiles, a.ntiles, a.cpt, a.u0);
     return;
   }
@@ -595,7 +666,8 @@ void launch_batch_space(const BatchArgs& a) {
     case SP_CENTRAL * 2: launch_batch_typed<ST, S, T, SP_CENTRAL, false>(a); break;
     case SP_CENTRAL * 2 + 1: launch_batch_typed<ST, S, T, SP_CENTRAL, true>(a); break;
     case SP_CUMULANT * 2: launch_batch_typed<ST, S, T, SP_CUMULANT, false>(a); break;
-    default: launch_batch_typed<ST, S, T, SP_CUMULANT, true>(a); break;
+    case SP_CUMULANT * 2 + 1: launch_batch_typed<ST, S, T, SP_CUMULANT, true>(a); break;
+    default: launch_batch_typed<ST, S, T, SP_TRT, false>(a); break;
   }
 }
 

@@ -17,12 +17,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
 D2Q9, D3Q19, D3Q27 = 0, 1, 2
-SPACE_POPULATIONS, SPACE_RAW, SPACE_CENTRAL, SPACE_CUMULANT = 0, 1, 2, 3
+SPACE_POPULATIONS, SPACE_RAW, SPACE_CENTRAL, SPACE_CUMULANT, SPACE_TRT = 0, 1, 2, 3, 4
 EQ_DELTA, EQ_ABSOLUTE = 0, 1
 STORE_F64, STORE_F32, STORE_F16_DELTA, STORE_BF16_DELTA, STORE_F64_ABSOLUTE = 0, 1, 2, 3, 4
 ARITH_DEVIATION, ARITH_AS_WRITTEN = 0, 1
 STEP_AUTO, STEP_DIRECT, STEP_STAGED = 0, 1, 2
-PULL, AA = 0, 1
+PULL, AA, ESOTERIC_TWIST = 0, 1, 2
 PERIODIC = 0
 Q_OF = {D2Q9: 9, D3Q19: 19, D3Q27: 27}
 ELEM_BYTES = {STORE_F64: 8, STORE_F32: 4, STORE_F16_DELTA: 2, STORE_BF16_DELTA: 2,

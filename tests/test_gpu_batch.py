@@ -41,18 +41,20 @@ def rel_linf(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
+@pytest.mark.parametrize("space", [L.SPACE_RAW, L.SPACE_TRT])
 @pytest.mark.parametrize("storage,tol", [(L.STORE_F64, 1e-12), (L.STORE_F32, 1e-5)])
-def test_instances_match_oracle(storage, tol):
+def test_instances_match_oracle(storage, tol, space):
     dims, om, u0 = ensemble()
     nsteps = 5
-    with L.Batch(ST, L.SPACE_RAW, L.EQ_DELTA, storage, RATES, dims, om) as b:
+    rates = RATES if space == L.SPACE_RAW else [1.0, 1.0, 1.75, 1.0, 1.0, 1.0]
+    with L.Batch(ST, space, L.EQ_DELTA, storage, rates, dims, om) as b:
         for k in range(len(dims)):
             b.init_velocity(k, *host_fields(dims[k], u0[k]))
         b.step(nsteps)
         assert b.time() == nsteps
         rng = np.random.default_rng(8)
         for k in sorted(set([1, 2, 3] + list(rng.choice(len(dims), 5, replace=False)))):
-            m = O.method(O.D3Q19, O.SPACE_RAW, O.EQ_DELTA, [om[k]] + [1.0] * 5)
+            m = O.method(O.D3Q19, space, O.EQ_DELTA, [om[k]] + rates[1:])
             rho, u = I.taylor_green(dims[k], u0[k])
             ref = O.step(m, dims[k], O.init(m, dims[k], rho, u), nsteps)
             assert rel_linf(b.get_populations(k), ref) < tol, k
@@ -103,7 +105,7 @@ def test_device_taylor_green_setup_matches_host_fields():
     with L.Batch(ST, L.SPACE_RAW, L.EQ_DELTA, L.STORE_F64, RATES, dims, om) as b:
         b.init_tgv(u0)
         for k in range(len(dims)):
-            m = O.method(O.D3Q19, O.SPACE_RAW, O.EQ_DELTA, [om[k]] + [1.0] * 5)
+            m = O.method(O.D3Q19, space, O.EQ_DELTA, [om[k]] + rates[1:])
             rho, u = I.taylor_green(dims[k], u0[k])
             ref = O.init(m, dims[k], rho, u)
             assert rel_linf(b.get_populations(k), ref) < 1e-13

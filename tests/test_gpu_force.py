@@ -25,6 +25,7 @@ METHODS = [  # (space, equilibrium, rates)
     (L.SPACE_RAW, L.EQ_DELTA, "gen"), (L.SPACE_RAW, L.EQ_ABSOLUTE, "unit"),
     (L.SPACE_CENTRAL, L.EQ_DELTA, "gen"), (L.SPACE_CENTRAL, L.EQ_ABSOLUTE, "unit"),
     (L.SPACE_CUMULANT, L.EQ_ABSOLUTE, "gen"), (L.SPACE_CUMULANT, L.EQ_ABSOLUTE, "unit"),
+    (L.SPACE_TRT, L.EQ_DELTA, "trt"),
 ]
 
 
@@ -35,7 +36,8 @@ def _built():
 
 
 def rates_of(kind):
-    return {"srt": [1.6] * 6, "gen": RATES_GEN, "unit": RATES_UNIT}[kind]
+    return {"srt": [1.6] * 6, "gen": RATES_GEN, "unit": RATES_UNIT,
+            "trt": [1.3, 1.0, 1.75, 1.0, 1.0, 1.0]}[kind]
 
 
 def rel_linf(a, b):
@@ -75,7 +77,7 @@ def case(st, mi, fkind):
 
 
 @pytest.mark.parametrize("fkind", ["uniform", "field"])
-@pytest.mark.parametrize("streaming", [L.PULL, L.AA])
+@pytest.mark.parametrize("streaming", [L.PULL, L.AA, L.ESOTERIC_TWIST])
 @pytest.mark.parametrize("storage", [L.STORE_F64, L.STORE_F32])
 @pytest.mark.parametrize("mi", range(len(METHODS)),
                          ids=[f"sp{m[0]}eq{m[1]}{m[2]}" for m in METHODS])

@@ -33,7 +33,9 @@ METHODS = [  # (space, equilibrium, regularised)
     (L.SPACE_CENTRAL, L.EQ_DELTA, False), (L.SPACE_CENTRAL, L.EQ_ABSOLUTE, True),
     (L.SPACE_CENTRAL, L.EQ_ABSOLUTE, False),
     (L.SPACE_CUMULANT, L.EQ_ABSOLUTE, False), (L.SPACE_CUMULANT, L.EQ_ABSOLUTE, True),
+    (L.SPACE_TRT, L.EQ_DELTA, False), (L.SPACE_TRT, L.EQ_ABSOLUTE, False),
 ]
+RATES_TRT = [1.3, 1.0, 1.75, 1.0, 1.0, 1.0]  # w+ (even part), w- (odd part) in slot 2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -45,6 +47,8 @@ def _built():
 def rates_of(space, reg):
     if space == L.SPACE_POPULATIONS:
         return [1.6] * 6
+    if space == L.SPACE_TRT:
+        return RATES_TRT
     return RATES_REG if reg else RATES_GEN
 
 
@@ -77,7 +81,7 @@ def gpu_lattice(st, space, eq, reg, storage, streaming):
     return L.Lattice(st, space, eq, storage, streaming, rates_of(space, reg), DIMS[st])
 
 
-@pytest.mark.parametrize("streaming", [L.PULL, L.AA])
+@pytest.mark.parametrize("streaming", [L.PULL, L.AA, L.ESOTERIC_TWIST])
 @pytest.mark.parametrize("storage", [L.STORE_F64, L.STORE_F32])
 @pytest.mark.parametrize("method", METHODS, ids=lambda m: f"sp{m[0]}eq{m[1]}reg{int(m[2])}")
 @pytest.mark.parametrize("st", [0, 1, 2], ids=["D2Q9", "D3Q19", "D3Q27"])
@@ -101,12 +105,12 @@ def test_step_parity(st, method, storage, streaming):
             rho_g, u_g = lat.macroscopic()
             assert rel_linf(u_g, u_r) < TOL[storage]
             assert rel_linf(rho_g - 1, rho_r - 1) < TOL[storage]
-            assert lat.time() == (n, (n % 2) if streaming == L.AA else 0)
+            assert lat.time() == (n, (n % 2) if streaming != L.PULL else 0)
 
 
 @pytest.mark.parametrize("space", [L.SPACE_RAW, L.SPACE_CENTRAL, L.SPACE_CUMULANT])
 @pytest.mark.parametrize("st", [0, 1, 2])
-@pytest.mark.parametrize("streaming", [L.PULL, L.AA])
+@pytest.mark.parametrize("streaming", [L.PULL, L.AA, L.ESOTERIC_TWIST])
 def test_init_velocity_is_the_method_equilibrium(st, space, streaming):
     eq = L.EQ_DELTA if space == L.SPACE_RAW else L.EQ_ABSOLUTE
     dims = DIMS[st]
@@ -129,18 +133,20 @@ def test_init_velocity_is_the_method_equilibrium(st, space, streaming):
 
 @pytest.mark.parametrize("storage", [L.STORE_F32, L.STORE_F64])
 def test_pull_and_aa_are_bitwise_identical(storage):
+    """Pull, AA and Esoteric Twist run the same per-cell arithmetic."""
     st, space, eq, reg = 2, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, False
     _, dims, df0 = initial_state(st, space, eq, reg)
     out = []
-    for streaming in (L.PULL, L.AA):
+    for streaming in (L.PULL, L.AA, L.ESOTERIC_TWIST):
         with gpu_lattice(st, space, eq, reg, storage, streaming) as lat:
             lat.set_populations(df0)
             lat.step(5)
             out.append(lat.get_populations())
     assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[2])
 
 
-@pytest.mark.parametrize("streaming", [L.PULL, L.AA])
+@pytest.mark.parametrize("streaming", [L.PULL, L.AA, L.ESOTERIC_TWIST])
 def test_checkpoint_resume_is_bitwise(streaming):
     st, space, eq, reg = 1, L.SPACE_RAW, L.EQ_DELTA, False
     _, dims, df0 = initial_state(st, space, eq, reg)
@@ -152,7 +158,7 @@ def test_checkpoint_resume_is_bitwise(streaming):
         straight = a.get_populations()
     with gpu_lattice(st, space, eq, reg, L.STORE_F32, streaming) as b:
         b.set_state(state)
-        assert b.time() == (3, 1 if streaming == L.AA else 0)
+        assert b.time() == (3, 1 if streaming != L.PULL else 0)
         b.step(4)
         assert np.array_equal(b.get_populations(), straight)
     # a state of another configuration is refused
@@ -221,7 +227,7 @@ def test_device_pointer_path_matches_host_path():
 
 @pytest.mark.parametrize("storage,p", [(L.STORE_F16_DELTA, 10), (L.STORE_BF16_DELTA, 7)])
 @pytest.mark.parametrize("space", [L.SPACE_CENTRAL, L.SPACE_CUMULANT])
-@pytest.mark.parametrize("streaming", [L.PULL, L.AA])
+@pytest.mark.parametrize("streaming", [L.PULL, L.AA, L.ESOTERIC_TWIST])
 def test_half_storage_error_bound(storage, p, space, streaming):
     """FP16 / BF16 delta storage: every store rounds each scaled deviation
     to p explicit mantissa bits, an error of at most 2^-(p+1) of |df_i|;
@@ -266,7 +272,7 @@ EVEN_DIMS = {0: (134, 37, 1), 1: (134, 6, 5), 2: (134, 6, 5)}
 
 
 @pytest.mark.parametrize("storage,p", [(L.STORE_F16_DELTA, 10), (L.STORE_BF16_DELTA, 7)])
-@pytest.mark.parametrize("method", METHODS[1:], ids=lambda m: f"sp{m[0]}eq{m[1]}reg{int(m[2])}")
+@pytest.mark.parametrize("method", METHODS, ids=lambda m: f"sp{m[0]}eq{m[1]}reg{int(m[2])}")
 @pytest.mark.parametrize("st", [0, 1, 2], ids=["D2Q9", "D3Q19", "D3Q27"])
 def test_packed_half_kernel_error_bound(st, method, storage, p):
     """Even Nx routes FP16 / BF16 pull steps to the two-cells-per-thread

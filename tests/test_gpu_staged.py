@@ -56,6 +56,7 @@ CASES = [  # (stencil, space, eq, rates, dims)
     (0, L.SPACE_RAW, L.EQ_DELTA, RATES_REG, (256, 37, 1)),
     (0, L.SPACE_POPULATIONS, L.EQ_DELTA, [1.6] * 6, (24, 11, 1)),
     (2, L.SPACE_POPULATIONS, L.EQ_DELTA, [1.6] * 6, (16, 2, 3)),
+    (1, L.SPACE_TRT, L.EQ_DELTA, [1.3, 1.0, 1.75, 1.0, 1.0, 1.0], (32, 5, 3)),
 ]
 
 
