@@ -86,6 +86,12 @@ def lib():
         L.lbm_oracle_collide_forced.argtypes = [m, ctypes.c_int64, d, d, d]
         L.lbm_oracle_step_forced.argtypes = [m, i64, d, d, ctypes.c_int64, ctypes.c_int]
         L.lbm_oracle_macroscopic_forced.argtypes = [m, i64, d, d, d, d]
+        L.lbm_oracle_swe_equilibrium.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                 d, d]
+        L.lbm_oracle_swe_collide.argtypes = [m, ctypes.c_double, ctypes.c_int64, d, d]
+        L.lbm_oracle_swe_init.argtypes = [m, ctypes.c_double, i64, d, d, d]
+        L.lbm_oracle_swe_step.argtypes = [m, ctypes.c_double, i64, d, ctypes.c_int64,
+                                          ctypes.c_int]
         L.lbm_oracle_closure_features.argtypes = [ctypes.c_int, d, ctypes.c_double, d]
         L.lbm_oracle_closure_mlp.argtypes = [d, d, d, d, d]
         L.lbm_oracle_closure_step.argtypes = [m, i64, d, d, d, d, ctypes.c_int]
@@ -266,6 +272,46 @@ def macroscopic(m, dims, df):
                                         _dp(_f64(df)), _dp(rho), _dp(u)))
     shp = (dm[2], dm[1], dm[0])
     return rho.reshape(shp), u.reshape((d,) + shp)
+
+
+# ------------------------------------------------------------ shallow water
+def swe_equilibrium(space, g, h, u):
+    """Absolute D2Q9 equilibrium populations [9] of the shallow-water method
+    (SPACE_CENTRAL: Zhou's discrete f_eq; SPACE_CUMULANT: Maxwellian with
+    c_s^2 = g h / 2) at depth h and velocity u[2]."""
+    out = np.zeros(9)
+    _check(lib().lbm_oracle_swe_equilibrium(int(space), float(g), float(h),
+                                            _dp(_f64(np.asarray(u, dtype=np.float64)[:2])), _dp(out)))
+    return out
+
+
+def swe_collide(m, g, df):
+    df = _f64(df)
+    flat = df.reshape(-1, 9)
+    out = np.empty_like(flat)
+    _check(lib().lbm_oracle_swe_collide(ctypes.byref(m), float(g), flat.shape[0], _dp(flat),
+                                        _dp(out)))
+    return out.reshape(df.shape)
+
+
+def swe_init(m, g, dims, h, u):
+    dm = _dims(dims)
+    N = int(np.prod(dm))
+    df = np.empty((9, N))
+    _check(lib().lbm_oracle_swe_init(ctypes.byref(m), float(g),
+                                     dm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                     _dp(_f64(h).reshape(N)), _dp(_f64(u).reshape(-1, N)),
+                                     _dp(df)))
+    return df.reshape(9, dm[2], dm[1], dm[0])
+
+
+def swe_step(m, g, dims, df, nsteps, nthreads=0):
+    dm = _dims(dims)
+    out = _f64(df).copy()
+    _check(lib().lbm_oracle_swe_step(ctypes.byref(m), float(g),
+                                     dm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                     _dp(out), int(nsteps), int(nthreads)))
+    return out
 
 
 # ------------------------------------------------------------ learned closure

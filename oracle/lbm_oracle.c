@@ -430,8 +430,12 @@ static void add_first_order(const lattice_t* L, const double* F, double* v) {
  *   cumulants:         orders >= 2 are translation invariant and relax as
  *                      without force; the first-order cumulant (the mean
  *                      velocity) leaves the collision as (j + F) / rho. */
+static void swe_zhou_feq(const lattice_t* L, double h, const double* u,
+                         double g, double* feq);
+
 static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
-                          const double* df, const double* F, double* out) {
+                          const double* df, const double* F, double swe_g,
+                          double* out) {
   const int q = L->q;
   /* conserved quantities from the deviations, Eq. 2.3, rho0 = 1 */
   double drho = 0.0, j[3] = {0, 0, 0}, u[3];
@@ -535,8 +539,14 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
       } else { /* Eq. 2.6 */
         for (int i = 0; i < q; ++i) f[i] = df[i] + L->w[i];
         matvec(q, K, f, tmp);
-        for (int k = 0; k < q; ++k)
-          veq[k] = maxwell_central_moment(L->expo[k], rho);
+        if (swe_g > 0.0) { /* shallow water: central moments of Zhou's f_eq */
+          double fz[QMAX];
+          swe_zhou_feq(L, rho, u, swe_g, fz);
+          matvec(q, K, fz, veq);
+        } else {
+          for (int k = 0; k < q; ++k)
+            veq[k] = maxwell_central_moment(L->expo[k], rho);
+        }
         relax(L, m, L->Pcm, L->Pcminv, tmp, veq, vout);
         add_first_order(L, F, vout);
         matvec(q, Kinv, vout, tmp2);
@@ -570,7 +580,7 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
           veq[k] = v[k];
         else
           veq[k] = (L->deg[k] == 2 && (e[0] == 2 || e[1] == 2 || e[2] == 2))
-                       ? rho_a / 3.0
+                       ? rho_a * (swe_g > 0.0 ? 0.5 * swe_g * rho_a : 1.0 / 3.0)
                        : 0.0;
       }
       relax(L, m, L->Pcm, L->Pcminv, v, veq, vout);
@@ -597,7 +607,7 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
 
 static int collide_cell(const lattice_t* L, const lbm_oracle_method* m,
                         const double* df, double* out) {
-  return collide_cell_f(L, m, df, NULL, out);
+  return collide_cell_f(L, m, df, NULL, 0.0, out);
 }
 
 static int check_method(const lbm_oracle_method* m) {
@@ -732,7 +742,7 @@ int lbm_oracle_collide_forced(const lbm_oracle_method* m, int64_t ncells,
   for (int64_t c = 0; c < ncells; ++c) {
     double tmp[QMAX], F[3] = {0, 0, 0};
     for (int d = 0; d < L->d; ++d) F[d] = force[c * 3 + d];
-    rc = collide_cell_f(L, m, df_in + c * L->q, F, tmp);
+    rc = collide_cell_f(L, m, df_in + c * L->q, F, 0.0, tmp);
     if (rc) return rc;
     memcpy(df_out + c * L->q, tmp, sizeof(double) * L->q);
   }
@@ -785,9 +795,19 @@ int lbm_oracle_step(const lbm_oracle_method* m, const int64_t* dims,
   return lbm_oracle_step_forced(m, dims, df, NULL, nsteps, nthreads);
 }
 
+static int step_impl(const lbm_oracle_method* m, const int64_t* dims,
+                     double* df, const double* force, double swe_g,
+                     int64_t nsteps, int nthreads);
+
 int lbm_oracle_step_forced(const lbm_oracle_method* m, const int64_t* dims,
                            double* df, const double* force, int64_t nsteps,
                            int nthreads) {
+  return step_impl(m, dims, df, force, 0.0, nsteps, nthreads);
+}
+
+static int step_impl(const lbm_oracle_method* m, const int64_t* dims,
+                     double* df, const double* force, double swe_g,
+                     int64_t nsteps, int nthreads) {
   int rc = check_method(m);
   if (rc) return rc;
   if (force && m->space == LBM_ORACLE_SPACE_NONE) return -1;
@@ -813,7 +833,7 @@ int lbm_oracle_step_forced(const lbm_oracle_method* m, const int64_t* dims,
       for (int i = 0; i < q; ++i) in[i] = df[i * N + c];
       if (force)
         for (int d = 0; d < L->d; ++d) F[d] = force[d * N + c];
-      if (collide_cell_f(L, m, in, force ? F : NULL, post)) err |= 1;
+      if (collide_cell_f(L, m, in, force ? F : NULL, swe_g, post)) err |= 1;
       /* Eq. 2.1b: f_i(x + xi_i, t + 1) = f*_i(x, t), periodic */
       for (int i = 0; i < q; ++i) {
         int64_t xd = (x + L->xi[i][0] + nx) % nx;
@@ -1023,4 +1043,106 @@ double lbm_oracle_closure_loss(const lbm_oracle_method* base,
   free(u1);
   free(u2);
   return loss;
+}
+
+/* ------------------------------------------------------------------ */
+/* shallow water (Sec. 5.2): D2Q9, depth h = sum f, h u = sum xi f       */
+/* ------------------------------------------------------------------ */
+/* Zhou's discrete equilibrium (Sec. 5.2): rest f0 = h (1 - 5gh/6 - 2u.u/3),
+ * moving f_i = l_i h (gh/6 + xi.u/3 + (xi.u)^2/2 - u.u/6), l_i = 1 on the
+ * axes and 1/4 on the diagonals. */
+static void swe_zhou_feq(const lattice_t* L, double h, const double* u,
+                         double g, double* feq) {
+  const double uu = u[0] * u[0] + u[1] * u[1];
+  for (int i = 0; i < L->q; ++i) {
+    const int s = abs(L->xi[i][0]) + abs(L->xi[i][1]);
+    const double cu = L->xi[i][0] * u[0] + L->xi[i][1] * u[1];
+    if (s == 0)
+      feq[i] = h * (1.0 - 5.0 * g * h / 6.0 - 2.0 * uu / 3.0);
+    else
+      feq[i] = (s == 1 ? 1.0 : 0.25) * h *
+               (g * h / 6.0 + cu / 3.0 + 0.5 * cu * cu - uu / 6.0);
+  }
+}
+
+/* continuous Maxwellian of variance c2 per axis (the cumulant method's
+ * equilibrium with c_s^2 = g h / 2), as D2Q9 populations */
+static void swe_maxwell_feq(const lattice_t* L, double h, const double* u,
+                            double c2, double* feq) {
+  double m[QMAX];
+  for (int k = 0; k < L->q; ++k) {
+    double p = h;
+    for (int d = 0; d < 2; ++d) {
+      const int e = L->expo[k][d];
+      p *= e == 0 ? 1.0 : (e == 1 ? u[d] : u[d] * u[d] + c2);
+    }
+    m[k] = p;
+  }
+  matvec(L->q, L->Minv, m, feq);
+}
+
+static int swe_check(const lbm_oracle_method* m, double g) {
+  int rc = check_method(m);
+  if (rc) return rc;
+  if (m->stencil != LBM_ORACLE_D2Q9 || !(g > 0.0) ||
+      m->equilibrium != LBM_ORACLE_EQ_ABSOLUTE ||
+      (m->space != LBM_ORACLE_SPACE_CENTRAL &&
+       m->space != LBM_ORACLE_SPACE_CUMULANT))
+    return -1;
+  return 0;
+}
+
+int lbm_oracle_swe_equilibrium(int space, double g, double h, const double* u,
+                               double* f) {
+  if (build_lattice(LBM_ORACLE_D2Q9) || !u || !f || !(g > 0.0)) return -1;
+  const lattice_t* L = &g_lat[LBM_ORACLE_D2Q9];
+  const double uu[3] = {u[0], u[1], 0.0};
+  if (space == LBM_ORACLE_SPACE_CENTRAL)
+    swe_zhou_feq(L, h, uu, g, f);
+  else if (space == LBM_ORACLE_SPACE_CUMULANT)
+    swe_maxwell_feq(L, h, uu, 0.5 * g * h, f);
+  else
+    return -1;
+  return 0;
+}
+
+int lbm_oracle_swe_collide(const lbm_oracle_method* m, double g, int64_t ncells,
+                           const double* df_in, double* df_out) {
+  int rc = swe_check(m, g);
+  if (rc) return rc;
+  const lattice_t* L = &g_lat[m->stencil];
+  for (int64_t c = 0; c < ncells; ++c) {
+    double tmp[QMAX];
+    rc = collide_cell_f(L, m, df_in + c * L->q, NULL, g, tmp);
+    if (rc) return rc;
+    memcpy(df_out + c * L->q, tmp, sizeof(double) * L->q);
+  }
+  return 0;
+}
+
+int lbm_oracle_swe_init(const lbm_oracle_method* m, double g,
+                        const int64_t* dims, const double* h, const double* u,
+                        double* df) {
+  int rc = swe_check(m, g);
+  if (rc) return rc;
+  const lattice_t* L = &g_lat[m->stencil];
+  const int64_t N = dims[0] * dims[1] * dims[2];
+  for (int64_t c = 0; c < N; ++c) {
+    const double uc[3] = {u[c], u[N + c], 0.0};
+    double fe[QMAX];
+    if (m->space == LBM_ORACLE_SPACE_CENTRAL)
+      swe_zhou_feq(L, h[c], uc, g, fe);
+    else
+      swe_maxwell_feq(L, h[c], uc, 0.5 * g * h[c], fe);
+    for (int i = 0; i < L->q; ++i) df[i * N + c] = fe[i] - L->w[i];
+  }
+  return 0;
+}
+
+int lbm_oracle_swe_step(const lbm_oracle_method* m, double g,
+                        const int64_t* dims, double* df, int64_t nsteps,
+                        int nthreads) {
+  int rc = swe_check(m, g);
+  if (rc) return rc;
+  return step_impl(m, dims, df, NULL, g, nsteps, nthreads);
 }

@@ -149,6 +149,30 @@ int lbm_oracle_macroscopic_forced(const lbm_oracle_method* m,
                                   const int64_t* dims, const double* df,
                                   const double* force, double* rho, double* u);
 
+/* Shallow-water methods (Sec. 5.2), D2Q9 only, depth h = sum f and
+ * h u = sum xi f, gravity g in lattice units, absolute equilibrium:
+ *   space CENTRAL  (de Rosis): central moments relax towards those of
+ *                  Zhou's discrete equilibrium
+ *                  f0 = h (1 - 5gh/6 - 2u.u/3),
+ *                  f_i = l_i h (gh/6 + xi.u/3 + (xi.u)^2/2 - u.u/6),
+ *                  l_i = 1 (axes), 1/4 (diagonals);
+ *   space CUMULANT (Venturi): the cumulant collision with the continuous
+ *                  Maxwellian of c_s^2 = g h / 2 (second-order equilibrium
+ *                  cumulants h * g h / 2, higher ones 0).
+ * Populations in and out are still df = f - w (w the D2Q9 weights), so
+ * lbm_oracle_macroscopic returns (h, u).  swe_equilibrium: absolute f[9]
+ * of the method's equilibrium at (h, u[2]). */
+int lbm_oracle_swe_equilibrium(int space, double g, double h, const double* u,
+                               double* f);
+int lbm_oracle_swe_collide(const lbm_oracle_method* m, double g, int64_t ncells,
+                           const double* df_in, double* df_out);
+int lbm_oracle_swe_init(const lbm_oracle_method* m, double g,
+                        const int64_t* dims, const double* h, const double* u,
+                        double* df);
+int lbm_oracle_swe_step(const lbm_oracle_method* m, double g,
+                        const int64_t* dims, double* df, int64_t nsteps,
+                        int nthreads);
+
 /* ------------------------------------------------------------------ */
 /* Learned closure (not in the paper): a per-cell MLP 7 -> 32 -> 32 -> 4 */
 /* sets the relaxation rates of orders 3..6 of the cumulant collision.    */
