@@ -273,6 +273,24 @@ int lbm_set_stream(lbm_ctx* ctx, void* stream);
 int lbm_set_force(lbm_ctx* ctx, const double* F);
 int lbm_set_force_field(lbm_ctx* ctx, const double* F, int on_device);
 
+/* Shallow-water methods (Sec. 5.2), g > 0 the gravity in lattice units
+ * (g = 0 returns to the context's own method).  The context must be D2Q9,
+ * LBM_STORE_F64_ABSOLUTE, LBM_EQ_ABSOLUTE, pull, space CENTRAL or CUMULANT,
+ * without a body force; otherwise LBM_ERR_UNSUPPORTED.  The conserved density
+ * becomes the water depth h = sum f and the velocity u = sum xi f / h;
+ *   CENTRAL  (de Rosis): central moments relax towards those of Zhou's
+ *            discrete equilibrium f0 = h (1 - 5gh/6 - 2u.u/3),
+ *            f_i = l_i h (gh/6 + xi.u/3 + (xi.u)^2/2 - u.u/6),
+ *            l_i = 1 on the axes, 1/4 on the diagonals;
+ *   CUMULANT (Venturi): the cumulant collision whose second-order
+ *            equilibrium cumulants are h * g h / 2 (the continuous Maxwellian
+ *            with c_s^2 = g h / 2), higher ones 0.
+ * rates[0] relaxes xy and x^2 - y^2, rates[1] x^2 + y^2, rates[2..3] orders
+ * 3 and 4.  lbm_init_velocity(rho = h, u) installs the method's equilibrium;
+ * lbm_macroscopic returns (h, u); populations read or written are still
+ * f - w.  Errors: INVALID, UNSUPPORTED. */
+int lbm_set_shallow_water(lbm_ctx* ctx, double g);
+
 /* Pull step kernel.  Both compute the same per-cell arithmetic (FP16/BF16
  * storage: bitwise-identical states; FP32/FP64: equal up to the compiler's
  * choice of multiply-add contractions); they differ in how the gather of

@@ -95,6 +95,7 @@ AuxArgs aux_base(const lbm_ctx* c, int op) {
   a.force_mode = c->force_mode;
   for (int d = 0; d < 3; ++d) a.force[d] = c->force[d];
   a.force_field = c->force_field;
+  a.swe_g = c->swe_g;
   a.stream = c->stream;
   return a;
 }
@@ -274,7 +275,7 @@ __global__ void k_f64_to_f32(const double* in, float* out, int64_t n) {
 
 bool force_served(const lbm_ctx* c) {
   return (c->p.storage == LBM_STORE_F64 || c->p.storage == LBM_STORE_F32) &&
-         c->p.arithmetic == LBM_ARITH_DEVIATION && !c->closure;
+         c->p.arithmetic == LBM_ARITH_DEVIATION && !c->closure && !(c->swe_g > 0.0);
 }
 
 void update_force_mode(lbm_ctx* c) {
@@ -341,6 +342,17 @@ int lbm_set_force_field(lbm_ctx* c, const double* F, int on_device) {
   if (c->force_field) cudaFree(c->force_field);
   c->force_field = dev;
   update_force_mode(c);
+  return LBM_OK;
+}
+
+int lbm_set_shallow_water(lbm_ctx* c, double g) {
+  if (!c || !(g >= 0.0) || !std::isfinite(g)) return LBM_ERR_INVALID;
+  if (g > 0.0 &&
+      (c->p.stencil != LBM_D2Q9 || c->p.storage != LBM_STORE_F64_ABSOLUTE ||
+       c->p.equilibrium != LBM_EQ_ABSOLUTE || c->p.streaming != LBM_PULL ||
+       (c->p.space != LBM_SPACE_CENTRAL && c->p.space != LBM_SPACE_CUMULANT) || c->force_mode))
+    return LBM_ERR_UNSUPPORTED;
+  c->swe_g = g;
   return LBM_OK;
 }
 
@@ -458,6 +470,8 @@ int lbm_step(lbm_ctx* c, int64_t n) {
   for (int d = 0; d < 3; ++d) a.force[d] = c->force[d];
   a.force_field = c->force_field;
   if (c->force_mode) a.reg = 0;  // forced kernels: the general instantiation
+  a.swe_g = c->swe_g;
+  if (c->swe_g > 0.0) a.reg = 0;  // shallow water: the general instantiation
   a.stream = c->stream;
   const step_fn fn = kStep[c->p.stencil][c->p.storage];
   for (int64_t s = 0; s < n; ++s) {

@@ -766,8 +766,42 @@ LBM_D void equilibrium(T drho, const T (&u)[3], T (&f)[q_of(ST)]) {
 //     (M is linear), and T^-1(q*) - f0 as M^-1 (raw moments of q* - M f0);
 //     the conserved moments keep their deviation values.  Population-space
 //     SRT (T = identity) adds and subtracts f0 = w itself.
-template <int ST, class T, int SPACE, bool REG, bool ZC = false>
-LBM_D void collide_abs(T (&f)[q_of(ST)], const Rates<T>& keep) {
+// Absolute equilibrium populations of the shallow-water methods (D2Q9,
+// Sec. 5.2): CENTRAL -> Zhou's discrete equilibrium
+// f0 = h (1 - 5gh/6 - 2u.u/3), f_i = l_i h (gh/6 + xi.u/3 + (xi.u)^2/2 -
+// u.u/6) with l_i = 1 on the axes and 1/4 on the diagonals; CUMULANT -> the
+// continuous Maxwellian of c_s^2 = g h / 2 (per axis E[1] = 1, E[x] = u,
+// E[x^2] = u^2 + c_s^2).
+template <int ST, class T, int SPACE>
+LBM_D void swe_feq(T h, const T (&u)[3], T g, T (&f)[q_of(ST)]) {
+  static_assert(ST == D2Q9, "shallow water is two-dimensional");
+  if constexpr (SPACE == SP_CENTRAL) {
+    const T uu = u[0] * u[0] + u[1] * u[1];
+    sfor<q_of(ST)>([&](auto I) {
+      constexpr int i = CI(I);
+      constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1);
+      constexpr int sabs = (cx < 0 ? -cx : cx) + (cy < 0 ? -cy : cy);
+      const T cu = T(cx) * u[0] + T(cy) * u[1];
+      if constexpr (sabs == 0)
+        f[i] = h * (T(1) - T(5.0 / 6.0) * g * h - T(2.0 / 3.0) * uu);
+      else
+        f[i] = T(sabs == 1 ? 1.0 : 0.25) * h *
+               (g * h * T(1.0 / 6.0) + cu * T(1.0 / 3.0) + T(0.5) * cu * cu - uu * T(1.0 / 6.0));
+    });
+  } else {
+    const T c2 = T(0.5) * g * h;
+    const T e[3][2] = {{T(1), T(1)}, {u[0], u[1]}, {u[0] * u[0] + c2, u[1] * u[1] + c2}};
+    T A[3][3][3];
+    sfor<27>([&](auto K) {
+      constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+      A[a][b][c] = c == 0 ? h * e[a][0] * e[b][1] : T(0);
+    });
+    bwd_raw<ST, T>(A, f);
+  }
+}
+
+template <int ST, class T, int SPACE, bool REG, bool ZC = false, bool SWE = false>
+LBM_D void collide_abs(T (&f)[q_of(ST)], const Rates<T>& keep, T swe_g = T(0)) {
   if constexpr (ZC && SPACE == SP_SRT) {
     sfor<q_of(ST)>([&](auto I) { f[CI(I)] += T(weight(ST, CI(I))); });
   }
@@ -871,18 +905,49 @@ LBM_D void collide_abs(T (&f)[q_of(ST)], const Rates<T>& keep) {
     // equilibrium: Gaussian moments bg3 (central) / 1/3 on the 2nd-order
     // diagonal and 0 above (cumulants)
     T X[3][3][3], Xeq[3][3][3];
-    if constexpr (SPACE == SP_CENTRAL) {
+    if constexpr (SPACE == SP_CENTRAL && SWE) {
+      // shallow water (de Rosis): normalised central moments of Zhou's
+      // discrete equilibrium about the same u
+      T fe[q_of(ST)];
+      swe_feq<ST, T, SP_CENTRAL>(rho, u, swe_g, fe);
+      T E[3][3][3];
+      fwd_raw_chimera<ST, T>(fe, E);
+      if constexpr (dim_of(ST) == 3) {
+        sfor<9>([&](auto K) {
+          binom3<-1, T, 0>(E[CI(K) / 3][CI(K) % 3][0], E[CI(K) / 3][CI(K) % 3][1],
+                           E[CI(K) / 3][CI(K) % 3][2], u[2], u2[2], T(0));
+        });
+      }
+      sfor<9>([&](auto K) {
+        constexpr int a = CI(K) / 3, c = CI(K) % 3;
+        if constexpr (dim_of(ST) == 3 || c == 0)
+          binom3<-1, T, 0>(E[a][0][c], E[a][1][c], E[a][2][c], u[1], u2[1], T(0));
+      });
+      sfor<9>([&](auto K) {
+        constexpr int b = CI(K) / 3, c = CI(K) % 3;
+        if constexpr (dim_of(ST) == 3 || c == 0)
+          binom3<-1, T, 0>(E[0][b][c], E[1][b][c], E[2][b][c], u[0], u2[0], T(0));
+      });
+      sfor<27>([&](auto K) {
+        constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+        X[a][b][c] = Kn[a][b][c];
+        Xeq[a][b][c] = (has_mono(ST, a, b, c) && a + b + c >= 2) ? E[a][b][c] * inv : T(0);
+      });
+    } else if constexpr (SPACE == SP_CENTRAL) {
       sfor<27>([&](auto K) {
         constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
         X[a][b][c] = Kn[a][b][c];
         Xeq[a][b][c] = T(bg3(a, b, c));
       });
     } else {
+      // cumulants: c_s^2 on the second-order diagonal (1/3, or g h / 2 for
+      // the shallow-water method of Venturi), 0 above
+      const T cs2 = SWE ? T(0.5) * swe_g * rho : T(1.0 / 3.0);
       sfor<27>([&](auto K) {
         constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
         constexpr int o = a + b + c;
         X[a][b][c] = Kn[a][b][c];
-        Xeq[a][b][c] = T(o == 2 ? bg3(a, b, c) : 0.0);
+        Xeq[a][b][c] = (o == 2 && bg3(a, b, c) != 0.0) ? cs2 : T(0);
       });
       cumulant_fwd<ST, T, true>(Kn, X);
     }

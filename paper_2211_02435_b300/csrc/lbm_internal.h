@@ -54,6 +54,7 @@ struct StepArgs {
   int force_mode;           // FORCE_NONE / FORCE_UNIFORM / FORCE_FIELD
   double force[3];          // uniform body force
   const void* force_field;  // per-cell force [D][N] in the compute type (FORCE_FIELD)
+  double swe_g;             // > 0: shallow-water method with this gravity (D2Q9)
   cudaStream_t stream;
 };
 
@@ -75,6 +76,7 @@ struct AuxArgs {
   int force_mode;           // gather: fluid velocity (j + F/2) / rho under a force
   double force[3];
   const void* force_field;
+  double swe_g;  // scatter from (h, u): the shallow-water equilibrium
   cudaStream_t stream;
 };
 
@@ -151,5 +153,6 @@ struct lbm_ctx {
   int force_mode;     // lbm::FORCE_*
   double force[3];    // uniform body force (zeros when unset)
   void* force_field;  // device [D][N] in the compute type, or NULL
+  double swe_g;       // > 0: shallow-water method (lbm_set_shallow_water)
 };
 

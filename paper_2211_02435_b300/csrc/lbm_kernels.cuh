@@ -164,6 +164,50 @@ __global__ void __launch_bounds__(LBM_BX) k_pull(const __grid_constant__ PullPtr
   });
 }
 
+// Shallow-water step (D2Q9, absolute FP64 storage, pull): the absolute
+// collision with the method's shallow-water equilibrium (Sec. 5.2).
+template <int ST, int SPACE>
+__global__ void __launch_bounds__(LBM_BX) k_pull_swe(const __grid_constant__ PullPtrs<AbsF64> P,
+                                                     Geo g, Rates<double> keep, double grav) {
+  const int x = blockIdx.x * LBM_BX + threadIdx.x;
+  if (x >= g.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int c = (z * g.ny + y) * g.nx + x;
+  const int nxy = g.nx * g.ny;
+  const int wxp = x == 0 ? g.nx : 0, wxm = x == g.nx - 1 ? -g.nx : 0;
+  const int wyp = y == 0 ? nxy : 0, wym = y == g.ny - 1 ? -nxy : 0;
+  double f[q_of(ST)];
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1);
+    const int wy = cy > 0 ? wyp : (cy < 0 ? wym : 0);
+    const int wx = cx > 0 ? wxp : (cx < 0 ? wxm : 0);
+    f[i] = P.src[i][c + wx + wy].v;
+  });
+  collide_abs<ST, double, SPACE, false, false, true>(f, keep, grav);
+  sfor<q_of(ST)>([&](auto I) { P.dst[CI(I)][c] = AbsF64{f[CI(I)]}; });
+}
+
+// Set-up of a shallow-water context from depth and velocity: the method's
+// equilibrium written upstream (pull layout) as absolute FP64 populations.
+template <int ST, int SPACE>
+__global__ void __launch_bounds__(LBM_BX) k_scatter_swe(AbsF64* buf, Geo g, const double* h,
+                                                        const double* u, double grav) {
+  const int x = blockIdx.x * LBM_BX + threadIdx.x;
+  if (x >= g.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const Nbr n = neighbours(x, y, z, g);
+  const int c = (z * g.ny + y) * g.nx + x;
+  const double uu[3] = {u[c], u[g.N + c], 0.0};
+  double f[q_of(ST)];
+  swe_feq<ST, double, SPACE>(h ? h[c] : 1.0, uu, grav, f);
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    const int dc = cell_at(n, g, -vel(ST, i, 0), -vel(ST, i, 1), -vel(ST, i, 2));
+    buf[(int64_t)i * g.N + dc] = AbsF64{f[i]};
+  });
+}
+
 // Two cells per thread (x even, x + 1) with the collision on packed FP32
 // pairs, for FP16 / BF16 delta storage and even Nx.  Directions with
 // xi_x = 0 read both cells with one aligned 2-element load; the others read
@@ -546,6 +590,12 @@ void launch_step_typed(const StepArgs& a) {
       }
     }
     if constexpr (std::is_same<S, AbsF64>::value) {
+      if constexpr (ST == D2Q9 && (SPACE == SP_CENTRAL || SPACE == SP_CUMULANT) && !REG) {
+        if (a.swe_g > 0.0) {
+          k_pull_swe<ST, SPACE><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep, a.swe_g);
+          return;
+        }
+      }
       // absolute forms serve SRT and the moment spaces (TRT is refused at create)
       if constexpr (SPACE != SP_TRT)
         k_pull<ST, S, T, SPACE, REG, FORM_ABS_STORE><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep);
@@ -615,6 +665,15 @@ void launch_aux_typed(const AuxArgs& a) {
       break;
     }
     case AUX_SCATTER: {
+      if constexpr (ST == D2Q9 && std::is_same<S, AbsF64>::value) {
+        if (a.swe_g > 0.0 && !a.df_in) {
+          if (a.space == SP_CENTRAL)
+            k_scatter_swe<ST, SP_CENTRAL><<<grid, LBM_BX, 0, a.stream>>>((AbsF64*)a.buf, a.g, a.rho_in, a.u_in, a.swe_g);
+          else
+            k_scatter_swe<ST, SP_CUMULANT><<<grid, LBM_BX, 0, a.stream>>>((AbsF64*)a.buf, a.g, a.rho_in, a.u_in, a.swe_g);
+          break;
+        }
+      }
       const bool raw = a.space == SP_RAW || a.space == SP_SRT || a.space == SP_TRT;
       auto go = [&](auto layout) {
         constexpr int LY = decltype(layout)::value;

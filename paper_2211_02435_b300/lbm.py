@@ -92,6 +92,7 @@ def lib():
         L.lbm_set_step_kernel.argtypes = [vp, c_int]
         L.lbm_set_force.argtypes = [vp, vp]
         L.lbm_set_force_field.argtypes = [vp, vp, c_int]
+        L.lbm_set_shallow_water.argtypes = [vp, ctypes.c_double]
         L.lbm_destroy.argtypes = [vp]
         L.lbm_destroy.restype = None
         L.lbm_error_string.argtypes = [c_int]
@@ -323,6 +324,11 @@ class Lattice:
             F = np.ascontiguousarray(F, dtype=np.float64)
         p, dev = _ptr(F, self.d * self.N)
         _check(lib().lbm_set_force_field(self._h, p, dev), "lbm_set_force_field")
+
+    def set_shallow_water(self, g):
+        """Switch a D2Q9 absolute-storage CENTRAL / CUMULANT context to the
+        shallow-water method with gravity g (0 switches back); include/lbm.h."""
+        _check(lib().lbm_set_shallow_water(self._h, float(g)), "lbm_set_shallow_water")
 
     def set_step_kernel(self, kernel):
         """STEP_AUTO, STEP_DIRECT or STEP_STAGED (include/lbm.h)."""

@@ -105,7 +105,7 @@ def test_device_taylor_green_setup_matches_host_fields():
     with L.Batch(ST, L.SPACE_RAW, L.EQ_DELTA, L.STORE_F64, RATES, dims, om) as b:
         b.init_tgv(u0)
         for k in range(len(dims)):
-            m = O.method(O.D3Q19, space, O.EQ_DELTA, [om[k]] + rates[1:])
+            m = O.method(O.D3Q19, O.SPACE_RAW, O.EQ_DELTA, [om[k]] + [1.0] * 5)
             rho, u = I.taylor_green(dims[k], u0[k])
             ref = O.init(m, dims[k], rho, u)
             assert rel_linf(b.get_populations(k), ref) < 1e-13
