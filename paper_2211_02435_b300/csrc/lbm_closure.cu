@@ -23,6 +23,10 @@ namespace lbm {
 #ifndef LBM_CLOSURE_TC
 #define LBM_CLOSURE_TC 0
 #endif
+// minimum resident CTAs per SM asked of the fused learned-rate step kernel
+#ifndef LBM_CLOSURE_MINB
+#define LBM_CLOSURE_MINB 1
+#endif
 
 constexpr int NIN = LBM_CLOSURE_NIN, NH = LBM_CLOSURE_NHIDDEN, NOUT = LBM_CLOSURE_NOUT;
 constexpr int NPARAM = LBM_CLOSURE_NPARAM;
@@ -307,7 +311,7 @@ __device__ __forceinline__ void load_params(T* sp, const T* gp) {
 
 // fused pull step of a context with the learned rates
 template <class S, class T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, LBM_CLOSURE_MINB)
     k_closure_pull(const S* __restrict__ src, S* __restrict__ dst, Geo g, Rates<T> keep,
                    const T* __restrict__ params) {
   __shared__ T sp[NSMEM];

@@ -20,6 +20,11 @@ namespace lbm {
 #ifndef LBM_BX
 #define LBM_BX 128
 #endif
+// minimum resident CTAs per SM asked of the packed FP16 / BF16 step kernel
+// (a compile-time tuning knob; 1 leaves the register budget to the compiler)
+#ifndef LBM_PULL2_MINB
+#define LBM_PULL2_MINB 1
+#endif
 
 // how a kernel reads the canonical populations f(n) of a cell
 enum { G_PULL = 0, G_LOCAL = 1, G_AAODD = 2, G_ET_EVEN = 3, G_ET_ODD = 4 };
@@ -214,7 +219,7 @@ __global__ void __launch_bounds__(LBM_BX) k_scatter_swe(AbsF64* buf, Geo g, cons
 // the two cells separately (their x wrap differs at the row ends).  Stores
 // are aligned 2-element stores.
 template <int ST, class S, int SPACE, bool REG>
-__global__ void __launch_bounds__(LBM_BX) k_pull2(const __grid_constant__ PullPtrs<S> P, Geo g,
+__global__ void __launch_bounds__(LBM_BX, LBM_PULL2_MINB) k_pull2(const __grid_constant__ PullPtrs<S> P, Geo g,
                                                   Rates<P2> keep) {
   const int x = 2 * (blockIdx.x * LBM_BX + threadIdx.x);
   if (x >= g.nx) return;
