@@ -24,8 +24,14 @@ namespace lbm {
 #define LBM_CLOSURE_TC 0
 #endif
 // minimum resident CTAs per SM asked of the fused learned-rate step kernel
+// (0: the compiler's choice, measured fastest on B300; 4 and 5 spill)
 #ifndef LBM_CLOSURE_MINB
-#define LBM_CLOSURE_MINB 1
+#define LBM_CLOSURE_MINB 0
+#endif
+#if LBM_CLOSURE_MINB > 0
+#define LBM_CLOSURE_BOUNDS __launch_bounds__(128, LBM_CLOSURE_MINB)
+#else
+#define LBM_CLOSURE_BOUNDS __launch_bounds__(128)
 #endif
 
 constexpr int NIN = LBM_CLOSURE_NIN, NH = LBM_CLOSURE_NHIDDEN, NOUT = LBM_CLOSURE_NOUT;
@@ -311,7 +317,7 @@ __device__ __forceinline__ void load_params(T* sp, const T* gp) {
 
 // fused pull step of a context with the learned rates
 template <class S, class T>
-__global__ void __launch_bounds__(128, LBM_CLOSURE_MINB)
+__global__ void LBM_CLOSURE_BOUNDS
     k_closure_pull(const S* __restrict__ src, S* __restrict__ dst, Geo g, Rates<T> keep,
                    const T* __restrict__ params) {
   __shared__ T sp[NSMEM];

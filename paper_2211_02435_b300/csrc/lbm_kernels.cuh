@@ -21,9 +21,15 @@ namespace lbm {
 #define LBM_BX 128
 #endif
 // minimum resident CTAs per SM asked of the packed FP16 / BF16 step kernel
-// (a compile-time tuning knob; 1 leaves the register budget to the compiler)
+// (a compile-time tuning knob; 0 leaves the register budget to the compiler,
+// which measured fastest on B300: 7 -> -1 %, 8 -> -5 %, 1 -> -8 %)
 #ifndef LBM_PULL2_MINB
-#define LBM_PULL2_MINB 1
+#define LBM_PULL2_MINB 0
+#endif
+#if LBM_PULL2_MINB > 0
+#define LBM_PULL2_BOUNDS __launch_bounds__(LBM_BX, LBM_PULL2_MINB)
+#else
+#define LBM_PULL2_BOUNDS __launch_bounds__(LBM_BX)
 #endif
 
 // how a kernel reads the canonical populations f(n) of a cell
@@ -219,7 +225,7 @@ __global__ void __launch_bounds__(LBM_BX) k_scatter_swe(AbsF64* buf, Geo g, cons
 // the two cells separately (their x wrap differs at the row ends).  Stores
 // are aligned 2-element stores.
 template <int ST, class S, int SPACE, bool REG>
-__global__ void __launch_bounds__(LBM_BX, LBM_PULL2_MINB) k_pull2(const __grid_constant__ PullPtrs<S> P, Geo g,
+__global__ void LBM_PULL2_BOUNDS k_pull2(const __grid_constant__ PullPtrs<S> P, Geo g,
                                                   Rates<P2> keep) {
   const int x = 2 * (blockIdx.x * LBM_BX + threadIdx.x);
   if (x >= g.nx) return;
