@@ -85,75 +85,31 @@ P2F P2 rcp(P2 x) {
 #endif
 }
 
-// Cache hints of the packed kernel's global accesses (compile-time tuning
-// knobs, off by default): LBM_PULL2_LDHINT = 1 loads through the read-only
-// path with a 256-byte L2 prefetch, LBM_PULL2_STHINT = 1 stores with the
-// streaming (evict-first) policy.
-#ifndef LBM_PULL2_LDHINT
-#define LBM_PULL2_LDHINT 0
-#endif
-#ifndef LBM_PULL2_STHINT
-#define LBM_PULL2_STHINT 0
-#endif
-
-P2F uint32_t ld_u32(const void* p) {
-#if defined(__CUDA_ARCH__) && LBM_PULL2_LDHINT
-  uint32_t v;
-  asm volatile("ld.global.nc.L2::256B.b32 %0, [%1];" : "=r"(v) : "l"(p));
-  return v;
-#else
-  return *reinterpret_cast<const uint32_t*>(p);
-#endif
-}
-P2F uint16_t ld_u16(const void* p) {
-#if defined(__CUDA_ARCH__) && LBM_PULL2_LDHINT
-  uint16_t v;
-  asm volatile("ld.global.nc.L2::256B.b16 %0, [%1];" : "=h"(v) : "l"(p));
-  return v;
-#else
-  return *reinterpret_cast<const uint16_t*>(p);
-#endif
-}
-P2F void st_u32(void* p, uint32_t v) {
-#if defined(__CUDA_ARCH__) && LBM_PULL2_STHINT
-  asm volatile("st.global.cs.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-#else
-  *reinterpret_cast<uint32_t*>(p) = v;
-#endif
-}
-
 // two cells' packed values of one population plane (x and x+1)
 template <class S>
 struct Pack;
 template <>
 struct Pack<__half> {
   P2F static P2 load2(const __half* p) {
-    const uint32_t u = ld_u32(p);
-    return P2(__half22float2(*reinterpret_cast<const __half2*>(&u)));
+    return P2(__half22float2(*reinterpret_cast<const __half2*>(p)));
   }
   P2F static P2 load11(const __half* p0, const __half* p1) {
-    const uint16_t a = ld_u16(p0), b = ld_u16(p1);
-    return P2(make_float2(__half2float(__ushort_as_half(a)), __half2float(__ushort_as_half(b))));
+    return P2(make_float2(__half2float(*p0), __half2float(*p1)));
   }
   P2F static void store2(__half* p, P2 v) {
-    const __half2 h = __float22half2_rn(v.v);
-    st_u32(p, *reinterpret_cast<const uint32_t*>(&h));
+    *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v);
   }
 };
 template <>
 struct Pack<__nv_bfloat16> {
   P2F static P2 load2(const __nv_bfloat16* p) {
-    const uint32_t u = ld_u32(p);
-    return P2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u)));
+    return P2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p)));
   }
   P2F static P2 load11(const __nv_bfloat16* p0, const __nv_bfloat16* p1) {
-    const uint16_t a = ld_u16(p0), b = ld_u16(p1);
-    return P2(make_float2(__bfloat162float(__ushort_as_bfloat16(a)),
-                          __bfloat162float(__ushort_as_bfloat16(b))));
+    return P2(make_float2(__bfloat162float(*p0), __bfloat162float(*p1)));
   }
   P2F static void store2(__nv_bfloat16* p, P2 v) {
-    const __nv_bfloat162 h = __float22bfloat162_rn(v.v);
-    st_u32(p, *reinterpret_cast<const uint32_t*>(&h));
+    *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v.v);
   }
 };
 
