@@ -76,7 +76,7 @@ typedef enum {
   LBM_SPACE_RAW = 1,      /* orthogonal raw moments, unweighted (O-MRT)  */
   LBM_SPACE_CENTRAL = 2,  /* polynomial central moments (CM)             */
   LBM_SPACE_CUMULANT = 3, /* polynomial cumulants (K)                    */
-  LBM_SPACE_TRT = 4       /* two relaxation times in population space:
+  LBM_SPACE_TRT = 4,      /* two relaxation times in population space:
                              per opposite pair the even part
                              (f_i + f_ibar)/2 relaxes with rates[0], the
                              odd part with rates[2]; the same method as
@@ -84,6 +84,11 @@ typedef enum {
                              odd orders at rates[2].  Deviation arithmetic
                              only (not with LBM_STORE_F64_ABSOLUTE or
                              LBM_ARITH_AS_WRITTEN: UNSUPPORTED) */
+  LBM_SPACE_RAW_WEIGHTED = 5 /* raw moments in the weighted orthogonal
+                                basis (WO-MRT, Sec. 4.2): the same rows
+                                orthogonalised under sum_i w_i p(xi_i)
+                                q(xi_i); equal to LBM_SPACE_RAW when every
+                                rate is 1 */
 } lbm_space;
 
 /* Equilibrium format (Sec. 2.2): relax deviations against the

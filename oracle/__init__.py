@@ -23,7 +23,8 @@ _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liblbm_oracle.so")
 
 D2Q9, D3Q19, D3Q27 = 0, 1, 2
-SPACE_POPULATIONS, SPACE_RAW, SPACE_CENTRAL, SPACE_CUMULANT, SPACE_TRT, SPACE_NONE = 0, 1, 2, 3, 4, 5
+SPACE_POPULATIONS, SPACE_RAW, SPACE_CENTRAL, SPACE_CUMULANT, SPACE_TRT = 0, 1, 2, 3, 4
+SPACE_RAW_WEIGHTED, SPACE_NONE = 5, 6
 EQ_DELTA, EQ_ABSOLUTE = 0, 1
 GROUP_CONSERVED, GROUP_SHEAR, GROUP_BULK = -1, 0, 1
 Q_OF = {D2Q9: 9, D3Q19: 19, D3Q27: 27}
@@ -74,6 +75,7 @@ def lib():
         L.lbm_oracle_lattice.argtypes = [ctypes.c_int, i32, i32, i32, d, i32]
         L.lbm_oracle_matrices.argtypes = [ctypes.c_int, d, d, d, d, i32]
         L.lbm_oracle_central_matrix.argtypes = [ctypes.c_int, d, d]
+        L.lbm_oracle_weighted_basis.argtypes = [ctypes.c_int, d]
         L.lbm_oracle_cumulants.argtypes = [ctypes.c_int, d, d]
         L.lbm_oracle_moments_from_cumulants.argtypes = [ctypes.c_int, d, d]
         L.lbm_oracle_cumulant_of.argtypes = [d, ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -126,6 +128,14 @@ def lattice(stencil):
     w = np.zeros(q)
     _check(lib().lbm_oracle_lattice(stencil, None, None, _ip(xi), _dp(w), _ip(ex)))
     return xi.astype(np.int64), w, ex.astype(np.int64)
+
+
+def weighted_basis(stencil):
+    """Weighted orthogonal raw basis Pw (q x q) of WO-MRT."""
+    q = Q_OF[stencil]
+    out = np.zeros((q, q))
+    _check(lib().lbm_oracle_weighted_basis(stencil, _dp(out)))
+    return out
 
 
 def matrices(stencil):

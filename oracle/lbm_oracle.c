@@ -32,6 +32,7 @@ typedef struct {
   double w[QMAX];
   double M[QMAX][QMAX], Minv[QMAX][QMAX];
   double Praw[QMAX][QMAX], Prawinv[QMAX][QMAX];
+  double Pw[QMAX][QMAX], Pwinv[QMAX][QMAX]; /* weighted orthogonal (WO-MRT) */
   double Pcm[QMAX][QMAX], Pcminv[QMAX][QMAX];
   int group[QMAX];
   int npart[QMAX];
@@ -157,8 +158,9 @@ static int in_set(int stencil, int a, int b, int c) {
 }
 
 /* Gram-Schmidt of the rows of B (polynomials in monomial coordinates) under
- * the unweighted inner product <p,q> = sum_i p(xi_i) q(xi_i). */
-static void gram_schmidt(lattice_t* L, double B[QMAX][QMAX]) {
+ * the inner product <p,q> = sum_i wt_i p(xi_i) q(xi_i) (wt = 1: unweighted;
+ * wt = lattice weights: the weighted product of WO-MRT). */
+static void gram_schmidt(lattice_t* L, double B[QMAX][QMAX], const double* wt) {
   int q = L->q;
   double V[QMAX][QMAX]; /* V[r][i] = p_r(xi_i) */
   for (int r = 0; r < q; ++r)
@@ -171,8 +173,8 @@ static void gram_schmidt(lattice_t* L, double B[QMAX][QMAX]) {
     for (int j = 0; j < r; ++j) {
       double num = 0.0, den = 0.0;
       for (int i = 0; i < q; ++i) {
-        num += V[r][i] * V[j][i];
-        den += V[j][i] * V[j][i];
+        num += wt[i] * V[r][i] * V[j][i];
+        den += wt[i] * V[j][i] * V[j][i];
       }
       double c = num / den;
       for (int i = 0; i < q; ++i) V[r][i] -= c * V[j][i];
@@ -277,9 +279,16 @@ static int build_lattice(int stencil) {
   if (invert(L->q, L->Pcm, L->Pcminv)) return -1;
   /* orthogonal raw-moment basis (O-MRT, Sec. 4.2): same rows, unweighted
    * Gram-Schmidt in degree order */
+  double ones[QMAX];
+  for (int i = 0; i < QMAX; ++i) ones[i] = 1.0;
   memcpy(L->Praw, L->Pcm, sizeof(L->Praw));
-  gram_schmidt(L, L->Praw);
+  gram_schmidt(L, L->Praw, ones);
   if (invert(L->q, L->Praw, L->Prawinv)) return -1;
+  /* weighted orthogonal raw basis (WO-MRT): Gram-Schmidt of the same rows
+   * under the lattice-weight inner product */
+  memcpy(L->Pw, L->Pcm, sizeof(L->Pw));
+  gram_schmidt(L, L->Pw, L->w);
+  if (invert(L->q, L->Pw, L->Pwinv)) return -1;
   for (int k = 0; k < L->q; ++k) enumerate_partitions(L, k);
   L->ready = 1;
   return 0;
@@ -504,20 +513,25 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
       }
       return 0;
     }
-    case LBM_ORACLE_SPACE_RAW: {
+    case LBM_ORACLE_SPACE_RAW:
+    case LBM_ORACLE_SPACE_RAW_WEIGHTED: {
+      /* O-MRT: unweighted orthogonal basis; WO-MRT: weighted (Sec. 4.2) */
+      const int wo = m->space == LBM_ORACLE_SPACE_RAW_WEIGHTED;
+      const double(*PR)[QMAX] = wo ? L->Pw : L->Praw;
+      const double(*PRinv)[QMAX] = wo ? L->Pwinv : L->Prawinv;
       if (delta) { /* Eq. 2.5: dq = T(df), dq_eq = q_eq - q0 */
         matvec(q, L->M, df, tmp);
         for (int k = 0; k < q; ++k)
           veq[k] = maxwell_raw_moment(L->expo[k], rho, u, 1) -
                    maxwell_raw_moment(L->expo[k], 1.0, zero_u, 1);
-        relax_forced(L, m, L->Praw, L->Prawinv, tmp, veq, sF, vout);
+        relax_forced(L, m, PR, PRinv, tmp, veq, sF, vout);
         matvec(q, L->Minv, vout, out);
       } else { /* Eq. 2.6 */
         for (int i = 0; i < q; ++i) f[i] = df[i] + L->w[i];
         matvec(q, L->M, f, tmp);
         for (int k = 0; k < q; ++k)
           veq[k] = maxwell_raw_moment(L->expo[k], rho, u, 1);
-        relax_forced(L, m, L->Praw, L->Prawinv, tmp, veq, sF, vout);
+        relax_forced(L, m, PR, PRinv, tmp, veq, sF, vout);
         matvec(q, L->Minv, vout, tmp2);
         for (int i = 0; i < q; ++i) out[i] = tmp2[i] - L->w[i];
       }
@@ -612,7 +626,7 @@ static int collide_cell(const lattice_t* L, const lbm_oracle_method* m,
 
 static int check_method(const lbm_oracle_method* m) {
   if (!m || build_lattice(m->stencil)) return -1;
-  if (m->space < 0 || m->space > 5) return -1;
+  if (m->space < 0 || m->space > 6) return -1;
   if (m->equilibrium != LBM_ORACLE_EQ_DELTA &&
       m->equilibrium != LBM_ORACLE_EQ_ABSOLUTE)
     return -1;
@@ -655,6 +669,14 @@ int lbm_oracle_matrices(int stencil, double* M, double* Minv, double* Praw,
     }
     if (group) group[r] = L->group[r];
   }
+  return 0;
+}
+
+int lbm_oracle_weighted_basis(int stencil, double* Pw) {
+  if (build_lattice(stencil) || !Pw) return -1;
+  const lattice_t* L = &g_lat[stencil];
+  for (int r = 0; r < L->q; ++r)
+    for (int c = 0; c < L->q; ++c) Pw[r * L->q + c] = L->Pw[r][c];
   return 0;
 }
 
@@ -756,6 +778,7 @@ static void equilibrium_cell(const lattice_t* L, const lbm_oracle_method* m,
    * moments), so each method's own equilibrium is a collision fixed point */
   static const double zero_u[3] = {0, 0, 0};
   const int trunc = m->space == LBM_ORACLE_SPACE_RAW ||
+                    m->space == LBM_ORACLE_SPACE_RAW_WEIGHTED ||
                     m->space == LBM_ORACLE_SPACE_POPULATIONS ||
                     m->space == LBM_ORACLE_SPACE_TRT ||
                     m->space == LBM_ORACLE_SPACE_NONE;

@@ -54,7 +54,10 @@ extern "C" {
 /* two-relaxation-time collision in population space: even part with
  * rates[0], odd part with rates[2] (the order-3 slot) */
 #define LBM_ORACLE_SPACE_TRT 4
-#define LBM_ORACLE_SPACE_NONE 5
+/* raw moments in the weighted orthogonal basis (WO-MRT): the same rows
+ * Gram-Schmidt-orthogonalised under <p,q> = sum_i w_i p(xi_i) q(xi_i) */
+#define LBM_ORACLE_SPACE_RAW_WEIGHTED 5
+#define LBM_ORACLE_SPACE_NONE 6
 /* equilibrium format: deviation-only (Eq. 2.5) or absolute (Eq. 2.6) */
 #define LBM_ORACLE_EQ_DELTA 0
 #define LBM_ORACLE_EQ_ABSOLUTE 1
@@ -85,6 +88,9 @@ int lbm_oracle_lattice(int stencil, int* q, int* d, int* xi, double* w,
 int lbm_oracle_matrices(int stencil, double* M, double* Minv, double* Praw,
                         double* Pcm, int* group);
 
+/* Weighted orthogonal raw basis (WO-MRT), row-major q x q, rows in the
+ * order and groups of the unweighted basis. */
+int lbm_oracle_weighted_basis(int stencil, double* Pw);
 /* Central-moment matrix K(u)[k][i] = prod_d (xi_{i,d} - u_d)^{e_{k,d}}
  * (Sec. 2.3.2), row-major q x q. */
 int lbm_oracle_central_matrix(int stencil, const double* u, double* K);

@@ -11,7 +11,7 @@
 * ``tgv_plateau``: the round-off plateau of the decaying Taylor-Green vortex
   (Sec. 5.1, Eq. 5.1/5.2, Table 3): D3Q27, L x L x 1 (the flow is
   z-invariant), u0 = 0.25, nu = 1/6 (every rate 1), FP64; the relative
-  kinetic energy E(t)/E0 of SRT, R-O-MRT, R-CM and R-K in each storage /
+  kinetic energy E(t)/E0 of SRT, R-WO-MRT, R-O-MRT, R-CM and R-K in each storage /
   equilibrium / arithmetic form, against the analytic exp(-4 nu kappa^2 t).
 
 The FP64 GPU runs are tied to the CPU oracle by the parity tests (1e-12 per
@@ -106,8 +106,9 @@ def half_storage(n=512, nu=1e-3, steps=5000, every=1000, seed=3, stream=None):
                       f"(seed {seed}), nu={nu}", "steps": steps, "rows": rows}
 
 
-PLATEAU_METHODS = (("SRT", L.SPACE_POPULATIONS), ("R-O-MRT", L.SPACE_RAW),
-                   ("R-CM", L.SPACE_CENTRAL), ("R-K", L.SPACE_CUMULANT))
+PLATEAU_METHODS = (("SRT", L.SPACE_POPULATIONS), ("R-WO-MRT", L.SPACE_RAW_WEIGHTED),
+                   ("R-O-MRT", L.SPACE_RAW), ("R-CM", L.SPACE_CENTRAL),
+                   ("R-K", L.SPACE_CUMULANT))
 # (name, storage, equilibrium, arithmetic): the three forms of Table 3 and
 # this library's default (absolute equilibrium in deviation arithmetic)
 PLATEAU_FORMS = (
@@ -125,8 +126,9 @@ def tgv_plateau(n=256, steps=200_000, every=10_000, u0=0.25, methods=None, forms
     E is the lattice sum of rho |u|^2 / 2 (lbm_invariants, a deterministic
     FP64 reduction); E0 is its value at t = 0, the equilibrium of Eq. 5.1.
     With nu = 1/6 the shear rate is 1 and every higher rate is 1 as well,
-    so the raw-moment method is the same in any orthogonal basis (all
-    non-conserved moments are set to equilibrium)."""
+    so the weighted (WO-MRT) and unweighted (O-MRT) raw-moment methods are
+    the same method (all non-conserved moments are set to equilibrium) and
+    differ only in rounding."""
     nu = 1.0 / 6.0
     kappa = 2 * np.pi / n
     rho, u = I.taylor_green((n, n, 1), u0)

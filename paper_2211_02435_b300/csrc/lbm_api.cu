@@ -178,7 +178,7 @@ const char* lbm_error_string(int code) {
 int lbm_create(lbm_ctx** out, const lbm_params* p) {
   if (!out || !p) return LBM_ERR_INVALID;
   *out = nullptr;
-  if (p->stencil < 0 || p->stencil > 2 || p->space < 0 || p->space > 4 || p->storage < 0 ||
+  if (p->stencil < 0 || p->stencil > 2 || p->space < 0 || p->space > 5 || p->storage < 0 ||
       p->storage > 4 || p->streaming < 0 || p->streaming > 2 ||
       (p->equilibrium != LBM_EQ_DELTA && p->equilibrium != LBM_EQ_ABSOLUTE) ||
       (p->arithmetic != LBM_ARITH_DEVIATION && p->arithmetic != LBM_ARITH_AS_WRITTEN))

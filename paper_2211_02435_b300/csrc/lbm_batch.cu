@@ -158,7 +158,7 @@ int lbm_batch_create(lbm_batch** out, const lbm_params* p, int n, const int64_t*
                      const double* shear_rates) {
   if (!out || !p || n < 1 || !dims) return LBM_ERR_INVALID;
   *out = nullptr;
-  if (p->stencil < 0 || p->stencil > 2 || p->space < 0 || p->space > 4 || p->storage < 0 ||
+  if (p->stencil < 0 || p->stencil > 2 || p->space < 0 || p->space > 5 || p->storage < 0 ||
       p->storage > 4 || (p->equilibrium != LBM_EQ_DELTA && p->equilibrium != LBM_EQ_ABSOLUTE))
     return LBM_ERR_INVALID;
   if (p->space == LBM_SPACE_CUMULANT && p->equilibrium == LBM_EQ_DELTA)

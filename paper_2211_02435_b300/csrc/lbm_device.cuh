@@ -34,7 +34,7 @@
 namespace lbm {
 
 enum { D2Q9 = 0, D3Q19 = 1, D3Q27 = 2 };
-enum { SP_SRT = 0, SP_RAW = 1, SP_CENTRAL = 2, SP_CUMULANT = 3, SP_TRT = 4 };
+enum { SP_SRT = 0, SP_RAW = 1, SP_CENTRAL = 2, SP_CUMULANT = 3, SP_TRT = 4, SP_RAW_W = 5 };
 
 // ---------------------------------------------------------------- helpers
 template <class F, int... Is>
@@ -319,16 +319,22 @@ LBM_D T raw_eq_dev(int a, int b, int c, T drho, T rho, const T (&u)[3]) {
 // orthogonal polynomials 1, x, x^2 - 2/3).  D3Q19: once the conserved
 // parts are zero only the fourth-order polynomials differ from monomials:
 // x^2y^2 - (10/21)(x^2 + y^2) + (4/21) z^2 + 4/21.  SIGN = -1 forward.
-template <int ST, int SIGN, class T>
+// W: the weighted orthogonal basis of WO-MRT (inner product with the lattice
+// weights): D2Q9 / D3Q27 tensor products of 1, x, x^2 - 1/3; D3Q19
+// x^2 y^2 - (x^2 + y^2)/3 + z^2/6 (the unweighted basis: x^2 - 2/3 and
+// x^2 y^2 - 10/21 (x^2 + y^2) + 4/21 z^2).  Lower-order and same-group
+// terms of the full Gram-Schmidt rows do not change the relaxation and are
+// left out.
+template <int ST, int SIGN, class T, bool W = false>
 LBM_D void ortho_raw(T (&N)[3][3][3]) {
   if constexpr (ST == D3Q19) {
-    const T c10 = T(10.0 / 21.0), c4 = T(4.0 / 21.0);
+    const T c10 = T(W ? 1.0 / 3.0 : 10.0 / 21.0), c4 = T(W ? 1.0 / 6.0 : 4.0 / 21.0);
     const T s = T(SIGN);
     N[2][2][0] += s * (c10 * (N[2][0][0] + N[0][2][0]) - c4 * N[0][0][2]);
     N[2][0][2] += s * (c10 * (N[2][0][0] + N[0][0][2]) - c4 * N[0][2][0]);
     N[0][2][2] += s * (c10 * (N[0][2][0] + N[0][0][2]) - c4 * N[2][0][0]);
   } else {
-    const T t = T(-SIGN) * T(-2.0 / 3.0);
+    const T t = T(-SIGN) * T(W ? -1.0 / 3.0 : -2.0 / 3.0);
     if constexpr (dim_of(ST) == 3) {
       sfor<9>([&](auto K) { N[CI(K) / 3][CI(K) % 3][2] += t * N[CI(K) / 3][CI(K) % 3][0]; });
     }
@@ -516,7 +522,9 @@ LBM_D void guo_source(const T (&u)[3], const T (&F)[3], T (&S)[q_of(ST)]) {
 //             (j + F) / rho (cumulants of order >= 2 are shift invariant).
 template <int ST, class T, int SPACE, bool REG, bool DEFER = false, bool FORCED = false>
 LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr) {
-  static_assert(!(FORCED && REG && SPACE == SP_RAW), "forced raw moments use the general path");
+  static_assert(!(FORCED && REG && (SPACE == SP_RAW || SPACE == SP_RAW_W)),
+                "forced raw moments use the general path");
+  constexpr bool WO = SPACE == SP_RAW_W;
   T A[3][3][3];
   fwd_raw_chimera<ST, T>(f, A);
   const T drho = A[0][0][0];
@@ -586,7 +594,7 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
     });
     if constexpr (DEFER) defer_scale<ST, T>(f);
     return;
-  } else if constexpr (SPACE == SP_RAW) {
+  } else if constexpr (SPACE == SP_RAW || SPACE == SP_RAW_W) {
     // non-equilibrium parts in the orthogonal basis, relax, transform back
     T E[3][3][3], N[3][3][3];
     sfor<27>([&](auto K) {
@@ -602,7 +610,7 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
         N[a][b][c] = T(0);
       }
     });
-    if constexpr (!REG) ortho_raw<ST, -1, T>(N);
+    if constexpr (!REG) ortho_raw<ST, -1, T, WO>(N);
     relax_order2<ST, T, REG>(N, keep.om[0], keep.om[1]);
     if constexpr (!REG) {
       sfor<27>([&](auto K) {
@@ -618,7 +626,7 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
       guo_source<ST, T>(u, Fv, S);
       fwd_raw_chimera<ST, T>(S, G);
       G[0][0][0] = T(0);
-      ortho_raw<ST, -1, T>(G);
+      ortho_raw<ST, -1, T, WO>(G);
       relax_order2<ST, T, false>(G, T(0.5) * (T(1) + keep.om[0]), T(0.5) * (T(1) + keep.om[1]));
       sfor<27>([&](auto K) {
         constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
@@ -629,7 +637,7 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
         }
       });
     }
-    ortho_raw<ST, +1, T>(N);
+    ortho_raw<ST, +1, T, WO>(N);
     sfor<27>([&](auto K) {
       constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
       if constexpr (has_mono(ST, a, b, c) && a + b + c >= 2) A[a][b][c] = E[a][b][c] + N[a][b][c];
@@ -846,7 +854,8 @@ LBM_D void collide_abs(T (&f)[q_of(ST)], const Rates<T>& keep, T swe_g = T(0)) {
       if constexpr (ZC) f[i] -= T(weight(ST, i));
     });
     return;
-  } else if constexpr (SPACE == SP_RAW) {
+  } else if constexpr (SPACE == SP_RAW || SPACE == SP_RAW_W) {
+    constexpr bool WO = SPACE == SP_RAW_W;
     T E[3][3][3], N[3][3][3];
     sfor<27>([&](auto K) {
       constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
@@ -860,7 +869,7 @@ LBM_D void collide_abs(T (&f)[q_of(ST)], const Rates<T>& keep, T swe_g = T(0)) {
         N[a][b][c] = T(0);
       }
     });
-    if constexpr (!REG) ortho_raw<ST, -1, T>(N);
+    if constexpr (!REG) ortho_raw<ST, -1, T, WO>(N);
     relax_order2<ST, T, REG>(N, keep.om[0], keep.om[1]);
     if constexpr (!REG) {
       sfor<27>([&](auto K) {
@@ -869,7 +878,7 @@ LBM_D void collide_abs(T (&f)[q_of(ST)], const Rates<T>& keep, T swe_g = T(0)) {
         if constexpr (has_mono(ST, a, b, c) && o >= 3) N[a][b][c] *= keep.om[o - 1];
       });
     }
-    ortho_raw<ST, +1, T>(N);
+    ortho_raw<ST, +1, T, WO>(N);
     sfor<27>([&](auto K) {
       constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
       if constexpr (has_mono(ST, a, b, c) && a + b + c >= 2) A[a][b][c] = E[a][b][c] + N[a][b][c];

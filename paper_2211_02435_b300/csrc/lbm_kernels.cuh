@@ -646,6 +646,8 @@ void launch_step_space(const StepArgs& a) {
     case SP_SRT * 2 + 1: launch_step_typed<ST, S, T, SP_SRT, false>(a); break;
     case SP_RAW * 2: launch_step_typed<ST, S, T, SP_RAW, false>(a); break;
     case SP_RAW * 2 + 1: launch_step_typed<ST, S, T, SP_RAW, true>(a); break;
+    case SP_RAW_W * 2: launch_step_typed<ST, S, T, SP_RAW_W, false>(a); break;
+    case SP_RAW_W * 2 + 1: launch_step_typed<ST, S, T, SP_RAW_W, true>(a); break;
     case SP_CENTRAL * 2: launch_step_typed<ST, S, T, SP_CENTRAL, false>(a); break;
     case SP_CENTRAL * 2 + 1: launch_step_typed<ST, S, T, SP_CENTRAL, true>(a); break;
     case SP_CUMULANT * 2: launch_step_typed<ST, S, T, SP_CUMULANT, false>(a); break;
@@ -685,7 +687,8 @@ void launch_aux_typed(const AuxArgs& a) {
           break;
         }
       }
-      const bool raw = a.space == SP_RAW || a.space == SP_SRT || a.space == SP_TRT;
+      const bool raw = a.space == SP_RAW || a.space == SP_SRT || a.space == SP_TRT ||
+                       a.space == SP_RAW_W;
       auto go = [&](auto layout) {
         constexpr int LY = decltype(layout)::value;
         if (raw)
@@ -716,7 +719,7 @@ void launch_aux_typed(const AuxArgs& a) {
 template <int ST, class S, class T, int SPACE, bool REG>
 void launch_batch_typed(const BatchArgs& a) {
   if (a.op == BATCH_TGV) {
-    k_batch_tgv<ST, S, T, (SPACE == SP_RAW || SPACE == SP_SRT || SPACE == SP_TRT ? SP_RAW : SP_CENTRAL)>
+    k_batch_tgv<ST, S, T, (SPACE == SP_RAW || SPACE == SP_SRT || SPACE == SP_TRT || SPACE == SP_RAW_W ? SP_RAW : SP_CENTRAL)>
         <<<a.grid, a.threads, 0, a.stream>>>((S*)a.dst, a.inst, a.tiles, a.ntiles, a.cpt, a.u0);
     return;
   }
@@ -733,6 +736,8 @@ void launch_batch_space(const BatchArgs& a) {
     case SP_SRT * 2 + 1: launch_batch_typed<ST, S, T, SP_SRT, false>(a); break;
     case SP_RAW * 2: launch_batch_typed<ST, S, T, SP_RAW, false>(a); break;
     case SP_RAW * 2 + 1: launch_batch_typed<ST, S, T, SP_RAW, true>(a); break;
+    case SP_RAW_W * 2: launch_batch_typed<ST, S, T, SP_RAW_W, false>(a); break;
+    case SP_RAW_W * 2 + 1: launch_batch_typed<ST, S, T, SP_RAW_W, true>(a); break;
     case SP_CENTRAL * 2: launch_batch_typed<ST, S, T, SP_CENTRAL, false>(a); break;
     case SP_CENTRAL * 2 + 1: launch_batch_typed<ST, S, T, SP_CENTRAL, true>(a); break;
     case SP_CUMULANT * 2: launch_batch_typed<ST, S, T, SP_CUMULANT, false>(a); break;

@@ -25,6 +25,7 @@ METHODS = [  # (space, regularised); equilibrium always absolute
     (L.SPACE_POPULATIONS, False), (L.SPACE_RAW, False), (L.SPACE_RAW, True),
     (L.SPACE_CENTRAL, False), (L.SPACE_CENTRAL, True),
     (L.SPACE_CUMULANT, False), (L.SPACE_CUMULANT, True),
+    (L.SPACE_RAW_WEIGHTED, False), (L.SPACE_RAW_WEIGHTED, True),
 ]
 FORMS = {  # name: (storage, arithmetic)
     "zc_feq": (L.STORE_F64, L.ARITH_AS_WRITTEN),

@@ -25,7 +25,7 @@ METHODS = [  # (space, equilibrium, rates)
     (L.SPACE_RAW, L.EQ_DELTA, "gen"), (L.SPACE_RAW, L.EQ_ABSOLUTE, "unit"),
     (L.SPACE_CENTRAL, L.EQ_DELTA, "gen"), (L.SPACE_CENTRAL, L.EQ_ABSOLUTE, "unit"),
     (L.SPACE_CUMULANT, L.EQ_ABSOLUTE, "gen"), (L.SPACE_CUMULANT, L.EQ_ABSOLUTE, "unit"),
-    (L.SPACE_TRT, L.EQ_DELTA, "trt"),
+    (L.SPACE_TRT, L.EQ_DELTA, "trt"), (L.SPACE_RAW_WEIGHTED, L.EQ_DELTA, "gen"),
 ]
 
 

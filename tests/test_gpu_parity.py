@@ -34,6 +34,7 @@ METHODS = [  # (space, equilibrium, regularised)
     (L.SPACE_CENTRAL, L.EQ_ABSOLUTE, False),
     (L.SPACE_CUMULANT, L.EQ_ABSOLUTE, False), (L.SPACE_CUMULANT, L.EQ_ABSOLUTE, True),
     (L.SPACE_TRT, L.EQ_DELTA, False), (L.SPACE_TRT, L.EQ_ABSOLUTE, False),
+    (L.SPACE_RAW_WEIGHTED, L.EQ_DELTA, False), (L.SPACE_RAW_WEIGHTED, L.EQ_ABSOLUTE, True),
 ]
 RATES_TRT = [1.3, 1.0, 1.75, 1.0, 1.0, 1.0]  # w+ (even part), w- (odd part) in slot 2
 
