@@ -85,8 +85,9 @@ def lib():
         L.lbm_oracle_init.argtypes = [m, i64, d, d, d]
         L.lbm_oracle_step.argtypes = [m, i64, d, ctypes.c_int64, ctypes.c_int]
         L.lbm_oracle_macroscopic.argtypes = [m, i64, d, d, d]
-        L.lbm_oracle_collide_forced.argtypes = [m, ctypes.c_int64, d, d, d]
-        L.lbm_oracle_step_forced.argtypes = [m, i64, d, d, ctypes.c_int64, ctypes.c_int]
+        L.lbm_oracle_collide_forced.argtypes = [m, ctypes.c_int64, d, d, ctypes.c_int, d]
+        L.lbm_oracle_step_forced.argtypes = [m, i64, d, d, ctypes.c_int, ctypes.c_int64,
+                                             ctypes.c_int]
         L.lbm_oracle_macroscopic_forced.argtypes = [m, i64, d, d, d, d]
         L.lbm_oracle_swe_equilibrium.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                  d, d]
@@ -184,16 +185,19 @@ def collide(m, df):
     return out.reshape(df.shape)
 
 
-def collide_forced(m, df, force):
-    """Collide cells under a body force (Guo; see lbm_oracle.h): df [ncells, q],
-    force [ncells, 3] (or [3] for one cell)."""
+FORCE_GUO, FORCE_HE = 0, 1
+
+
+def collide_forced(m, df, force, model=FORCE_GUO):
+    """Collide cells under a body force (Guo or He; see lbm_oracle.h):
+    df [ncells, q], force [ncells, 3] (or [3] for one cell)."""
     df = _f64(df)
     flat = df.reshape(-1, Q_OF[m.stencil])
     F = _f64(np.broadcast_to(np.asarray(force, dtype=np.float64).reshape(-1, 3),
                              (flat.shape[0], 3))).copy()
     out = np.empty_like(flat)
     _check(lib().lbm_oracle_collide_forced(ctypes.byref(m), flat.shape[0], _dp(flat), _dp(F),
-                                           _dp(out)))
+                                           int(model), _dp(out)))
     return out.reshape(df.shape)
 
 
@@ -245,14 +249,15 @@ def _force_field(m, dims, force):
     return np.ascontiguousarray(F.reshape(d, N))
 
 
-def step_forced(m, dims, df, force, nsteps, nthreads=0):
+def step_forced(m, dims, df, force, nsteps, nthreads=0, model=FORCE_GUO):
     """step() under a time-constant body force (a vector or a [D, ...] field)."""
     dm = _dims(dims)
     out = _f64(df).copy()
     F = _force_field(m, dims, force)
     _check(lib().lbm_oracle_step_forced(ctypes.byref(m),
                                         dm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                                        _dp(out), _dp(F), int(nsteps), int(nthreads)))
+                                        _dp(out), _dp(F), int(model), int(nsteps),
+                                        int(nthreads)))
     return out
 
 

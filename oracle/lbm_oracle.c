@@ -442,9 +442,20 @@ static void add_first_order(const lattice_t* L, const double* F, double* v) {
 static void swe_zhou_feq(const lattice_t* L, double h, const double* u,
                          double g, double* feq);
 
+/* He's population source of a body force F at velocity u: the equilibrium
+ * populations f_eq (absolute) weighted by (xi_i - u).F / (rho c_s^2) */
+static void he_source(const lattice_t* L, double rho, const double* u,
+                      const double* F, const double* feq, double* S) {
+  for (int i = 0; i < L->q; ++i) {
+    double cf = 0.0;
+    for (int d = 0; d < 3; ++d) cf += (L->xi[i][d] - u[d]) * F[d];
+    S[i] = 3.0 * cf / rho * feq[i];
+  }
+}
+
 static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
                           const double* df, const double* F, double swe_g,
-                          double* out) {
+                          int model, double* out) {
   const int q = L->q;
   /* conserved quantities from the deviations, Eq. 2.3, rho0 = 1 */
   double drho = 0.0, j[3] = {0, 0, 0}, u[3];
@@ -459,7 +470,17 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
   const int shift = forced && m->space != LBM_ORACLE_SPACE_CUMULANT;
   for (int d = 0; d < 3; ++d) u[d] = (j[d] + (shift ? 0.5 * F[d] : 0.0)) / rho;
   double S[QMAX] = {0}, sF[QMAX] = {0};
-  if (forced) {
+  const int he = forced && model == 1;
+  if (he && m->space == LBM_ORACLE_SPACE_CUMULANT) return -1;
+  if (he) {
+    /* the method's own equilibrium populations (absolute) at u */
+    const int full = m->space == LBM_ORACLE_SPACE_CENTRAL;
+    double meq[QMAX], feq[QMAX];
+    for (int k = 0; k < q; ++k) meq[k] = maxwell_raw_moment(L->expo[k], rho, u, !full);
+    matvec(q, L->Minv, meq, feq);
+    he_source(L, rho, u, F, feq, S);
+    matvec(q, L->M, S, sF);
+  } else if (forced) {
     guo_source(L, u, F, S);
     matvec(q, L->M, S, sF);
   }
@@ -547,8 +568,14 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
         matvec(q, K, L->w, k0);
         for (int k = 0; k < q; ++k)
           veq[k] = maxwell_central_moment(L->expo[k], rho) - k0[k];
-        relax(L, m, L->Pcm, L->Pcminv, tmp, veq, vout);
-        add_first_order(L, F, vout);
+        if (he) { /* q^F = (I - S/2) P K(u) S */
+          double sK[QMAX];
+          matvec(q, K, S, sK);
+          relax_forced(L, m, L->Pcm, L->Pcminv, tmp, veq, sK, vout);
+        } else {
+          relax(L, m, L->Pcm, L->Pcminv, tmp, veq, vout);
+          add_first_order(L, F, vout);
+        }
         matvec(q, Kinv, vout, out);
       } else { /* Eq. 2.6 */
         for (int i = 0; i < q; ++i) f[i] = df[i] + L->w[i];
@@ -561,8 +588,14 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
           for (int k = 0; k < q; ++k)
             veq[k] = maxwell_central_moment(L->expo[k], rho);
         }
-        relax(L, m, L->Pcm, L->Pcminv, tmp, veq, vout);
-        add_first_order(L, F, vout);
+        if (he) {
+          double sK[QMAX];
+          matvec(q, K, S, sK);
+          relax_forced(L, m, L->Pcm, L->Pcminv, tmp, veq, sK, vout);
+        } else {
+          relax(L, m, L->Pcm, L->Pcminv, tmp, veq, vout);
+          add_first_order(L, F, vout);
+        }
         matvec(q, Kinv, vout, tmp2);
         for (int i = 0; i < q; ++i) out[i] = tmp2[i] - L->w[i];
       }
@@ -621,7 +654,7 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
 
 static int collide_cell(const lattice_t* L, const lbm_oracle_method* m,
                         const double* df, double* out) {
-  return collide_cell_f(L, m, df, NULL, 0.0, out);
+  return collide_cell_f(L, m, df, NULL, 0.0, 0, out);
 }
 
 static int check_method(const lbm_oracle_method* m) {
@@ -756,15 +789,16 @@ int lbm_oracle_collide(const lbm_oracle_method* m, int64_t ncells,
 
 int lbm_oracle_collide_forced(const lbm_oracle_method* m, int64_t ncells,
                               const double* df_in, const double* force,
-                              double* df_out) {
+                              int model, double* df_out) {
   int rc = check_method(m);
   if (rc) return rc;
-  if (!force || m->space == LBM_ORACLE_SPACE_NONE) return -1;
+  if (!force || m->space == LBM_ORACLE_SPACE_NONE || model < 0 || model > 1)
+    return -1;
   const lattice_t* L = &g_lat[m->stencil];
   for (int64_t c = 0; c < ncells; ++c) {
     double tmp[QMAX], F[3] = {0, 0, 0};
     for (int d = 0; d < L->d; ++d) F[d] = force[c * 3 + d];
-    rc = collide_cell_f(L, m, df_in + c * L->q, F, 0.0, tmp);
+    rc = collide_cell_f(L, m, df_in + c * L->q, F, 0.0, model, tmp);
     if (rc) return rc;
     memcpy(df_out + c * L->q, tmp, sizeof(double) * L->q);
   }
@@ -815,21 +849,22 @@ int lbm_oracle_init(const lbm_oracle_method* m, const int64_t* dims,
 
 int lbm_oracle_step(const lbm_oracle_method* m, const int64_t* dims,
                     double* df, int64_t nsteps, int nthreads) {
-  return lbm_oracle_step_forced(m, dims, df, NULL, nsteps, nthreads);
+  return lbm_oracle_step_forced(m, dims, df, NULL, 0, nsteps, nthreads);
 }
 
 static int step_impl(const lbm_oracle_method* m, const int64_t* dims,
-                     double* df, const double* force, double swe_g,
+                     double* df, const double* force, double swe_g, int model,
                      int64_t nsteps, int nthreads);
 
 int lbm_oracle_step_forced(const lbm_oracle_method* m, const int64_t* dims,
-                           double* df, const double* force, int64_t nsteps,
-                           int nthreads) {
-  return step_impl(m, dims, df, force, 0.0, nsteps, nthreads);
+                           double* df, const double* force, int model,
+                           int64_t nsteps, int nthreads) {
+  if (model < 0 || model > 1) return -1;
+  return step_impl(m, dims, df, force, 0.0, model, nsteps, nthreads);
 }
 
 static int step_impl(const lbm_oracle_method* m, const int64_t* dims,
-                     double* df, const double* force, double swe_g,
+                     double* df, const double* force, double swe_g, int model,
                      int64_t nsteps, int nthreads) {
   int rc = check_method(m);
   if (rc) return rc;
@@ -856,7 +891,7 @@ static int step_impl(const lbm_oracle_method* m, const int64_t* dims,
       for (int i = 0; i < q; ++i) in[i] = df[i * N + c];
       if (force)
         for (int d = 0; d < L->d; ++d) F[d] = force[d * N + c];
-      if (collide_cell_f(L, m, in, force ? F : NULL, swe_g, post)) err |= 1;
+      if (collide_cell_f(L, m, in, force ? F : NULL, swe_g, model, post)) err |= 1;
       /* Eq. 2.1b: f_i(x + xi_i, t + 1) = f*_i(x, t), periodic */
       for (int i = 0; i < q; ++i) {
         int64_t xd = (x + L->xi[i][0] + nx) % nx;
@@ -1136,7 +1171,7 @@ int lbm_oracle_swe_collide(const lbm_oracle_method* m, double g, int64_t ncells,
   const lattice_t* L = &g_lat[m->stencil];
   for (int64_t c = 0; c < ncells; ++c) {
     double tmp[QMAX];
-    rc = collide_cell_f(L, m, df_in + c * L->q, NULL, g, tmp);
+    rc = collide_cell_f(L, m, df_in + c * L->q, NULL, g, 0, tmp);
     if (rc) return rc;
     memcpy(df_out + c * L->q, tmp, sizeof(double) * L->q);
   }
@@ -1167,5 +1202,5 @@ int lbm_oracle_swe_step(const lbm_oracle_method* m, double g,
                         int nthreads) {
   int rc = swe_check(m, g);
   if (rc) return rc;
-  return step_impl(m, dims, df, NULL, g, nsteps, nthreads);
+  return step_impl(m, dims, df, NULL, g, 0, nsteps, nthreads);
 }

@@ -142,15 +142,19 @@ int lbm_oracle_macroscopic(const lbm_oracle_method* m, const int64_t* dims,
  *               (kappa_1 = -F/2 before and +F/2 after the collision)
  *   cumulant:   cumulants of order >= 2 relax as without force; the
  *               first-order cumulant (mean velocity) leaves as (j + F)/rho.
+ * model 0 is Guo's model above; model 1 is He's: the same velocity shift and
+ * (I - S/2) weighting with the source S_i = (xi_i - u).F / (rho c_s^2)
+ * f_eq_i (the method's absolute equilibrium populations), entering central
+ * space as q^F = (I - S/2) P K(u) S; not defined for cumulants (-1).
  * collide: force[ncells][3] cell-major (z ignored for D2Q9).  step /
  * macroscopic: force SoA [D][N] (D = 2 for D2Q9, else 3), constant in time,
  * NULL = none; macroscopic then returns the fluid velocity (j + F/2)/rho. */
 int lbm_oracle_collide_forced(const lbm_oracle_method* m, int64_t ncells,
                               const double* df_in, const double* force,
-                              double* df_out);
+                              int model, double* df_out);
 int lbm_oracle_step_forced(const lbm_oracle_method* m, const int64_t* dims,
-                           double* df, const double* force, int64_t nsteps,
-                           int nthreads);
+                           double* df, const double* force, int model,
+                           int64_t nsteps, int nthreads);
 int lbm_oracle_macroscopic_forced(const lbm_oracle_method* m,
                                   const int64_t* dims, const double* df,
                                   const double* force, double* rho, double* u);

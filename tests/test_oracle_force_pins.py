@@ -140,3 +140,76 @@ def test_trt_is_raw_mrt_with_rates_by_parity(st, eq, forced):
     else:
         a, b = O.collide(trt, df), O.collide(mrt, df)
     assert np.abs(a - b).max() < 1e-15
+
+
+# --------------------------------------------------------------- He's model
+HE_SPACES = [O.SPACE_POPULATIONS, O.SPACE_RAW, O.SPACE_CENTRAL, O.SPACE_TRT,
+             O.SPACE_RAW_WEIGHTED]
+
+
+@pytest.mark.parametrize("space", HE_SPACES)
+@pytest.mark.parametrize("st", [O.D2Q9, O.D3Q19, O.D3Q27])
+def test_he_force_adds_exactly_F_and_keeps_mass(st, space):
+    df = random_cells(st, 16, seed=40 + space)
+    F = 1e-3 * np.random.default_rng(9).standard_normal((16, 3))
+    if st == O.D2Q9:
+        F[:, 2] = 0
+    m = O.method(st, space, O.EQ_ABSOLUTE, [1.3, 1.1, 1.2, 1.4, 1.5, 1.6])
+    out = O.collide_forced(m, df, F, model=O.FORCE_HE)
+    rho0, j0 = moments(st, df)
+    rho1, j1 = moments(st, out)
+    assert np.abs(rho1 - rho0).max() < 1e-15
+    assert np.abs(j1 - (j0 + F)).max() < 1e-15
+
+
+@pytest.mark.parametrize("st", [O.D2Q9, O.D3Q19, O.D3Q27])
+def test_he_and_guo_agree_to_second_order_for_central_moments(st):
+    """He's source has Guo's moments up to order 2 except for terms of order
+    u^3 F (the lattice aliases the equilibrium's odd central moments), so
+    the two collisions' second-order raw moments differ by O(u^3 F): halving
+    the velocity divides the difference by 8."""
+    _, w, ex = O.lattice(st)
+    M = O.matrices(st)["M"]
+    low = ex.sum(1) <= 2
+    rng = np.random.default_rng(10)
+    F = 1e-3 * rng.standard_normal((16, 3))
+    u0 = 0.08 * rng.standard_normal((16, 3))
+    if st == O.D2Q9:
+        F[:, 2] = 0
+        u0[:, 2] = 0
+    rho = 1 + 0.02 * rng.standard_normal(16)
+    m = O.method(st, O.SPACE_CENTRAL, O.EQ_ABSOLUTE, [1.3, 1.1, 1.2, 1.4, 1.5, 1.6])
+    diff = []
+    for sc in (1.0, 0.5):
+        df = O.equilibrium(m, rho, sc * u0)
+        a = O.collide_forced(m, df, F, model=O.FORCE_HE)
+        b = O.collide_forced(m, df, F, model=O.FORCE_GUO)
+        diff.append(np.abs((a - b) @ M.T[:, low]).max())
+        assert np.abs((a - b) @ M.T[:, ~low]).max() > 1e-9  # different models
+    assert diff[0] < 10 * np.abs(u0).max() ** 3 * np.abs(F).max()
+    assert 6.5 < diff[0] / diff[1] < 9.5, diff
+
+
+@pytest.mark.parametrize("space", [O.SPACE_POPULATIONS, O.SPACE_RAW, O.SPACE_CENTRAL])
+def test_he_kolmogorov_flow_steady_state(space):
+    ny, st = 32, O.D3Q27
+    dims = (1, ny, 1)
+    k = 2 * np.pi / ny
+    omega = 1.6
+    nu = (1.0 / omega - 0.5) / 3.0
+    F0 = 1e-6
+    force = np.zeros((3, 1, ny, 1))
+    force[0, 0, :, 0] = F0 * np.sin(k * np.arange(ny))
+    m = O.method(st, space, O.EQ_ABSOLUTE, [omega] + [1.0] * 5)
+    df = O.init(m, dims, np.ones((1, ny, 1)), np.zeros((3, 1, ny, 1)))
+    df = O.step_forced(m, dims, df, force, int(12 / (nu * k * k)), model=O.FORCE_HE)
+    _, u = O.macroscopic_forced(m, dims, df, force)
+    amp = F0 / (nu * k * k)
+    err = np.abs(u[0, 0, :, 0] - amp * np.sin(k * np.arange(ny))).max() / amp
+    assert err < 0.01, err
+
+
+def test_he_is_undefined_for_cumulants():
+    m = O.method(O.D3Q27, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [1.3] + [1.0] * 5)
+    with pytest.raises(RuntimeError):
+        O.collide_forced(m, random_cells(O.D3Q27, 2, seed=1), [1e-3, 0, 0], model=O.FORCE_HE)
