@@ -278,6 +278,17 @@ int lbm_set_stream(lbm_ctx* ctx, void* stream);
 int lbm_set_force(lbm_ctx* ctx, const double* F);
 int lbm_set_force_field(lbm_ctx* ctx, const double* F, int on_device);
 
+/* Force model of the source term: LBM_FORCE_GUO (default, above) or
+ * LBM_FORCE_HE: He's model with the same velocity shift and (I - S/2)
+ * weighting but the source S_i = (xi_i - u).F / (rho c_s^2) f_eq_i, f_eq_i
+ * the method's absolute equilibrium populations (truncated raw moments for
+ * POPULATIONS, TRT, RAW, RAW_WEIGHTED; the full Maxwellian for CENTRAL, where
+ * q^F = (I - S/2) P K(u) S).  He's model is not defined for cumulants:
+ * LBM_ERR_UNSUPPORTED.  Errors: INVALID, UNSUPPORTED. */
+#define LBM_FORCE_GUO 0
+#define LBM_FORCE_HE 1
+int lbm_set_force_model(lbm_ctx* ctx, int model);
+
 /* Shallow-water methods (Sec. 5.2), g > 0 the gravity in lattice units
  * (g = 0 returns to the context's own method).  The context must be D2Q9,
  * LBM_STORE_F64_ABSOLUTE, LBM_EQ_ABSOLUTE, pull, space CENTRAL or CUMULANT,

@@ -285,6 +285,13 @@ void update_force_mode(lbm_ctx* c) {
 
 }  // namespace
 
+int lbm_set_force_model(lbm_ctx* c, int model) {
+  if (!c || (model != LBM_FORCE_GUO && model != LBM_FORCE_HE)) return LBM_ERR_INVALID;
+  if (model == LBM_FORCE_HE && c->p.space == LBM_SPACE_CUMULANT) return LBM_ERR_UNSUPPORTED;
+  c->force_model = model;
+  return LBM_OK;
+}
+
 int lbm_set_force(lbm_ctx* c, const double* F) {
   if (!c) return LBM_ERR_INVALID;
   if (F) {
@@ -467,6 +474,7 @@ int lbm_step(lbm_ctx* c, int64_t n) {
   a.variant = use_staged(c) ? lbm::VARIANT_STAGED : lbm::VARIANT_DIRECT;
   a.status = c->status;
   a.force_mode = c->force_mode;
+  a.force_model = c->force_model;
   for (int d = 0; d < 3; ++d) a.force[d] = c->force[d];
   a.force_field = c->force_field;
   if (c->force_mode) a.reg = 0;  // forced kernels: the general instantiation

@@ -513,15 +513,33 @@ LBM_D void guo_source(const T (&u)[3], const T (&F)[3], T (&S)[q_of(ST)]) {
   });
 }
 
-// FORCED: a body force F per cell (source term of Eq. 2.1a, q^F of Eq. 2.4,
-// Guo's model).  The equilibrium velocity is u = (j + F/2) / rho and
+// He's population source: S_i = 3 (xi_i - u).F / rho * f_eq_i with the
+// method's absolute equilibrium populations f_eq (truncated raw moments for
+// SRT / TRT / raw spaces, the full Maxwellian for central moments).
+template <int ST, class T, int SPACE>
+LBM_D void he_source(T drho, T inv, const T (&u)[3], const T (&F)[3], T (&S)[q_of(ST)]) {
+  T feq[q_of(ST)];
+  equilibrium<ST, T, (SPACE == SP_CENTRAL ? SP_CENTRAL : SP_RAW)>(drho, u, feq);
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1), cz = vel(ST, i, 2);
+    const T cf = (T(cx) - u[0]) * F[0] + (T(cy) - u[1]) * F[1] + (T(cz) - u[2]) * F[2];
+    S[i] = T(3) * cf * inv * (feq[i] + T(weight(ST, i)));
+  });
+}
+
+// FORCED: a body force F per cell (source term of Eq. 2.1a, q^F of Eq. 2.4;
+// Guo's model, or He's with HE: the same velocity shift and (I - S/2)
+// weighting with he_source for S, in central space q^F = (I - S/2) K(u) S).  The equilibrium velocity is u = (j + F/2) / rho and
 //   SRT: f* = f + w (f_eq - f) + (1 - w/2) S
 //   raw: q^F = (I - S/2) P M S in the orthogonal basis (general path only)
 //   central: moments about u, first-order central moments leave as +F/2
 //   cumulant: cumulants relax about the mean j / rho; the mean leaves as
 //             (j + F) / rho (cumulants of order >= 2 are shift invariant).
-template <int ST, class T, int SPACE, bool REG, bool DEFER = false, bool FORCED = false>
+template <int ST, class T, int SPACE, bool REG, bool DEFER = false, bool FORCED = false,
+          bool HE = false>
 LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr) {
+  static_assert(!(HE && SPACE == SP_CUMULANT), "He's model is not defined for cumulants");
   static_assert(!(FORCED && REG && (SPACE == SP_RAW || SPACE == SP_RAW_W)),
                 "forced raw moments use the general path");
   constexpr bool WO = SPACE == SP_RAW_W;
@@ -542,6 +560,10 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
                   SHIFT ? (j[1] + T(0.5) * Fv[1]) * inv : j[1] * inv,
                   SHIFT ? (j[2] + T(0.5) * Fv[2]) * inv : j[2] * inv};
   const T u2[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
+  auto force_source = [&](T (&S)[q_of(ST)]) {
+    if constexpr (HE) he_source<ST, T, SPACE>(drho, inv, u, Fv, S);
+    else guo_source<ST, T>(u, Fv, S);
+  };
 
   if constexpr (SPACE == SP_SRT) {
     // single relaxation time in population space against f_eq = M^-1 m_eq
@@ -549,7 +571,7 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
     equilibrium<ST, T, SP_RAW>(drho, u, feq);
     if constexpr (FORCED) {
       T S[q_of(ST)];
-      guo_source<ST, T>(u, Fv, S);
+      force_source(S);
       const T half = T(0.5) * (T(1) + keep.om[0]);  // 1 - w/2
       sfor<q_of(ST)>([&](auto I) {
         constexpr int i = CI(I);
@@ -568,7 +590,7 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
     // keep.om[0] = 1 - w+, the odd part with keep.om[2] = 1 - w-
     T feq[q_of(ST)], S[q_of(ST)];
     equilibrium<ST, T, SP_RAW>(drho, u, feq);
-    if constexpr (FORCED) guo_source<ST, T>(u, Fv, S);
+    if constexpr (FORCED) force_source(S);
     const T kp = keep.om[0], km = keep.om[2];
     sfor<q_of(ST)>([&](auto I) {
       constexpr int i = CI(I);
@@ -623,7 +645,7 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
       // q^F = (I - S/2) P M S: the source's raw moments in the orthogonal
       // basis, each rate group scaled by 1 - w/2 (conserved rows by 1)
       T S[q_of(ST)], G[3][3][3];
-      guo_source<ST, T>(u, Fv, S);
+      force_source(S);
       fwd_raw_chimera<ST, T>(S, G);
       G[0][0][0] = T(0);
       ortho_raw<ST, -1, T, WO>(G);
@@ -668,6 +690,38 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
           else Kn[a][b][c] *= keep.om[o - 1];
         }
       });
+      if constexpr (FORCED && HE) {
+        // q^F = (I - S/2) K(u) S: central moments of He's source about u,
+        // scaled per rate group, added to the normalised deviations
+        T S[q_of(ST)], G[3][3][3];
+        force_source(S);
+        fwd_raw_chimera<ST, T>(S, G);
+        if constexpr (dim_of(ST) == 3) {
+          sfor<9>([&](auto K) {
+            binom3<-1, T, 0>(G[CI(K) / 3][CI(K) % 3][0], G[CI(K) / 3][CI(K) % 3][1],
+                             G[CI(K) / 3][CI(K) % 3][2], u[2], u2[2], T(0));
+          });
+        }
+        sfor<9>([&](auto K) {
+          constexpr int a = CI(K) / 3, c = CI(K) % 3;
+          if constexpr (dim_of(ST) == 3 || c == 0)
+            binom3<-1, T, 0>(G[a][0][c], G[a][1][c], G[a][2][c], u[1], u2[1], T(0));
+        });
+        sfor<9>([&](auto K) {
+          constexpr int b = CI(K) / 3, c = CI(K) % 3;
+          if constexpr (dim_of(ST) == 3 || c == 0)
+            binom3<-1, T, 0>(G[0][b][c], G[1][b][c], G[2][b][c], u[0], u2[0], T(0));
+        });
+        relax_order2<ST, T, false>(G, T(0.5) * (T(1) + keep.om[0]), T(0.5) * (T(1) + keep.om[1]));
+        sfor<27>([&](auto K) {
+          constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+          constexpr int o = a + b + c;
+          if constexpr (has_mono(ST, a, b, c) && o >= 2) {
+            if constexpr (o >= 3) Kn[a][b][c] += T(0.5) * (T(1) + keep.om[o - 1]) * G[a][b][c] * inv;
+            else Kn[a][b][c] += G[a][b][c] * inv;
+          }
+        });
+      }
     } else {  // cumulants; equilibrium deviations are all 0 as well
       T Cm[3][3][3];
       sfor<27>([&](auto K) {

@@ -18,7 +18,7 @@ struct Geo {
 enum { STORE_F64 = 0, STORE_F32 = 1, STORE_F16 = 2, STORE_BF16 = 3, STORE_F64_ABS = 4 };
 enum { MODE_PULL = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2, MODE_ET_EVEN = 3, MODE_ET_ODD = 4 };
 enum { VARIANT_DIRECT = 0, VARIANT_STAGED = 1 };
-enum { FORCE_NONE = 0, FORCE_UNIFORM = 1, FORCE_FIELD = 2 };
+enum { FORCE_NONE = 0, FORCE_UNIFORM = 1, FORCE_FIELD = 2, FORCE_UNIFORM_HE = 3, FORCE_FIELD_HE = 4 };
 
 // shared-memory staged pull kernel (lbm_staged.cuh); the stage cap is a
 // compile-time tuning knob
@@ -52,6 +52,7 @@ struct StepArgs {
   int variant;  // VARIANT_DIRECT / VARIANT_STAGED (pull only)
   int* status;  // device word set by a kernel whose bounded wait ran out
   int force_mode;           // FORCE_NONE / FORCE_UNIFORM / FORCE_FIELD
+  int force_model;          // 0 Guo, 1 He
   double force[3];          // uniform body force
   const void* force_field;  // per-cell force [D][N] in the compute type (FORCE_FIELD)
   double swe_g;             // > 0: shallow-water method with this gravity (D2Q9)
@@ -151,6 +152,7 @@ struct lbm_ctx {
   int* status;    // device word after the invariants scratch: nonzero = a bounded wait ran out
   int kernel;     // requested step kernel (LBM_STEP_*)
   int force_mode;     // lbm::FORCE_*
+  int force_model;    // LBM_FORCE_GUO / LBM_FORCE_HE
   double force[3];    // uniform body force (zeros when unset)
   void* force_field;  // device [D][N] in the compute type, or NULL
   double swe_g;       // > 0: shallow-water method (lbm_set_shallow_water)

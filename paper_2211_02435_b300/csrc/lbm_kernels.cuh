@@ -76,7 +76,7 @@ template <int ST, int FORCE, class T>
 LBM_D void cell_force(const ForceArg<T>& fa, const Geo& g, int c, T (&Fc)[3]) {
   for (int d = 0; d < 3; ++d) {
     Fc[d] = d < dim_of(ST) ? fa.F[d] : T(0);
-    if constexpr (FORCE == FORCE_FIELD)
+    if constexpr (FORCE == FORCE_FIELD || FORCE == FORCE_FIELD_HE)
       if (d < dim_of(ST)) Fc[d] += fa.field[(int64_t)d * g.N + c];
   }
 }
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(LBM_BX) k_pull(const __grid_constant__ PullPtr
   if constexpr (FORM == FORM_DEV && FORCE != FORCE_NONE) {
     T Fc[3];
     cell_force<ST, FORCE>(fa, g, c, Fc);
-    collide<ST, T, SPACE, REG, false, true>(f, keep, Fc);
+    collide<ST, T, SPACE, REG, false, true, (FORCE >= FORCE_UNIFORM_HE)>(f, keep, Fc);
   } else if constexpr (FORM == FORM_DEV) {
     collide<ST, T, SPACE, REG>(f, keep);
   } else {
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(LBM_BX) k_aa(S* buf, Geo g, Rates<T> keep,
   if constexpr (FORCE != FORCE_NONE) {
     T Fc[3];
     cell_force<ST, FORCE>(fa, g, c, Fc);
-    collide<ST, T, SPACE, REG, false, true>(f, keep, Fc);
+    collide<ST, T, SPACE, REG, false, true, (FORCE >= FORCE_UNIFORM_HE)>(f, keep, Fc);
   } else {
     collide<ST, T, SPACE, REG>(f, keep);
   }
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(LBM_BX) k_et(S* buf, Geo g, Rates<T> keep,
   if constexpr (FORCE != FORCE_NONE) {
     T Fc[3];
     cell_force<ST, FORCE>(fa, g, c, Fc);
-    collide<ST, T, SPACE, REG, false, true>(f, keep, Fc);
+    collide<ST, T, SPACE, REG, false, true, (FORCE >= FORCE_UNIFORM_HE)>(f, keep, Fc);
   } else {
     collide<ST, T, SPACE, REG>(f, keep);
   }
@@ -537,40 +537,37 @@ void launch_forced(const StepArgs& a, const Rates<T>& keep, const dim3& grid) {
   ForceArg<T> fa;
   for (int d = 0; d < 3; ++d) fa.F[d] = T(a.force[d]);
   fa.field = (const T*)a.force_field;
-  const bool field = a.force_mode == FORCE_FIELD;
-  if (a.mode == MODE_PULL) {
-    PullPtrs<S> P;
-    const int64_t nx = a.g.nx, nxy = int64_t(a.g.nx) * a.g.ny;
-    for (int i = 0; i < 27; ++i) {
-      const int64_t delta =
-          i < q_of(ST) ? -(vel(ST, i, 2) * nxy + vel(ST, i, 1) * nx + vel(ST, i, 0)) : 0;
-      P.src[i] = i < q_of(ST) ? (const S*)a.src + (int64_t(i) * a.g.N + delta) : nullptr;
-      P.dst[i] = i < q_of(ST) ? (S*)a.dst + int64_t(i) * a.g.N : nullptr;
+  auto go = [&](auto force_tag) {
+    constexpr int FC = decltype(force_tag)::value;
+    if constexpr (FC >= FORCE_UNIFORM_HE && SPACE == SP_CUMULANT) {
+      return;  // refused at lbm_set_force_model
+    } else if (a.mode == MODE_PULL) {
+      PullPtrs<S> P;
+      const int64_t nx = a.g.nx, nxy = int64_t(a.g.nx) * a.g.ny;
+      for (int i = 0; i < 27; ++i) {
+        const int64_t delta =
+            i < q_of(ST) ? -(vel(ST, i, 2) * nxy + vel(ST, i, 1) * nx + vel(ST, i, 0)) : 0;
+        P.src[i] = i < q_of(ST) ? (const S*)a.src + (int64_t(i) * a.g.N + delta) : nullptr;
+        P.dst[i] = i < q_of(ST) ? (S*)a.dst + int64_t(i) * a.g.N : nullptr;
+      }
+      k_pull<ST, S, T, SPACE, false, FORM_DEV, FC><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep, fa);
+    } else if (a.mode == MODE_ET_EVEN) {
+      k_et<ST, S, T, SPACE, false, false, FC><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
+    } else if (a.mode == MODE_ET_ODD) {
+      k_et<ST, S, T, SPACE, false, true, FC><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
+    } else if (a.mode == MODE_AA_EVEN) {
+      k_aa<ST, S, T, SPACE, false, false, FC><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
+    } else {
+      k_aa<ST, S, T, SPACE, false, true, FC><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
     }
-    if (field)
-      k_pull<ST, S, T, SPACE, false, FORM_DEV, FORCE_FIELD><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep, fa);
-    else
-      k_pull<ST, S, T, SPACE, false, FORM_DEV, FORCE_UNIFORM><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep, fa);
-  } else if (a.mode == MODE_ET_EVEN || a.mode == MODE_ET_ODD) {
-    const bool odd = a.mode == MODE_ET_ODD;
-    if (field && odd)
-      k_et<ST, S, T, SPACE, false, true, FORCE_FIELD><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
-    else if (field)
-      k_et<ST, S, T, SPACE, false, false, FORCE_FIELD><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
-    else if (odd)
-      k_et<ST, S, T, SPACE, false, true, FORCE_UNIFORM><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
-    else
-      k_et<ST, S, T, SPACE, false, false, FORCE_UNIFORM><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
-  } else if (a.mode == MODE_AA_EVEN) {
-    if (field)
-      k_aa<ST, S, T, SPACE, false, false, FORCE_FIELD><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
-    else
-      k_aa<ST, S, T, SPACE, false, false, FORCE_UNIFORM><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
+  };
+  const bool field = a.force_mode == FORCE_FIELD;
+  if (a.force_model == 1) {
+    if (field) go(std::integral_constant<int, FORCE_FIELD_HE>{});
+    else go(std::integral_constant<int, FORCE_UNIFORM_HE>{});
   } else {
-    if (field)
-      k_aa<ST, S, T, SPACE, false, true, FORCE_FIELD><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
-    else
-      k_aa<ST, S, T, SPACE, false, true, FORCE_UNIFORM><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
+    if (field) go(std::integral_constant<int, FORCE_FIELD>{});
+    else go(std::integral_constant<int, FORCE_UNIFORM>{});
   }
 }
 

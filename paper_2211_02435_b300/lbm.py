@@ -23,6 +23,7 @@ EQ_DELTA, EQ_ABSOLUTE = 0, 1
 STORE_F64, STORE_F32, STORE_F16_DELTA, STORE_BF16_DELTA, STORE_F64_ABSOLUTE = 0, 1, 2, 3, 4
 ARITH_DEVIATION, ARITH_AS_WRITTEN = 0, 1
 STEP_AUTO, STEP_DIRECT, STEP_STAGED = 0, 1, 2
+FORCE_GUO, FORCE_HE = 0, 1
 PULL, AA, ESOTERIC_TWIST = 0, 1, 2
 PERIODIC = 0
 Q_OF = {D2Q9: 9, D3Q19: 19, D3Q27: 27}
@@ -93,6 +94,7 @@ def lib():
         L.lbm_set_step_kernel.argtypes = [vp, c_int]
         L.lbm_set_force.argtypes = [vp, vp]
         L.lbm_set_force_field.argtypes = [vp, vp, c_int]
+        L.lbm_set_force_model.argtypes = [vp, c_int]
         L.lbm_set_shallow_water.argtypes = [vp, ctypes.c_double]
         L.lbm_destroy.argtypes = [vp]
         L.lbm_destroy.restype = None
@@ -315,6 +317,10 @@ class Lattice:
             return
         arr = (ctypes.c_double * 3)(*[float(v) for v in list(F)[:3]])
         _check(lib().lbm_set_force(self._h, ctypes.cast(arr, ctypes.c_void_p)), "lbm_set_force")
+
+    def set_force_model(self, model):
+        """FORCE_GUO (default) or FORCE_HE (include/lbm.h)."""
+        _check(lib().lbm_set_force_model(self._h, int(model)), "lbm_set_force_model")
 
     def set_force_field(self, F):
         """Per-cell body force [D, N] (numpy FP64 or a CUDA tensor); None removes it."""

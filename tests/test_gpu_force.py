@@ -60,7 +60,7 @@ def force_of(st, kind):
 
 
 @functools.lru_cache(maxsize=None)
-def case(st, mi, fkind):
+def case(st, mi, fkind, model=0):
     space, eq, rk = METHODS[mi]
     dims = DIMS[st]
     d = 2 if st == 0 else 3
@@ -72,7 +72,7 @@ def case(st, mi, fkind):
     pert = I.random_deviations(len(w), int(np.prod(dims)), 2e-3, seed=32)
     df0 = df + (w[:, None] * pert).reshape(df.shape)
     F = force_of(st, fkind)
-    ref = {n: O.step_forced(m, dims, df0, F, n) for n in (3, 4)}
+    ref = {n: O.step_forced(m, dims, df0, F, n, model=model) for n in (3, 4)}
     return m, dims, df0, F, ref
 
 
@@ -99,6 +99,40 @@ def test_forced_step_parity(st, mi, storage, streaming, fkind):
             rho_r, u_r = O.macroscopic_forced(m, dims, ref[n], F)
             rho_g, u_g = lat.macroscopic()
             assert rel_linf(u_g, u_r) < TOL[storage]
+
+
+HE_METHODS = [i for i, m in enumerate(METHODS) if m[0] != L.SPACE_CUMULANT]
+
+
+@pytest.mark.parametrize("fkind", ["uniform", "field"])
+@pytest.mark.parametrize("streaming", [L.PULL, L.ESOTERIC_TWIST])
+@pytest.mark.parametrize("storage", [L.STORE_F64, L.STORE_F32])
+@pytest.mark.parametrize("mi", HE_METHODS, ids=[f"sp{METHODS[i][0]}eq{METHODS[i][1]}{METHODS[i][2]}"
+                                                for i in HE_METHODS])
+@pytest.mark.parametrize("st", [0, 1, 2], ids=["D2Q9", "D3Q19", "D3Q27"])
+def test_he_forced_step_parity(st, mi, storage, streaming, fkind):
+    m, dims, df0, F, ref = case(st, mi, fkind, O.FORCE_HE)
+    space, eq, rk = METHODS[mi]
+    with L.Lattice(st, space, eq, storage, streaming, rates_of(rk), dims) as lat:
+        lat.set_force_model(L.FORCE_HE)
+        if fkind == "uniform":
+            lat.set_force(F)
+        else:
+            lat.set_force_field(F)
+        lat.set_populations(df0)
+        lat.step(3)
+        assert rel_linf(lat.get_populations(), ref[3]) < TOL[storage]
+
+
+def test_he_model_refused_for_cumulants():
+    with L.Lattice(2, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F32, L.PULL, RATES_UNIT,
+                   (8, 8, 8)) as lat:
+        with pytest.raises(L.LBMError) as e:
+            lat.set_force_model(L.FORCE_HE)
+        assert e.value.code == -2
+        with pytest.raises(L.LBMError) as e:
+            lat.set_force_model(7)
+        assert e.value.code == -1
 
 
 def test_removing_the_force_restores_the_plain_step():
