@@ -326,13 +326,22 @@ def run_cuda(args):
     # ---- headline: FP32 storage (or --storage), kernel-only, inputs in HBM
     main_store = {"f32": L.STORE_F32, "f16": L.STORE_F16_DELTA, "bf16": L.STORE_BF16_DELTA}[args.storage]
     main_key = {"f32": "f32", "f16": "f16_delta", "bf16": "bf16_delta"}[args.storage]
+    main_stream = {"pull": L.PULL, "aa": L.AA, "et": L.ESOTERIC_TWIST}[args.streaming]
+    main_force = None
+    if args.force == "uniform":
+        main_force = np.array([1e-6, 0.0, 0.0])
+    elif args.force == "field":
+        main_force = torch.full((3, N), 1e-6, dtype=torch.float64, device="cuda")
     with ClockSampler(local) as clk:
-        lat32, ms32 = time_form(main_store, args.steps, args.warmup)
+        lat32, ms32 = time_form(main_store, args.steps, args.warmup, streaming=main_stream,
+                                force=main_force)
+    del main_force
     clocks = clk.summary()
     ms_max = max_over_ranks(ms32, dist, "cuda")
     per_step_s = ms_max / 1e3 / args.steps
     value = job_mlups(world, N, args.steps, ms_max / 1e3)
-    achieved = BYTES_PER_CELL[main_key] * N / (ms32 / 1e3 / args.steps) / 1e9
+    main_bpc = BYTES_PER_CELL[main_key] + (12 if args.force == "field" else 0)
+    achieved = main_bpc * N / (ms32 / 1e3 / args.steps) / 1e9
     # velocity of the timed run, copied to the host once its stream is idle
     u32 = np.empty(3 * N)
     lat32.macroscopic(None, u32)
@@ -441,7 +450,8 @@ def run_cuda(args):
                "sample": f"{edge}^3 cells x {args.cpu_steps} steps of the same method and flow "
                          f"({dt:.1f} s, OpenMP over all cores)"}
 
-    traffic = kernel_traffic_per_cell() if args.storage == "f32" else None
+    default_kernel = args.storage == "f32" and args.streaming == "pull" and args.force == "none"
+    traffic = kernel_traffic_per_cell() if default_kernel else None
     if traffic is not None:
         traffic *= N
 
@@ -452,14 +462,19 @@ def run_cuda(args):
             "data": "synthetic",
             "config": {"workload": "D3Q27 cumulant LBM (R-: shear from nu=1e-3, bulk and "
                                    "orders 3-6 rate 1), periodic 512^3 Taylor-Green u0=0.05 "
-                                   f"+ uniform 1e-3 noise, {main_key} zero-centered storage, pull",
+                                   f"+ uniform 1e-3 noise, {main_key} zero-centered storage, "
+                                   f"{args.streaming}"
+                                   + ("" if args.force == "none" else f", {args.force} body force"),
                        "cells": N, "global_batch": world, "parallelism": "replicas",
                        "l2": "working set 29 GB >> 126 MB L2, no flush needed"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
-                         "bytes_per_cell": BYTES_PER_CELL[main_key],
-                         "kernel": f"k_pull<D3Q27, {main_key} storage, cumulant, regularised>",
+                         "bytes_per_cell": main_bpc,
+                         "kernel": (f"{ {'pull': 'k_pull', 'aa': 'k_aa', 'et': 'k_et'}[args.streaming]}"
+                                    f"<D3Q27, {main_key} storage, cumulant, "
+                                    + ("regularised>" if args.force == "none"
+                                       else f"{args.force} force>")),
                          "step_kernel": args.step_kernel},
             "forms": forms, "batched": batched, "learned": learned, "clocks": clocks, "e2e": e2e,
             "cpu_baseline": cpu,
@@ -495,6 +510,10 @@ def main():
     ap.add_argument("--batch-n", type=int, default=4096)
     ap.add_argument("--step-kernel", choices=list(STEP_KERNELS), default="auto",
                     help="pull step kernel of the D3Q27 forms (include/lbm.h)")
+    ap.add_argument("--streaming", choices=["pull", "aa", "et"], default="pull",
+                    help="streaming pattern of the headline run")
+    ap.add_argument("--force", choices=["none", "uniform", "field"], default="none",
+                    help="body force (Guo) of the headline run")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "cuda":
         args.warmup = 3
