@@ -220,28 +220,15 @@ __global__ void __launch_bounds__(LBM_BX) k_scatter_swe(AbsF64* buf, Geo g, cons
 }
 
 // Two cells per thread (x even, x + 1) with the collision on packed FP32
-// pairs, for FP16 / BF16 delta storage and even Nx.  Every direction reads
-// the aligned 2-element pair (x, x+1) of its source row; for xi_x = +-1 the
-// cell whose source lies in the neighbouring pair takes that element from
-// the neighbouring lane by a warp shuffle (lane 0 / lane 31 and the row ends
-// load it directly, with the periodic wrap).  All lanes of a warp stay
-// active for the shuffles; lanes past the row end load a valid pair and do
-// not store.  Stores are aligned 2-element stores.
-// LBM_PULL2_SHFL = 0 (compile time) reads the xi_x = +-1 cells with two
-// 2-element loads instead.
-#ifndef LBM_PULL2_SHFL
-#define LBM_PULL2_SHFL 1
-#endif
+// pairs, for FP16 / BF16 delta storage and even Nx.  Directions with
+// xi_x = 0 read both cells with one aligned 2-element load; the others read
+// the two cells separately (their x wrap differs at the row ends).  Stores
+// are aligned 2-element stores.
 template <int ST, class S, int SPACE, bool REG>
 __global__ void LBM_PULL2_BOUNDS k_pull2(const __grid_constant__ PullPtrs<S> P, Geo g,
                                                   Rates<P2> keep) {
-  const int x0 = 2 * (blockIdx.x * LBM_BX + threadIdx.x);
-  const bool active = x0 < g.nx;
-#if !LBM_PULL2_SHFL
-  if (!active) return;
-#endif
-  const int x = active ? x0 : g.nx - 2;
-  const int lane = threadIdx.x & 31;
+  const int x = 2 * (blockIdx.x * LBM_BX + threadIdx.x);
+  if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
   const int c = (z * g.ny + y) * g.nx + x;
   const int nxy = g.nx * g.ny;
@@ -255,37 +242,14 @@ __global__ void LBM_PULL2_BOUNDS k_pull2(const __grid_constant__ PullPtrs<S> P, 
     constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1), cz = vel(ST, i, 2);
     const int off = c + (cy > 0 ? wyp : (cy < 0 ? wym : 0)) + (cz > 0 ? wzp : (cz < 0 ? wzm : 0));
     P2 v;
-    if constexpr (cx == 0) {
-      v = Pack<S>::load2(P.src[i] + off);
-    } else {
-#if LBM_PULL2_SHFL
-      // the aligned pair (x, x+1) of the source row: undo the x shift
-      const uint32_t pr = Pack<S>::bits2(P.src[i] + off + cx);
-      if constexpr (cx > 0) {
-        // cell x reads x - 1: the high half of lane - 1's pair
-        const uint32_t nb = __shfl_up_sync(0xffffffffu, pr, 1);
-        const uint16_t left = lane == 0 ? Pack<S>::bits1(P.src[i] + off + wxp0)
-                                        : uint16_t(nb >> 16);
-        v = Pack<S>::from_bits(left, uint16_t(pr & 0xffffu));
-      } else {
-        // cell x + 1 reads x + 2: the low half of lane + 1's pair
-        const uint32_t nb = __shfl_down_sync(0xffffffffu, pr, 1);
-        const uint16_t right = (lane == 31 || x + 2 >= g.nx)
-                                   ? Pack<S>::bits1(P.src[i] + off + 1 + wxm1)
-                                   : uint16_t(nb & 0xffffu);
-        v = Pack<S>::from_bits(uint16_t(pr >> 16), right);
-      }
-#else
-      if constexpr (cx > 0) v = Pack<S>::load11(P.src[i] + off + wxp0, P.src[i] + off + 1);
-      else v = Pack<S>::load11(P.src[i] + off, P.src[i] + off + 1 + wxm1);
-#endif
-    }
+    if constexpr (cx == 0) v = Pack<S>::load2(P.src[i] + off);
+    else if constexpr (cx > 0) v = Pack<S>::load11(P.src[i] + off + wxp0, P.src[i] + off + 1);
+    else v = Pack<S>::load11(P.src[i] + off, P.src[i] + off + 1 + wxm1);
     f[i] = v * P2(1.0f / float(1u << scale_exp(ST, i)));
   });
   // the backward transform leaves population i multiplied by 2^|xi_i|^2;
   // the storage scale 2^s_i absorbs it exactly
   collide<ST, P2, SPACE, REG, true>(f, keep);
-  if (!active) return;
   sfor<q_of(ST)>([&](auto I) {
     constexpr int i = CI(I);
     constexpr int k = vel(ST, i, 0) * vel(ST, i, 0) + vel(ST, i, 1) * vel(ST, i, 1) +

@@ -90,12 +90,6 @@ template <class S>
 struct Pack;
 template <>
 struct Pack<__half> {
-  // raw bits: an aligned pair (low half = first element) and one element
-  P2F static uint32_t bits2(const __half* p) { return *reinterpret_cast<const uint32_t*>(p); }
-  P2F static uint16_t bits1(const __half* p) { return *reinterpret_cast<const uint16_t*>(p); }
-  P2F static P2 from_bits(uint16_t a, uint16_t b) {
-    return P2(make_float2(__half2float(__ushort_as_half(a)), __half2float(__ushort_as_half(b))));
-  }
   P2F static P2 load2(const __half* p) {
     return P2(__half22float2(*reinterpret_cast<const __half2*>(p)));
   }
@@ -108,16 +102,6 @@ struct Pack<__half> {
 };
 template <>
 struct Pack<__nv_bfloat16> {
-  P2F static uint32_t bits2(const __nv_bfloat16* p) {
-    return *reinterpret_cast<const uint32_t*>(p);
-  }
-  P2F static uint16_t bits1(const __nv_bfloat16* p) {
-    return *reinterpret_cast<const uint16_t*>(p);
-  }
-  P2F static P2 from_bits(uint16_t a, uint16_t b) {
-    return P2(make_float2(__bfloat162float(__ushort_as_bfloat16(a)),
-                          __bfloat162float(__ushort_as_bfloat16(b))));
-  }
   P2F static P2 load2(const __nv_bfloat16* p) {
     return P2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p)));
   }
