@@ -258,21 +258,65 @@ __global__ void LBM_PULL2_BOUNDS k_pull2(const __grid_constant__ PullPtrs<S> P, 
   });
 }
 
-// AA pattern, in place on one buffer (Sec. 4.3).  Even kernels read slot i
-// of the own cell and write f*_i into slot ibar of the own cell; odd
-// kernels read slot ibar at x - xi_i and write f*_i into slot i at
-// x + xi_i.  Each cell reads and writes the same set of addresses, so no
-// two threads touch one element.
-template <int ST, class S, class T, int SPACE, bool REG, bool ODD, int FORCE = FORCE_NONE>
-__global__ void __launch_bounds__(LBM_BX) k_aa(S* buf, Geo g, Rates<T> keep,
-                                               ForceArg<T> fa = {}) {
+// In-place streaming on one buffer (Sec. 4.3), both patterns through one
+// kernel with per-direction plane pointers (as the pull kernel): population
+// i is read from slot rd_i at node x + r_i and f*_i written to slot wr_i at
+// node x + w_i, with the offsets r_i, w_i in {-1, 0, 1}^3 baked into the
+// pointers and a wrap correction only on the periodic boundary.
+//   AA, even: r = w = 0, read slot i, write slot ibar (the own cell).
+//   AA, odd:  r = -xi_i, read slot ibar; w = +xi_i, write slot i.
+//   Esoteric Twist: with a_i = max(-xi_i, 0) per component, r = a_i and
+//     w = a_ibar; even steps read slot i and write slot ibar, odd steps read
+//     slot ibar and write slot i.  The cell writes exactly the elements it
+//     read (node x + a_ibar, slot ibar is where it read population ibar), so
+//     no two cells touch one element; at the next time f*_i sits at
+//     (x + xi_i) + a_i, the same rule with the slots swapped.
+// Each cell reads and writes the same set of elements in every variant.
+template <class S>
+struct InPlacePtrs {
+  const S* rd[27];
+  S* wr[27];
+};
+
+// the per-direction offsets and slots of an in-place variant
+template <int ST, int MODE, int i>
+struct InPlaceMap {
+  static constexpr int b = opp(i);
+  static constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1), cz = vel(ST, i, 2);
+  static constexpr bool ET = MODE == MODE_ET_EVEN || MODE == MODE_ET_ODD;
+  static constexpr bool ODD = MODE == MODE_AA_ODD || MODE == MODE_ET_ODD;
+  static constexpr int rx = ET ? (cx < 0 ? 1 : 0) : (MODE == MODE_AA_ODD ? -cx : 0);
+  static constexpr int ry = ET ? (cy < 0 ? 1 : 0) : (MODE == MODE_AA_ODD ? -cy : 0);
+  static constexpr int rz = ET ? (cz < 0 ? 1 : 0) : (MODE == MODE_AA_ODD ? -cz : 0);
+  static constexpr int wx = ET ? (cx > 0 ? 1 : 0) : (MODE == MODE_AA_ODD ? cx : 0);
+  static constexpr int wy = ET ? (cy > 0 ? 1 : 0) : (MODE == MODE_AA_ODD ? cy : 0);
+  static constexpr int wz = ET ? (cz > 0 ? 1 : 0) : (MODE == MODE_AA_ODD ? cz : 0);
+  static constexpr int rslot = ODD ? b : i;
+  static constexpr int wslot = ODD ? i : b;
+};
+
+template <int ST, class S, class T, int SPACE, bool REG, int MODE, int FORCE = FORCE_NONE>
+__global__ void __launch_bounds__(LBM_BX) k_inplace(const __grid_constant__ InPlacePtrs<S> P, Geo g,
+                                                    Rates<T> keep, ForceArg<T> fa = {}) {
   const int x = blockIdx.x * LBM_BX + threadIdx.x;
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
-  const Nbr n = neighbours(x, y, z, g);
   const int c = (z * g.ny + y) * g.nx + x;
+  const int nxy = g.nx * g.ny;
+  // wrap corrections for an offset of -1 (p) and +1 (m) per axis
+  const int wxp = x == 0 ? g.nx : 0, wxm = x == g.nx - 1 ? -g.nx : 0;
+  const int wyp = y == 0 ? nxy : 0, wym = y == g.ny - 1 ? -nxy : 0;
+  const int wzp = z == 0 ? int(g.N) : 0, wzm = z == g.nz - 1 ? -int(g.N) : 0;
+  auto wrap = [&](int ox, int oy, int oz) {
+    return (ox < 0 ? wxp : (ox > 0 ? wxm : 0)) + (oy < 0 ? wyp : (oy > 0 ? wym : 0)) +
+           (oz < 0 ? wzp : (oz > 0 ? wzm : 0));
+  };
   T f[q_of(ST)];
-  load_pops<ST, S, T, ODD ? G_AAODD : G_LOCAL>(buf, g, n, c, f);
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    using Mp = InPlaceMap<ST, MODE, i>;
+    f[i] = dec_pop<ST, i, S, T>(P.rd[i][c + wrap(Mp::rx, Mp::ry, Mp::rz)]);
+  });
   if constexpr (FORCE != FORCE_NONE) {
     T Fc[3];
     cell_force<ST, FORCE>(fa, g, c, Fc);
@@ -282,49 +326,41 @@ __global__ void __launch_bounds__(LBM_BX) k_aa(S* buf, Geo g, Rates<T> keep,
   }
   sfor<q_of(ST)>([&](auto I) {
     constexpr int i = CI(I);
-    constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1), cz = vel(ST, i, 2);
-    int dc = c, slot = opp(i);
-    if constexpr (ODD) {
-      dc = cell_at(n, g, cx, cy, cz);
-      slot = i;
-    }
-    buf[(int64_t)slot * g.N + dc] = enc_pop<ST, i, S, T>(f[i]);
+    using Mp = InPlaceMap<ST, MODE, i>;
+    P.wr[i][c + wrap(Mp::wx, Mp::wy, Mp::wz)] = enc_pop<ST, i, S, T>(f[i]);
   });
 }
 
-// Esoteric Twist, in place on one buffer (Sec. 4.3).  With a_i = max(-xi_i, 0)
-// per component, cell x reads population i from node x + a_i (slot i at even
-// times, slot ibar at odd times) and writes f*_i to node x + a_ibar (slot
-// ibar at even times, slot i at odd times).  Node x + a_ibar, slot ibar (even)
-// is one the cell has just read, so each cell writes exactly the elements it
-// read and no two cells touch one element; at the next time the population
-// sits at x + xi_i + a_i, the same rule with the slots swapped.  Even and odd
-// steps differ only in the slot labels; every step reaches the cell and its
-// positive neighbours.
-template <int ST, class S, class T, int SPACE, bool REG, bool ODD, int FORCE = FORCE_NONE>
-__global__ void __launch_bounds__(LBM_BX) k_et(S* buf, Geo g, Rates<T> keep,
-                                               ForceArg<T> fa = {}) {
-  const int x = blockIdx.x * LBM_BX + threadIdx.x;
-  if (x >= g.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
-  const Nbr n = neighbours(x, y, z, g);
-  const int c = (z * g.ny + y) * g.nx + x;
-  T f[q_of(ST)];
-  load_pops<ST, S, T, ODD ? G_ET_ODD : G_ET_EVEN>(buf, g, n, c, f);
-  if constexpr (FORCE != FORCE_NONE) {
-    T Fc[3];
-    cell_force<ST, FORCE>(fa, g, c, Fc);
-    collide<ST, T, SPACE, REG, false, true, (FORCE >= FORCE_UNIFORM_HE)>(f, keep, Fc);
-  } else {
-    collide<ST, T, SPACE, REG>(f, keep);
-  }
+// host: the pointer table of an in-place variant on buffer buf
+template <int ST, int MODE, class S>
+InPlacePtrs<S> inplace_ptrs(S* buf, const Geo& g) {
+  InPlacePtrs<S> P;
+  const int64_t nx = g.nx, nxy = int64_t(g.nx) * g.ny;
+  for (int i = 0; i < 27; ++i) P.rd[i] = nullptr, P.wr[i] = nullptr;
   sfor<q_of(ST)>([&](auto I) {
     constexpr int i = CI(I);
-    constexpr int b = opp(i);
-    const int dc = cell_at(n, g, et_off<ST, b, 0>(), et_off<ST, b, 1>(), et_off<ST, b, 2>());
-    const int slot = ODD ? i : b;
-    buf[(int64_t)slot * g.N + dc] = enc_pop<ST, i, S, T>(f[i]);
+    using Mp = InPlaceMap<ST, MODE, i>;
+    P.rd[i] = buf + (int64_t(Mp::rslot) * g.N + Mp::rz * nxy + Mp::ry * nx + Mp::rx);
+    P.wr[i] = buf + (int64_t(Mp::wslot) * g.N + Mp::wz * nxy + Mp::wy * nx + Mp::wx);
   });
+  return P;
+}
+
+template <int ST, class S, class T, int SPACE, bool REG, int FORCE = FORCE_NONE>
+void launch_inplace(const StepArgs& a, const Rates<T>& keep, const dim3& grid,
+                    const ForceArg<T>& fa = {}) {
+  S* buf = (S*)a.dst;
+  auto go = [&](auto mode_tag) {
+    constexpr int MODE = decltype(mode_tag)::value;
+    k_inplace<ST, S, T, SPACE, REG, MODE, FORCE>
+        <<<grid, LBM_BX, 0, a.stream>>>(inplace_ptrs<ST, MODE>(buf, a.g), a.g, keep, fa);
+  };
+  switch (a.mode) {
+    case MODE_AA_EVEN: go(std::integral_constant<int, MODE_AA_EVEN>{}); break;
+    case MODE_AA_ODD: go(std::integral_constant<int, MODE_AA_ODD>{}); break;
+    case MODE_ET_EVEN: go(std::integral_constant<int, MODE_ET_EVEN>{}); break;
+    default: go(std::integral_constant<int, MODE_ET_ODD>{}); break;
+  }
 }
 
 // ------------------------------------------------------ read-out kernels
@@ -551,14 +587,8 @@ void launch_forced(const StepArgs& a, const Rates<T>& keep, const dim3& grid) {
         P.dst[i] = i < q_of(ST) ? (S*)a.dst + int64_t(i) * a.g.N : nullptr;
       }
       k_pull<ST, S, T, SPACE, false, FORM_DEV, FC><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep, fa);
-    } else if (a.mode == MODE_ET_EVEN) {
-      k_et<ST, S, T, SPACE, false, false, FC><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
-    } else if (a.mode == MODE_ET_ODD) {
-      k_et<ST, S, T, SPACE, false, true, FC><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
-    } else if (a.mode == MODE_AA_EVEN) {
-      k_aa<ST, S, T, SPACE, false, false, FC><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
     } else {
-      k_aa<ST, S, T, SPACE, false, true, FC><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep, fa);
+      launch_inplace<ST, S, T, SPACE, false, FC>(a, keep, grid, fa);
     }
   };
   const bool field = a.force_mode == FORCE_FIELD;
@@ -626,14 +656,8 @@ void launch_step_typed(const StepArgs& a) {
     }
     k_pull<ST, S, T, SPACE, REG><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep);
   }
-  else if (a.mode == MODE_ET_EVEN)
-    k_et<ST, S, T, SPACE, REG, false><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep);
-  else if (a.mode == MODE_ET_ODD)
-    k_et<ST, S, T, SPACE, REG, true><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep);
-  else if (a.mode == MODE_AA_EVEN)
-    k_aa<ST, S, T, SPACE, REG, false><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep);
   else
-    k_aa<ST, S, T, SPACE, REG, true><<<grid, LBM_BX, 0, a.stream>>>((S*)a.dst, a.g, keep);
+    launch_inplace<ST, S, T, SPACE, REG>(a, keep, grid);
 }
 
 template <int ST, class S, class T>
