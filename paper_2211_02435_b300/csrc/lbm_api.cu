@@ -477,7 +477,10 @@ int lbm_step(lbm_ctx* c, int64_t n) {
   a.force_model = c->force_model;
   for (int d = 0; d < 3; ++d) a.force[d] = c->force[d];
   a.force_field = c->force_field;
-  if (c->force_mode) a.reg = 0;  // forced kernels: the general instantiation
+  // forced raw-moment collisions use the general instance (the source needs
+  // every orthogonal row)
+  if (c->force_mode && (c->space == LBM_SPACE_RAW || c->space == LBM_SPACE_RAW_WEIGHTED))
+    a.reg = 0;
   a.swe_g = c->swe_g;
   if (c->swe_g > 0.0) a.reg = 0;  // shallow water: the general instantiation
   a.stream = c->stream;

@@ -566,9 +566,8 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS)
 // --------------------------------------------------------------- launchers
 inline dim3 step_grid(const Geo& g) { return dim3((g.nx + LBM_BX - 1) / LBM_BX, g.ny, g.nz); }
 
-// forced steps (FP32 / FP64 storage, deviation arithmetic): the general
-// (non-regularised) instantiation, which is the same method for unit rates
-template <int ST, class S, class T, int SPACE>
+// forced steps (FP32 / FP64 storage, deviation arithmetic)
+template <int ST, class S, class T, int SPACE, bool REG>
 void launch_forced(const StepArgs& a, const Rates<T>& keep, const dim3& grid) {
   ForceArg<T> fa;
   for (int d = 0; d < 3; ++d) fa.F[d] = T(a.force[d]);
@@ -586,9 +585,9 @@ void launch_forced(const StepArgs& a, const Rates<T>& keep, const dim3& grid) {
         P.src[i] = i < q_of(ST) ? (const S*)a.src + (int64_t(i) * a.g.N + delta) : nullptr;
         P.dst[i] = i < q_of(ST) ? (S*)a.dst + int64_t(i) * a.g.N : nullptr;
       }
-      k_pull<ST, S, T, SPACE, false, FORM_DEV, FC><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep, fa);
+      k_pull<ST, S, T, SPACE, REG, FORM_DEV, FC><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep, fa);
     } else {
-      launch_inplace<ST, S, T, SPACE, false, FC>(a, keep, grid, fa);
+      launch_inplace<ST, S, T, SPACE, REG, FC>(a, keep, grid, fa);
     }
   };
   const bool field = a.force_mode == FORCE_FIELD;
@@ -606,9 +605,12 @@ void launch_step_typed(const StepArgs& a) {
   Rates<T> keep;
   for (int k = 0; k < 6; ++k) keep.om[k] = T(1.0 - a.rates[k]);
   const dim3 grid = step_grid(a.g);
-  if constexpr ((std::is_same<S, float>::value || std::is_same<S, double>::value) && !REG) {
+  // forced steps: FP32 / FP64 storage; raw-moment spaces run the general
+  // instance (the context clears REG for them), the others keep REG
+  if constexpr ((std::is_same<S, float>::value || std::is_same<S, double>::value) &&
+                !(REG && (SPACE == SP_RAW || SPACE == SP_RAW_W))) {
     if (a.force_mode != FORCE_NONE) {
-      launch_forced<ST, S, T, SPACE>(a, keep, grid);
+      launch_forced<ST, S, T, SPACE, REG>(a, keep, grid);
       return;
     }
   }
