@@ -205,6 +205,8 @@ int lbm_batch_create(lbm_batch** out, const lbm_params* p, int n, const int64_t*
     I.N = int(nx * ny * nz);
     I.off = off;
     I.keep_shear = 1.0 - om;
+    I.rnx = 1.0f / float(nx);
+    I.rny = 1.0f / float(ny);
     b->shear[k] = om;
     off += int64_t(b->q) * I.N;
     b->cells += I.N;

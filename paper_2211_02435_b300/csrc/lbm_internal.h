@@ -95,6 +95,7 @@ struct BInst {
   int nx, ny, nz, N;  // box of the instance, N = nx * ny * nz
   int64_t off;        // element offset of its population block
   double keep_shear;  // 1 - shear rate of the instance
+  float rnx, rny;     // 1 / nx, 1 / ny (cell index -> x, y, z without division)
 };
 enum { BATCH_STEP = 0, BATCH_TGV = 1 };
 struct BatchArgs {

@@ -497,13 +497,29 @@ LBM_D void cell_xyz(int c, const Geo& g, int& x, int& y, int& z) {
   y = yz - z * g.ny;
 }
 
+// q = a / d and a - q d for 0 <= a < 2^24 and d >= 1, from the float
+// reciprocal rd = fl(1/d): a is exact in FP32 and the rounded product is
+// within (a/d) 2^-23 < 1 of a/d, so one correction step gives the quotient
+LBM_D int fast_divmod(int a, int d, float rd, int& r) {
+  int q = int(float(a) * rd);
+  r = a - q * d;
+  if (r < 0) r += d, --q;
+  else if (r >= d) r -= d, ++q;
+  return q;
+}
+
 template <int ST, class S, class T, int SPACE, bool REG>
 __global__ void __launch_bounds__(BATCH_MAX_THREADS)
     k_batch_pull(const S* __restrict__ src, S* __restrict__ dst, const BInst* __restrict__ inst,
                  const int2* __restrict__ tiles, int ntiles, int cpt, Rates<T> keep) {
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int2 tl = tiles[t];
-    const BInst I = inst[tl.x];
+  // the next tile's descriptors are loaded while the current one runs
+  int t = blockIdx.x;
+  int2 tl = t < ntiles ? tiles[t] : make_int2(0, 0);
+  BInst I = inst[t < ntiles ? tl.x : 0];
+  for (; t < ntiles; t += gridDim.x) {
+    const int tn = t + gridDim.x;
+    const int2 tln = tn < ntiles ? tiles[tn] : tl;
+    const BInst In = inst[tln.x];
     const Geo g{I.nx, I.ny, I.nz, (int64_t)I.N};
     Rates<T> k = keep;
     k.om[0] = T(I.keep_shear);
@@ -513,7 +529,12 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS)
       const int c = tl.y + j * (int)blockDim.x + (int)threadIdx.x;
       if (c >= I.N) break;
       int x, y, z;
-      cell_xyz(c, g, x, y, z);
+      if (I.N < (1 << 24)) {  // float quotient within one of the true one
+        const int yz = fast_divmod(c, I.nx, I.rnx, x);
+        z = fast_divmod(yz, I.ny, I.rny, y);
+      } else {
+        cell_xyz(c, g, x, y, z);
+      }
       const Nbr n = neighbours(x, y, z, g);
       T f[q_of(ST)];
       load_pops<ST, S, T, G_PULL>(s, g, n, c, f);
@@ -523,6 +544,8 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS)
         d[(int64_t)i * g.N + c] = enc_pop<ST, i, S, T>(f[i]);
       });
     }
+    tl = tln;
+    I = In;
   }
 }
 
