@@ -4,14 +4,16 @@
  * Code Generation for Multiple Relaxation-Time Lattice Boltzmann Methods"
  * (arXiv 2211.02435).
  *
- * One call of lbm_step advances every cell by the fused pull-stream +
- * collide update of Eq. 2.1: gather the populations (Eq. 2.1b, pull or
- * in-place AA pattern, Sec. 4.3), collide (Eq. 2.4-2.6) in raw-moment,
- * central-moment or cumulant space (Sec. 2.3) using the raw-moment Chimera
- * (Eq. 4.1), the binomial raw<->central Chimera (Eq. 4.3-4.4), the
- * central<->cumulant relations (Eq. 4.5) and the split backward transform
- * (Eq. 4.2), and store.  Populations are stored zero-centered,
- * df_i = f_i - w_i (Sec. 2.1).
+ * One call of lbm_step advances every cell by the fused stream + collide
+ * update of Eq. 2.1: gather the populations (Eq. 2.1b: pull, or the in-place
+ * AA or Esoteric Twist patterns, Sec. 4.3), collide (Eq. 2.4-2.6) in
+ * population (SRT, TRT), raw-moment (O-MRT, WO-MRT), central-moment or
+ * cumulant space (Sec. 2.3) using the raw-moment Chimera (Eq. 4.1), the
+ * binomial raw<->central Chimera (Eq. 4.3-4.4), the central<->cumulant
+ * relations (Eq. 4.5) and the split backward transform (Eq. 4.2), with an
+ * optional body force (Eq. 2.1a source term, Guo or He), and store.
+ * Populations are stored zero-centered, df_i = f_i - w_i (Sec. 2.1), or
+ * absolute for the round-off studies and the shallow-water methods.
  *
  * Conventions shared by every call
  *  - Return value: LBM_OK (0) or a negative LBM_ERR_* code.  No C++
