@@ -157,6 +157,17 @@ def oracle_sample(n_cells_edge, steps, nthreads=0):
     return n_cells_edge ** 3 * steps / dt / 1e6, dt
 
 
+def main_config(args, cells, world):
+    """The workload the cuda arm times (and the reference arm samples)."""
+    key = {"f32": "f32", "f16": "f16_delta", "bf16": "bf16_delta"}[args.storage]
+    return {"workload": f"D3Q27 cumulant LBM (R-: shear from nu=1e-3, bulk and orders 3-6 "
+                        f"rate 1), periodic {args.size}^3 Taylor-Green u0=0.05 + uniform 1e-3 "
+                        f"noise, {key} zero-centered storage, {args.streaming}"
+                        + ("" if args.force == "none" else f", {args.force} body force"),
+            "cells": cells, "global_batch": world, "parallelism": "replicas",
+            "l2": "working set 29 GB >> 126 MB L2, no flush needed"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -177,8 +188,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"D3Q27 cumulant R- nu=1e-3, TGV u0=0.05 + 1e-3 noise, "
-                                   f"{edge}^3 sample", "parallelism": "replicas"},
+            "config": main_config(args, args.size ** 3, args.gpus),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -460,13 +470,7 @@ def run_cuda(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.storage == "f32" else f"f32 compute, {args.storage} storage",
             "data": "synthetic",
-            "config": {"workload": "D3Q27 cumulant LBM (R-: shear from nu=1e-3, bulk and "
-                                   "orders 3-6 rate 1), periodic 512^3 Taylor-Green u0=0.05 "
-                                   f"+ uniform 1e-3 noise, {main_key} zero-centered storage, "
-                                   f"{args.streaming}"
-                                   + ("" if args.force == "none" else f", {args.force} body force"),
-                       "cells": N, "global_batch": world, "parallelism": "replicas",
-                       "l2": "working set 29 GB >> 126 MB L2, no flush needed"},
+            "config": main_config(args, N, world),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
