@@ -336,7 +336,7 @@ def run_cuda(args):
     # ---- headline: FP32 storage (or --storage), kernel-only, inputs in HBM
     main_store = {"f32": L.STORE_F32, "f16": L.STORE_F16_DELTA, "bf16": L.STORE_BF16_DELTA}[args.storage]
     main_key = {"f32": "f32", "f16": "f16_delta", "bf16": "bf16_delta"}[args.storage]
-    main_stream = {"pull": L.PULL, "aa": L.AA, "et": L.ESOTERIC_TWIST}[args.streaming]
+    main_stream = STREAMINGS[args.streaming]
     main_force = None
     if args.force == "uniform":
         main_force = np.array([1e-6, 0.0, 0.0])
@@ -475,8 +475,8 @@ def run_cuda(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
                          "bytes_per_cell": main_bpc,
-                         "kernel": (f"{ {'pull': 'k_pull', 'aa': 'k_aa', 'et': 'k_et'}[args.streaming]}"
-                                    f"<D3Q27, {main_key} storage, cumulant, "
+                         "kernel": (("k_pull" if args.streaming == "pull" else "k_inplace")
+                                    + f"<D3Q27, {args.streaming}, {main_key} storage, cumulant, "
                                     + ("regularised>" if args.force == "none"
                                        else f"{args.force} force>")),
                          "step_kernel": args.step_kernel},
@@ -492,6 +492,8 @@ def run_cuda(args):
 
 
 STEP_KERNELS = {"auto": 0, "direct": 1, "staged": 2}  # LBM_STEP_* of include/lbm.h
+# lbm_streaming of include/lbm.h: pull, AA, Esoteric Twist / Pull / Push
+STREAMINGS = {"pull": 0, "aa": 1, "et": 2, "epull": 3, "epush": 4}
 
 
 def main():
@@ -514,7 +516,7 @@ def main():
     ap.add_argument("--batch-n", type=int, default=4096)
     ap.add_argument("--step-kernel", choices=list(STEP_KERNELS), default="auto",
                     help="pull step kernel of the D3Q27 forms (include/lbm.h)")
-    ap.add_argument("--streaming", choices=["pull", "aa", "et"], default="pull",
+    ap.add_argument("--streaming", choices=list(STREAMINGS), default="pull",
                     help="streaming pattern of the headline run")
     ap.add_argument("--force", choices=["none", "uniform", "field"], default="none",
                     help="body force (Guo) of the headline run")

@@ -6,12 +6,13 @@
  *
  * One call of lbm_step advances every cell by the fused stream + collide
  * update of Eq. 2.1: gather the populations (Eq. 2.1b: pull, or the in-place
- * AA or Esoteric Twist patterns, Sec. 4.3), collide (Eq. 2.4-2.6) in
- * population (SRT, TRT), raw-moment (O-MRT, WO-MRT), central-moment or
- * cumulant space (Sec. 2.3) using the raw-moment Chimera (Eq. 4.1), the
- * binomial raw<->central Chimera (Eq. 4.3-4.4), the central<->cumulant
- * relations (Eq. 4.5) and the split backward transform (Eq. 4.2), with an
- * optional body force (Eq. 2.1a source term, Guo or He), and store.
+ * AA, Esoteric Twist, Esoteric Pull or Esoteric Push patterns, Sec. 4.3),
+ * collide (Eq. 2.4-2.6) in population (SRT, TRT), raw-moment (O-MRT,
+ * WO-MRT), central-moment or cumulant space (Sec. 2.3) using the raw-moment
+ * Chimera (Eq. 4.1), the binomial raw<->central Chimera (Eq. 4.3-4.4), the
+ * central<->cumulant relations (Eq. 4.5) and the split backward transform
+ * (Eq. 4.2), with an optional body force (Eq. 2.1a source term, Guo or He),
+ * and store.
  * Populations are stored zero-centered, df_i = f_i - w_i (Sec. 2.1), or
  * absolute for the round-off studies and the shallow-water methods.
  *
@@ -132,11 +133,25 @@ typedef enum { LBM_ARITH_DEVIATION = 0, LBM_ARITH_AS_WRITTEN = 1 } lbm_arithmeti
 
 /* Streaming pattern (Sec. 4.3): pull with two buffers, or one of the
  * in-place patterns with one buffer: AA (even steps local, odd steps across
- * all neighbours) or Esoteric Twist (every step reads and writes the cell
- * and its positive neighbours: population i of cell x lives at node
- * x + max(-xi_i, 0), slot i at even and slot ibar at odd times).  All give
- * identical states f(n); lbm_get_time reports the in-place parity. */
-typedef enum { LBM_PULL = 0, LBM_AA = 1, LBM_ESOTERIC_TWIST = 2 } lbm_streaming;
+ * all neighbours) or one of the esoteric patterns, in which every opposite
+ * pair (p, pbar), p the member whose first nonzero component is +1 (odd
+ * index), occupies the two elements (x + a_p, slot p) and
+ * (x + a_p + xi_p, slot pbar) of cell x at even times and the same elements
+ * with the slots swapped at odd times:
+ *   Esoteric Twist: a_p = max(-xi_p, 0) per component (the cell and its
+ *                   positive neighbours);
+ *   Esoteric Pull:  a_p = 0 (p at the own node, pbar at x - xi_pbar);
+ *   Esoteric Push:  a_p = -xi_p (pbar at the own node, p at x - xi_p).
+ * Each step a cell reads and overwrites exactly its own elements.  All
+ * patterns give identical states f(n); lbm_get_time reports the in-place
+ * parity. */
+typedef enum {
+  LBM_PULL = 0,
+  LBM_AA = 1,
+  LBM_ESOTERIC_TWIST = 2,
+  LBM_ESOTERIC_PULL = 3,
+  LBM_ESOTERIC_PUSH = 4
+} lbm_streaming;
 
 #define LBM_PERIODIC 0 /* the only boundary; others -> LBM_ERR_UNSUPPORTED */
 

@@ -70,7 +70,8 @@ int lbm_trainer_create(lbm_trainer** out, const int64_t coarse_dims[3],
                        int max_snapshots, void* stream);
 
 /* Append a snapshot: the 4^3 block average of the canonical populations of
- * a D3Q27 context whose dims are 4 x coarse_dims (any storage, pull or AA). */
+ * a D3Q27 context whose dims are 4 x coarse_dims (any zero-centered
+ * storage, pull or AA streaming; the esoteric patterns -> UNSUPPORTED). */
 int lbm_trainer_add_restricted(lbm_trainer* t, lbm_ctx* fine);
 
 /* Append a snapshot given as canonical FP64 populations df[27 * N]. */

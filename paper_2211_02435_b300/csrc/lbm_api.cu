@@ -34,7 +34,20 @@ const aux_fn kAux[3][5] = {
     {lbm::launch_aux_2_0, lbm::launch_aux_2_1, lbm::launch_aux_2_2, lbm::launch_aux_2_3,
      lbm::launch_aux_2_4}};
 
-constexpr int G_PULL = 0, G_LOCAL = 1, G_AAODD = 2, G_ET_EVEN = 3, G_ET_ODD = 4;
+constexpr int G_PULL = 0, G_LOCAL = 1, G_AAODD = 2;
+// esoteric pattern k (Twist 0, Pull 1, Push 2) at parity p: 3 + 2 k + p,
+// equal to the step modes MODE_ET_EVEN .. MODE_EPUSH_ODD
+constexpr int G_ESO_BASE = 3;
+static_assert(lbm::MODE_ET_EVEN == G_ESO_BASE && lbm::MODE_EPULL_EVEN == G_ESO_BASE + 2 &&
+                  lbm::MODE_EPUSH_ODD == G_ESO_BASE + 5,
+              "esoteric gather and step modes share their numbering");
+bool esoteric(int streaming) {
+  return streaming == LBM_ESOTERIC_TWIST || streaming == LBM_ESOTERIC_PULL ||
+         streaming == LBM_ESOTERIC_PUSH;
+}
+int eso_mode(int streaming, int parity) {
+  return G_ESO_BASE + 2 * (streaming - LBM_ESOTERIC_TWIST) + parity;
+}
 constexpr uint64_t kStateMagic = 0x4c424d3253544154ull;  // "LBM2STAT"
 
 int q_of(int st) { return st == LBM_D2Q9 ? 9 : (st == LBM_D3Q19 ? 19 : 27); }
@@ -62,7 +75,7 @@ int cuda_err(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
 
 int gather_mode(const lbm_ctx* c) {
   if (c->p.streaming == LBM_PULL) return G_PULL;
-  if (c->p.streaming == LBM_ESOTERIC_TWIST) return c->parity ? G_ET_ODD : G_ET_EVEN;
+  if (esoteric(c->p.streaming)) return eso_mode(c->p.streaming, c->parity);
   return c->parity ? G_AAODD : G_LOCAL;
 }
 void* state_buf(const lbm_ctx* c) {
@@ -179,7 +192,7 @@ int lbm_create(lbm_ctx** out, const lbm_params* p) {
   if (!out || !p) return LBM_ERR_INVALID;
   *out = nullptr;
   if (p->stencil < 0 || p->stencil > 2 || p->space < 0 || p->space > 5 || p->storage < 0 ||
-      p->storage > 4 || p->streaming < 0 || p->streaming > 2 ||
+      p->storage > 4 || p->streaming < 0 || p->streaming > 4 ||
       (p->equilibrium != LBM_EQ_DELTA && p->equilibrium != LBM_EQ_ABSOLUTE) ||
       (p->arithmetic != LBM_ARITH_DEVIATION && p->arithmetic != LBM_ARITH_AS_WRITTEN))
     return LBM_ERR_INVALID;
@@ -389,7 +402,7 @@ static int scatter(lbm_ctx* c, const double* df, const double* rho, const double
   AuxArgs a = aux_base(c, lbm::AUX_SCATTER);
   a.gather_mode = c->p.streaming == LBM_PULL
                       ? G_PULL
-                      : (c->p.streaming == LBM_ESOTERIC_TWIST ? G_ET_EVEN : G_LOCAL);
+                      : (esoteric(c->p.streaming) ? eso_mode(c->p.streaming, 0) : G_LOCAL);
   a.df_in = df;
   a.rho_in = rho;
   a.u_in = u;
@@ -496,8 +509,8 @@ int lbm_step(lbm_ctx* c, int64_t n) {
         fn(a);
       c->cur = 1 - c->cur;
     } else {
-      if (c->p.streaming == LBM_ESOTERIC_TWIST)
-        a.mode = c->parity ? lbm::MODE_ET_ODD : lbm::MODE_ET_EVEN;
+      if (esoteric(c->p.streaming))
+        a.mode = eso_mode(c->p.streaming, c->parity);
       else
         a.mode = c->parity ? lbm::MODE_AA_ODD : lbm::MODE_AA_EVEN;
       a.src = c->buf[0];

@@ -1034,7 +1034,7 @@ int lbm_trainer_add_restricted(lbm_trainer* t, lbm_ctx* fine) {
   if (fine->p.stencil != LBM_D3Q27 || fine->g.nx != 4 * t->g.nx || fine->g.ny != 4 * t->g.ny ||
       fine->g.nz != 4 * t->g.nz || fine->p.storage > LBM_STORE_BF16_DELTA)
     return LBM_ERR_INVALID;
-  if (fine->p.streaming == LBM_ESOTERIC_TWIST) return LBM_ERR_UNSUPPORTED;
+  if (fine->p.streaming != LBM_PULL && fine->p.streaming != LBM_AA) return LBM_ERR_UNSUPPORTED;
   const int mode = fine->p.streaming == LBM_PULL ? lbm::G_PULL
                                                  : (fine->parity ? lbm::G_AAODD : lbm::G_LOCAL);
   const void* buf = fine->p.streaming == LBM_PULL ? fine->buf[fine->cur] : fine->buf[0];

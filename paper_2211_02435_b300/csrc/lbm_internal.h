@@ -16,7 +16,10 @@ struct Geo {
 };
 
 enum { STORE_F64 = 0, STORE_F32 = 1, STORE_F16 = 2, STORE_BF16 = 3, STORE_F64_ABS = 4 };
-enum { MODE_PULL = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2, MODE_ET_EVEN = 3, MODE_ET_ODD = 4 };
+enum {
+  MODE_PULL = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2, MODE_ET_EVEN = 3, MODE_ET_ODD = 4,
+  MODE_EPULL_EVEN = 5, MODE_EPULL_ODD = 6, MODE_EPUSH_EVEN = 7, MODE_EPUSH_ODD = 8
+};
 enum { VARIANT_DIRECT = 0, VARIANT_STAGED = 1 };
 enum { FORCE_NONE = 0, FORCE_UNIFORM = 1, FORCE_FIELD = 2, FORCE_UNIFORM_HE = 3, FORCE_FIELD_HE = 4 };
 
@@ -65,7 +68,7 @@ struct AuxArgs {
   Geo g;
   int storage;
   int space;
-  int gather_mode;  // G_* of lbm_kernels.cuh (scatter: G_PULL, G_LOCAL or G_ET_EVEN)
+  int gather_mode;  // G_* of lbm_kernels.cuh (scatter: G_PULL, G_LOCAL or an even esoteric layout)
   double* df;       // gather outputs (nullable)
   double* rho;
   double* u;

@@ -32,15 +32,56 @@ namespace lbm {
 #define LBM_PULL2_BOUNDS __launch_bounds__(LBM_BX)
 #endif
 
-// how a kernel reads the canonical populations f(n) of a cell
-enum { G_PULL = 0, G_LOCAL = 1, G_AAODD = 2, G_ET_EVEN = 3, G_ET_ODD = 4 };
+// how a kernel reads the canonical populations f(n) of a cell; the in-place
+// family below takes an even and an odd value per pattern (3 + 2 k + parity)
+enum {
+  G_PULL = 0, G_LOCAL = 1, G_AAODD = 2, G_ET_EVEN = 3, G_ET_ODD = 4,
+  G_EPULL_EVEN = 5, G_EPULL_ODD = 6, G_EPUSH_EVEN = 7, G_EPUSH_ODD = 8
+};
 
-// Esoteric Twist offset of direction i: a_i = max(-xi_i, 0) per component.
-// Population i of cell x lives at node x + a_i (slot i at even times, slot
-// ibar at odd times), so a cell touches itself and its positive neighbours.
-template <int ST, int i, int d>
-LBM_HD constexpr int et_off() {
-  return vel(ST, i, d) < 0 ? 1 : 0;
+// The esoteric in-place family (Sec. 4.3).  Every opposite pair (p, pbar),
+// p the member whose first nonzero component is +1 (odd index), owns the two
+// elements (x + a_p, slot p) and (x + a_p + xi_p, slot pbar) of cell x:
+//   Esoteric Twist a_p = max(-xi_p, 0) per component (positive neighbours),
+//   Esoteric Pull  a_p = 0  (p local, pbar pulled from x - xi_pbar),
+//   Esoteric Push  a_p = -xi_p (pbar local, p pulled from x - xi_p).
+// Population i of cell x is held at node x + r_i (slot i at even times, slot
+// ibar at odd times); f*_i goes to node x + w_i, slot ibar at even steps and
+// slot i at odd ones, which is where population i of cell x + xi_i is read
+// at the next time.  A cell writes exactly the elements it read, so the
+// update is race-free in place.
+enum { IP_ET = 0, IP_EPULL = 1, IP_EPUSH = 2 };
+LBM_HD constexpr int ip_kind(int mode) { return (mode - 3) / 2; }
+LBM_HD constexpr bool ip_odd(int mode) { return mode >= 3 && ((mode - 3) & 1); }
+LBM_HD constexpr int ip_alpha(int kind, int xi) {
+  return kind == IP_ET ? (xi < 0 ? 1 : 0) : (kind == IP_EPULL ? 0 : -xi);
+}
+// component d of the read offset r_i and the write offset w_i
+template <int ST, int KIND, int i, int d>
+LBM_HD constexpr int ip_read_off() {
+  constexpr int xi = vel(ST, i, d);
+  return i == 0 ? 0 : ((i & 1) ? ip_alpha(KIND, xi) : ip_alpha(KIND, -xi) - xi);
+}
+template <int ST, int KIND, int i, int d>
+LBM_HD constexpr int ip_write_off() {
+  constexpr int xi = vel(ST, i, d);
+  return i == 0 ? 0 : ((i & 1) ? ip_alpha(KIND, xi) + xi : ip_alpha(KIND, -xi));
+}
+
+// runtime gather mode -> compile-time constant for go(integral_constant)
+template <class F>
+void with_gather_mode(int gm, F&& go) {
+  switch (gm) {
+    case G_PULL: go(std::integral_constant<int, G_PULL>{}); break;
+    case G_LOCAL: go(std::integral_constant<int, G_LOCAL>{}); break;
+    case G_AAODD: go(std::integral_constant<int, G_AAODD>{}); break;
+    case G_ET_EVEN: go(std::integral_constant<int, G_ET_EVEN>{}); break;
+    case G_ET_ODD: go(std::integral_constant<int, G_ET_ODD>{}); break;
+    case G_EPULL_EVEN: go(std::integral_constant<int, G_EPULL_EVEN>{}); break;
+    case G_EPULL_ODD: go(std::integral_constant<int, G_EPULL_ODD>{}); break;
+    case G_EPUSH_EVEN: go(std::integral_constant<int, G_EPUSH_EVEN>{}); break;
+    default: go(std::integral_constant<int, G_EPUSH_ODD>{}); break;
+  }
 }
 
 // absolute FP64 storage element (LBM_STORE_F64_ABSOLUTE): holds f_i itself
@@ -108,6 +149,7 @@ LBM_D int cell_at(const Nbr& n, const Geo& g, int ox, int oy, int oz) {
 //   G_PULL : f_i(x) = buf[i][x - xi_i]       (pull buffer after a step)
 //   G_LOCAL: f_i(x) = buf[i][x]              (AA, even parity)
 //   G_AAODD: f_i(x) = buf[ibar][x - xi_i]    (AA, odd parity)
+//   esoteric: f_i(x) = buf[i or ibar][x + r_i]  (even / odd parity)
 template <int ST, class S, class T, int MODE>
 LBM_D void load_pops(const S* buf, const Geo& g, const Nbr& n, int c, T (&f)[q_of(ST)]) {
   sfor<q_of(ST)>([&](auto I) {
@@ -116,9 +158,12 @@ LBM_D void load_pops(const S* buf, const Geo& g, const Nbr& n, int c, T (&f)[q_o
     int src_c = c;
     int slot = i;
     if constexpr (MODE == G_PULL || MODE == G_AAODD) src_c = cell_at(n, g, -cx, -cy, -cz);
-    if constexpr (MODE == G_ET_EVEN || MODE == G_ET_ODD)
-      src_c = cell_at(n, g, et_off<ST, i, 0>(), et_off<ST, i, 1>(), et_off<ST, i, 2>());
-    if constexpr (MODE == G_AAODD || MODE == G_ET_ODD) slot = opp(i);
+    if constexpr (MODE >= G_ET_EVEN) {
+      constexpr int K = ip_kind(MODE);
+      src_c = cell_at(n, g, ip_read_off<ST, K, i, 0>(), ip_read_off<ST, K, i, 1>(),
+                      ip_read_off<ST, K, i, 2>());
+    }
+    if constexpr (MODE == G_AAODD || ip_odd(MODE)) slot = opp(i);
     const S v = buf[(int64_t)slot * g.N + src_c];
     f[i] = dec_pop<ST, i, S, T>(v);
   });
@@ -258,19 +303,18 @@ __global__ void LBM_PULL2_BOUNDS k_pull2(const __grid_constant__ PullPtrs<S> P, 
   });
 }
 
-// In-place streaming on one buffer (Sec. 4.3), both patterns through one
+// In-place streaming on one buffer (Sec. 4.3), every pattern through one
 // kernel with per-direction plane pointers (as the pull kernel): population
 // i is read from slot rd_i at node x + r_i and f*_i written to slot wr_i at
 // node x + w_i, with the offsets r_i, w_i in {-1, 0, 1}^3 baked into the
 // pointers and a wrap correction only on the periodic boundary.
 //   AA, even: r = w = 0, read slot i, write slot ibar (the own cell).
 //   AA, odd:  r = -xi_i, read slot ibar; w = +xi_i, write slot i.
-//   Esoteric Twist: with a_i = max(-xi_i, 0) per component, r = a_i and
-//     w = a_ibar; even steps read slot i and write slot ibar, odd steps read
-//     slot ibar and write slot i.  The cell writes exactly the elements it
-//     read (node x + a_ibar, slot ibar is where it read population ibar), so
-//     no two cells touch one element; at the next time f*_i sits at
-//     (x + xi_i) + a_i, the same rule with the slots swapped.
+//   Esoteric Twist / Pull / Push: r_i, w_i of the esoteric family above;
+//     even steps read slot i and write slot ibar, odd steps read slot ibar
+//     and write slot i.  For the Twist r_i = max(-xi_i, 0) and
+//     w_i = max(xi_i, 0) per component: a cell touches itself and its
+//     positive neighbours only.
 // Each cell reads and writes the same set of elements in every variant.
 template <class S>
 struct InPlacePtrs {
@@ -283,14 +327,16 @@ template <int ST, int MODE, int i>
 struct InPlaceMap {
   static constexpr int b = opp(i);
   static constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1), cz = vel(ST, i, 2);
-  static constexpr bool ET = MODE == MODE_ET_EVEN || MODE == MODE_ET_ODD;
-  static constexpr bool ODD = MODE == MODE_AA_ODD || MODE == MODE_ET_ODD;
-  static constexpr int rx = ET ? (cx < 0 ? 1 : 0) : (MODE == MODE_AA_ODD ? -cx : 0);
-  static constexpr int ry = ET ? (cy < 0 ? 1 : 0) : (MODE == MODE_AA_ODD ? -cy : 0);
-  static constexpr int rz = ET ? (cz < 0 ? 1 : 0) : (MODE == MODE_AA_ODD ? -cz : 0);
-  static constexpr int wx = ET ? (cx > 0 ? 1 : 0) : (MODE == MODE_AA_ODD ? cx : 0);
-  static constexpr int wy = ET ? (cy > 0 ? 1 : 0) : (MODE == MODE_AA_ODD ? cy : 0);
-  static constexpr int wz = ET ? (cz > 0 ? 1 : 0) : (MODE == MODE_AA_ODD ? cz : 0);
+  static constexpr bool ESO = MODE >= MODE_ET_EVEN;
+  static constexpr int K = ESO ? ip_kind(MODE) : 0;
+  static constexpr bool ODD = MODE == MODE_AA_ODD || ip_odd(MODE);
+  static constexpr int aa = MODE == MODE_AA_ODD ? 1 : 0;
+  static constexpr int rx = ESO ? ip_read_off<ST, K, i, 0>() : -aa * cx;
+  static constexpr int ry = ESO ? ip_read_off<ST, K, i, 1>() : -aa * cy;
+  static constexpr int rz = ESO ? ip_read_off<ST, K, i, 2>() : -aa * cz;
+  static constexpr int wx = ESO ? ip_write_off<ST, K, i, 0>() : aa * cx;
+  static constexpr int wy = ESO ? ip_write_off<ST, K, i, 1>() : aa * cy;
+  static constexpr int wz = ESO ? ip_write_off<ST, K, i, 2>() : aa * cz;
   static constexpr int rslot = ODD ? b : i;
   static constexpr int wslot = ODD ? i : b;
 };
@@ -359,7 +405,11 @@ void launch_inplace(const StepArgs& a, const Rates<T>& keep, const dim3& grid,
     case MODE_AA_EVEN: go(std::integral_constant<int, MODE_AA_EVEN>{}); break;
     case MODE_AA_ODD: go(std::integral_constant<int, MODE_AA_ODD>{}); break;
     case MODE_ET_EVEN: go(std::integral_constant<int, MODE_ET_EVEN>{}); break;
-    default: go(std::integral_constant<int, MODE_ET_ODD>{}); break;
+    case MODE_ET_ODD: go(std::integral_constant<int, MODE_ET_ODD>{}); break;
+    case MODE_EPULL_EVEN: go(std::integral_constant<int, MODE_EPULL_EVEN>{}); break;
+    case MODE_EPULL_ODD: go(std::integral_constant<int, MODE_EPULL_ODD>{}); break;
+    case MODE_EPUSH_EVEN: go(std::integral_constant<int, MODE_EPUSH_EVEN>{}); break;
+    default: go(std::integral_constant<int, MODE_EPUSH_ODD>{}); break;
   }
 }
 
@@ -426,8 +476,11 @@ __global__ void __launch_bounds__(LBM_BX) k_scatter(S* buf, Geo g, const double*
     constexpr int i = CI(I);
     int dc = c;
     if constexpr (LAYOUT == G_PULL) dc = cell_at(n, g, -vel(ST, i, 0), -vel(ST, i, 1), -vel(ST, i, 2));
-    if constexpr (LAYOUT == G_ET_EVEN)
-      dc = cell_at(n, g, et_off<ST, i, 0>(), et_off<ST, i, 1>(), et_off<ST, i, 2>());
+    if constexpr (LAYOUT >= G_ET_EVEN) {
+      constexpr int K = ip_kind(LAYOUT);
+      dc = cell_at(n, g, ip_read_off<ST, K, i, 0>(), ip_read_off<ST, K, i, 1>(),
+                   ip_read_off<ST, K, i, 2>());
+    }
     buf[(int64_t)i * g.N + dc] = enc_pop<ST, i, S, T>(f[i]);
   });
 }
@@ -711,16 +764,10 @@ void launch_aux_typed(const AuxArgs& a) {
       ForceArg<T> fa;
       for (int d = 0; d < 3; ++d) fa.F[d] = T(a.force_mode != FORCE_NONE ? a.force[d] : 0.0);
       fa.field = a.force_mode == FORCE_FIELD ? (const T*)a.force_field : nullptr;
-      if (gm == G_PULL)
-        k_gather<ST, S, T, G_PULL><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
-      else if (gm == G_LOCAL)
-        k_gather<ST, S, T, G_LOCAL><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
-      else if (gm == G_AAODD)
-        k_gather<ST, S, T, G_AAODD><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
-      else if (gm == G_ET_EVEN)
-        k_gather<ST, S, T, G_ET_EVEN><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
-      else
-        k_gather<ST, S, T, G_ET_ODD><<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
+      with_gather_mode(gm, [&](auto mode) {
+        k_gather<ST, S, T, decltype(mode)::value>
+            <<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
+      });
       break;
     }
     case AUX_SCATTER: {
@@ -742,22 +789,20 @@ void launch_aux_typed(const AuxArgs& a) {
         else
           k_scatter<ST, S, T, SP_CENTRAL, LY><<<grid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in);
       };
-      if (gm == G_PULL) go(std::integral_constant<int, G_PULL>{});
-      else if (gm == G_ET_EVEN) go(std::integral_constant<int, G_ET_EVEN>{});
-      else go(std::integral_constant<int, G_LOCAL>{});
+      switch (gm) {  // scatter writes the even-parity layout of each pattern
+        case G_PULL: go(std::integral_constant<int, G_PULL>{}); break;
+        case G_ET_EVEN: go(std::integral_constant<int, G_ET_EVEN>{}); break;
+        case G_EPULL_EVEN: go(std::integral_constant<int, G_EPULL_EVEN>{}); break;
+        case G_EPUSH_EVEN: go(std::integral_constant<int, G_EPUSH_EVEN>{}); break;
+        default: go(std::integral_constant<int, G_LOCAL>{}); break;
+      }
       break;
     }
     case AUX_INVARIANTS:
-      if (gm == G_PULL)
-        k_invariants<ST, S, T, G_PULL><<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
-      else if (gm == G_LOCAL)
-        k_invariants<ST, S, T, G_LOCAL><<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
-      else if (gm == G_AAODD)
-        k_invariants<ST, S, T, G_AAODD><<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
-      else if (gm == G_ET_EVEN)
-        k_invariants<ST, S, T, G_ET_EVEN><<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
-      else
-        k_invariants<ST, S, T, G_ET_ODD><<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
+      with_gather_mode(gm, [&](auto mode) {
+        k_invariants<ST, S, T, decltype(mode)::value>
+            <<<a.nparts, INV_THREADS, 0, a.stream>>>((const S*)a.buf, a.g, a.part);
+      });
       break;
   }
 }

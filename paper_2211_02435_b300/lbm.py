@@ -24,7 +24,8 @@ STORE_F64, STORE_F32, STORE_F16_DELTA, STORE_BF16_DELTA, STORE_F64_ABSOLUTE = 0,
 ARITH_DEVIATION, ARITH_AS_WRITTEN = 0, 1
 STEP_AUTO, STEP_DIRECT, STEP_STAGED = 0, 1, 2
 FORCE_GUO, FORCE_HE = 0, 1
-PULL, AA, ESOTERIC_TWIST = 0, 1, 2
+PULL, AA, ESOTERIC_TWIST, ESOTERIC_PULL, ESOTERIC_PUSH = 0, 1, 2, 3, 4
+STREAMING_PATTERNS = (PULL, AA, ESOTERIC_TWIST, ESOTERIC_PULL, ESOTERIC_PUSH)
 PERIODIC = 0
 Q_OF = {D2Q9: 9, D3Q19: 19, D3Q27: 27}
 ELEM_BYTES = {STORE_F64: 8, STORE_F32: 4, STORE_F16_DELTA: 2, STORE_BF16_DELTA: 2,

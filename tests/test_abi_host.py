@@ -50,7 +50,7 @@ def _params(**kw):
     (dict(stencil=3), -1),
     (dict(space=7), -1),
     (dict(storage=9), -1),
-    (dict(streaming=3), -1),
+    (dict(streaming=5), -1),
     (dict(equilibrium=5), -1),
     (dict(dims=(0, 4, 4)), -1),
     (dict(dims=(4, 70000, 4)), -1),

@@ -155,6 +155,17 @@ def test_restriction_is_the_block_average(streaming, storage):
     assert np.abs(snap - ref).max() <= 1e-6 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("streaming", [L.ESOTERIC_TWIST, L.ESOTERIC_PULL, L.ESOTERIC_PUSH])
+def test_restriction_refuses_esoteric_layouts(streaming):
+    coarse = (2, 2, 2)
+    with L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F32, streaming,
+                   [OMEGA_S] + [1.0] * 5, tuple(4 * v for v in coarse)) as lat, \
+            L.Trainer(coarse, OMEGA_S, 1.0, 1) as tr:
+        with pytest.raises(L.LBMError) as e:
+            tr.add_restricted(lat)
+        assert e.value.code == -2
+
+
 def test_features_match_oracle():
     dims = (9, 7, 5)
     df = noisy_state(dims, 7)

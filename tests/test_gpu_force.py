@@ -77,7 +77,7 @@ def case(st, mi, fkind, model=0):
 
 
 @pytest.mark.parametrize("fkind", ["uniform", "field"])
-@pytest.mark.parametrize("streaming", [L.PULL, L.AA, L.ESOTERIC_TWIST])
+@pytest.mark.parametrize("streaming", L.STREAMING_PATTERNS)
 @pytest.mark.parametrize("storage", [L.STORE_F64, L.STORE_F32])
 @pytest.mark.parametrize("mi", range(len(METHODS)),
                          ids=[f"sp{m[0]}eq{m[1]}{m[2]}" for m in METHODS])
@@ -105,7 +105,7 @@ HE_METHODS = [i for i, m in enumerate(METHODS) if m[0] != L.SPACE_CUMULANT]
 
 
 @pytest.mark.parametrize("fkind", ["uniform", "field"])
-@pytest.mark.parametrize("streaming", [L.PULL, L.ESOTERIC_TWIST])
+@pytest.mark.parametrize("streaming", [L.PULL, L.ESOTERIC_TWIST, L.ESOTERIC_PULL, L.ESOTERIC_PUSH])
 @pytest.mark.parametrize("storage", [L.STORE_F64, L.STORE_F32])
 @pytest.mark.parametrize("mi", HE_METHODS, ids=[f"sp{METHODS[i][0]}eq{METHODS[i][1]}{METHODS[i][2]}"
                                                 for i in HE_METHODS])

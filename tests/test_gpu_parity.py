@@ -82,7 +82,7 @@ def gpu_lattice(st, space, eq, reg, storage, streaming):
     return L.Lattice(st, space, eq, storage, streaming, rates_of(space, reg), DIMS[st])
 
 
-@pytest.mark.parametrize("streaming", [L.PULL, L.AA, L.ESOTERIC_TWIST])
+@pytest.mark.parametrize("streaming", L.STREAMING_PATTERNS)
 @pytest.mark.parametrize("storage", [L.STORE_F64, L.STORE_F32])
 @pytest.mark.parametrize("method", METHODS, ids=lambda m: f"sp{m[0]}eq{m[1]}reg{int(m[2])}")
 @pytest.mark.parametrize("st", [0, 1, 2], ids=["D2Q9", "D3Q19", "D3Q27"])
@@ -111,7 +111,7 @@ def test_step_parity(st, method, storage, streaming):
 
 @pytest.mark.parametrize("space", [L.SPACE_RAW, L.SPACE_CENTRAL, L.SPACE_CUMULANT])
 @pytest.mark.parametrize("st", [0, 1, 2])
-@pytest.mark.parametrize("streaming", [L.PULL, L.AA, L.ESOTERIC_TWIST])
+@pytest.mark.parametrize("streaming", L.STREAMING_PATTERNS)
 def test_init_velocity_is_the_method_equilibrium(st, space, streaming):
     eq = L.EQ_DELTA if space == L.SPACE_RAW else L.EQ_ABSOLUTE
     dims = DIMS[st]
@@ -134,20 +134,22 @@ def test_init_velocity_is_the_method_equilibrium(st, space, streaming):
 
 @pytest.mark.parametrize("storage", [L.STORE_F32, L.STORE_F64])
 def test_pull_and_aa_are_bitwise_identical(storage):
-    """Pull, AA and Esoteric Twist run the same per-cell arithmetic."""
+    """Pull, AA and the three esoteric patterns run the same per-cell
+    arithmetic; odd and even step counts end on both in-place parities."""
     st, space, eq, reg = 2, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, False
     _, dims, df0 = initial_state(st, space, eq, reg)
-    out = []
-    for streaming in (L.PULL, L.AA, L.ESOTERIC_TWIST):
-        with gpu_lattice(st, space, eq, reg, storage, streaming) as lat:
-            lat.set_populations(df0)
-            lat.step(5)
-            out.append(lat.get_populations())
-    assert np.array_equal(out[0], out[1])
-    assert np.array_equal(out[0], out[2])
+    for n in (4, 5):
+        out = []
+        for streaming in L.STREAMING_PATTERNS:
+            with gpu_lattice(st, space, eq, reg, storage, streaming) as lat:
+                lat.set_populations(df0)
+                lat.step(n)
+                out.append(lat.get_populations())
+        for k in range(1, len(out)):
+            assert np.array_equal(out[0], out[k]), (n, k)
 
 
-@pytest.mark.parametrize("streaming", [L.PULL, L.AA, L.ESOTERIC_TWIST])
+@pytest.mark.parametrize("streaming", L.STREAMING_PATTERNS)
 def test_checkpoint_resume_is_bitwise(streaming):
     st, space, eq, reg = 1, L.SPACE_RAW, L.EQ_DELTA, False
     _, dims, df0 = initial_state(st, space, eq, reg)
@@ -228,7 +230,7 @@ def test_device_pointer_path_matches_host_path():
 
 @pytest.mark.parametrize("storage,p", [(L.STORE_F16_DELTA, 10), (L.STORE_BF16_DELTA, 7)])
 @pytest.mark.parametrize("space", [L.SPACE_CENTRAL, L.SPACE_CUMULANT])
-@pytest.mark.parametrize("streaming", [L.PULL, L.AA, L.ESOTERIC_TWIST])
+@pytest.mark.parametrize("streaming", L.STREAMING_PATTERNS)
 def test_half_storage_error_bound(storage, p, space, streaming):
     """FP16 / BF16 delta storage: every store rounds each scaled deviation
     to p explicit mantissa bits, an error of at most 2^-(p+1) of |df_i|;
