@@ -4,8 +4,9 @@ Workload (default): D3Q27 cumulant LBM, regularised (shear rate from
 nu = 1e-3, bulk and higher-order rates 1), periodic 512^3 Taylor-Green vortex
 u0 = 0.05 plus seeded uniform +-1e-3 velocity noise, populations stored as
 FP32 deviations, pull streaming.  The same step is also timed with FP16- and
-BF16-delta storage and reported under "forms" with its velocity error
-against an FP64 run of the same steps.
+BF16-delta storage (reported under "forms" with its velocity error against an
+FP64 run of the same steps), with the in-place patterns (AA, Esoteric Twist,
+Pull, Push) and with a Guo body force.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
 
@@ -388,16 +389,17 @@ def run_cuda(args):
                            "u_rel_linf_vs_f64": uerr(uu),
                            "vs_f32_mlups": (N * args.steps / (ms / 1e3)) / (N * args.steps / (ms32 / 1e3))}
             del uu
-        # in-place AA pattern (one buffer), FP32, even number of steps
-        lat, ms = time_form(L.STORE_F32, 2 * (args.steps // 2), args.warmup + args.warmup % 2,
-                            streaming=L.AA)
-        lat.close()
-        del lat
-        st_aa = 2 * (args.steps // 2)
-        ach = BYTES_PER_CELL["f32"] * N / (ms / 1e3 / st_aa) / 1e9
-        forms["f32_aa"] = {"mlups": N * st_aa / (ms / 1e3) / 1e6, "achieved_gbs": ach,
-                           "roofline_frac": ach / peak, "buffers": 1,
-                           "note": "same per-cell arithmetic as pull (bitwise equal states)"}
+        # in-place patterns (one buffer), FP32, even number of steps
+        st_ip = 2 * (args.steps // 2)
+        for name in ("aa", "et", "epull", "epush"):
+            lat, ms = time_form(L.STORE_F32, st_ip, args.warmup + args.warmup % 2,
+                                streaming=STREAMINGS[name])
+            lat.close()
+            del lat
+            ach = BYTES_PER_CELL["f32"] * N / (ms / 1e3 / st_ip) / 1e9
+            forms[f"f32_{name}"] = {"mlups": N * st_ip / (ms / 1e3) / 1e6, "achieved_gbs": ach,
+                                    "roofline_frac": ach / peak, "buffers": 1,
+                                    "note": "same per-cell arithmetic as pull (bitwise equal states)"}
         # body force (Guo): uniform, and a per-cell field (+12 B/cell of reads)
         for name, force, bpc in (
                 ("f32_force_uniform", np.array([1e-6, 0.0, 0.0]), BYTES_PER_CELL["f32"]),

@@ -63,7 +63,7 @@ typedef struct lbm_trainer lbm_trainer;
 
 /* Trainer for a coarse lattice of coarse_dims (each >= 1, product < 2^31)
  * with the given shear and bulk rates, holding at most max_snapshots
- * snapshots (27 * N FP32 values each).  Parameters start at zero (rates 1,
+ * snapshots (27 * N FP32 values each; at least 2, a training pair).  Parameters start at zero (rates 1,
  * the plain method), shift 0, scale 1.  Errors: INVALID, OOM, CUDA. */
 int lbm_trainer_create(lbm_trainer** out, const int64_t coarse_dims[3],
                        double omega_shear, double omega_bulk,

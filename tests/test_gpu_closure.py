@@ -160,7 +160,7 @@ def test_restriction_refuses_esoteric_layouts(streaming):
     coarse = (2, 2, 2)
     with L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F32, streaming,
                    [OMEGA_S] + [1.0] * 5, tuple(4 * v for v in coarse)) as lat, \
-            L.Trainer(coarse, OMEGA_S, 1.0, 1) as tr:
+            L.Trainer(coarse, OMEGA_S, 1.0, 2) as tr:
         with pytest.raises(L.LBMError) as e:
             tr.add_restricted(lat)
         assert e.value.code == -2
