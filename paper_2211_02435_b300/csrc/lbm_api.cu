@@ -110,6 +110,7 @@ AuxArgs aux_base(const lbm_ctx* c, int op) {
   a.force_field = c->force_field;
   a.swe_g = c->swe_g;
   a.stream = c->stream;
+  lbm::whole_slab(a);
   return a;
 }
 
@@ -270,8 +271,18 @@ void lbm_destroy(lbm_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  for (int b = 0; b < 2; ++b)
+  if (c->io_stream) {
+    cudaStreamSynchronize(c->io_stream);
+    cudaStreamDestroy(c->io_stream);
+    for (int b = 0; b < 2; ++b) {
+      cudaEventDestroy(c->io_ready[b]);
+      cudaEventDestroy(c->io_done[b]);
+    }
+  }
+  for (int b = 0; b < 2; ++b) {
+    if (c->io_buf[b]) cudaFree(c->io_buf[b]);
     if (c->buf[b]) cudaFree(c->buf[b]);
+  }
   if (c->part) cudaFree(c->part);
   if (c->closure) lbm::free_closure(c->closure);
   if (c->force_field) cudaFree(c->force_field);
@@ -397,12 +408,16 @@ int lbm_get_time(const lbm_ctx* c, int64_t* step, int* parity) {
   return LBM_OK;
 }
 
+static int scatter_layout(const lbm_ctx* c) {
+  return c->p.streaming == LBM_PULL
+             ? G_PULL
+             : (esoteric(c->p.streaming) ? eso_mode(c->p.streaming, 0) : G_LOCAL);
+}
+
 static int scatter(lbm_ctx* c, const double* df, const double* rho, const double* u) {
   if (c->p.streaming != LBM_PULL) c->parity = 0;
   AuxArgs a = aux_base(c, lbm::AUX_SCATTER);
-  a.gather_mode = c->p.streaming == LBM_PULL
-                      ? G_PULL
-                      : (esoteric(c->p.streaming) ? eso_mode(c->p.streaming, 0) : G_LOCAL);
+  a.gather_mode = scatter_layout(c);
   a.df_in = df;
   a.rho_in = rho;
   a.u_in = u;
@@ -410,9 +425,185 @@ static int scatter(lbm_ctx* c, const double* df, const double* rho, const double
   return cuda_err(cudaGetLastError());
 }
 
+static int read_status(lbm_ctx* c);
+
+// ------------------------------------------------ host transfers in slabs
+// Host arrays are moved slab by slab: a slab is a run of z-planes (of y-rows
+// when Nz = 1) whose ncomp components sit in one of two device staging
+// buffers (component k at k * cells + (c - c0)).  The copies of slab k run
+// on the context's copy stream while the set-up / read-out kernel of slab
+// k - 1 runs on its stream, so the host link and the kernels overlap; events
+// keep a staging buffer from being refilled before its kernel (set-up) or
+// its copy (read-out) is done.
+namespace {
+
+constexpr size_t IO_SLAB_BYTES = size_t(64) << 20;  // per staging buffer
+
+struct SlabPlan {
+  bool planes;  // slabs of z-planes (else of y-rows)
+  int64_t unit_cells;
+  int nunits, per;  // units in the lattice / in a full slab
+};
+
+// false: move the arrays whole (small lattices, or one plane beyond the
+// staging size)
+bool slab_plan(const lbm_ctx* c, int ncomp, SlabPlan* sp) {
+  sp->planes = c->g.nz > 1;
+  sp->unit_cells = sp->planes ? int64_t(c->g.nx) * c->g.ny : c->g.nx;
+  sp->nunits = sp->planes ? c->g.nz : c->g.ny;
+  const size_t unit_bytes = size_t(sp->unit_cells) * ncomp * sizeof(double);
+  if (size_t(c->g.N) * ncomp * sizeof(double) < 4 * IO_SLAB_BYTES) return false;
+  if (unit_bytes > IO_SLAB_BYTES) return false;
+  sp->per = int(IO_SLAB_BYTES / unit_bytes);
+  return true;
+}
+
+// create the copy stream and events once, grow the staging buffers
+int io_ready(lbm_ctx* c, size_t doubles) {
+  if (!c->io_stream) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k < 4 && ok; ++k)
+      ok = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      for (int k = 0; k < 4; ++k)
+        if (ev[k]) cudaEventDestroy(ev[k]);
+      if (s) cudaStreamDestroy(s);
+      return LBM_ERR_CUDA;
+    }
+    c->io_stream = s;
+    c->io_ready[0] = ev[0];
+    c->io_ready[1] = ev[1];
+    c->io_done[0] = ev[2];
+    c->io_done[1] = ev[3];
+  }
+  if (c->io_cap < doubles) {
+    for (int b = 0; b < 2; ++b) {
+      if (c->io_buf[b]) cudaFree(c->io_buf[b]);
+      c->io_buf[b] = nullptr;
+    }
+    c->io_cap = 0;
+    for (int b = 0; b < 2; ++b) {
+      if (cudaMalloc((void**)&c->io_buf[b], doubles * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        for (int k = 0; k < 2; ++k) {
+          if (c->io_buf[k]) cudaFree(c->io_buf[k]);
+          c->io_buf[k] = nullptr;
+        }
+        return LBM_ERR_OOM;
+      }
+    }
+    c->io_cap = doubles;
+  }
+  return LBM_OK;
+}
+
+void set_slab(AuxArgs& a, const SlabPlan& sp, int u0, int nu, int64_t cells) {
+  if (sp.planes) {
+    a.z0 = u0;
+    a.nzc = nu;
+  } else {
+    a.y0 = u0;
+    a.nyc = nu;
+  }
+  a.c0 = int64_t(u0) * sp.unit_cells;
+  a.stride = cells;
+}
+
+// host -> device: comps[k] is the host array of component k (N doubles) or
+// NULL; df_mode: the q components are populations, else (rho, u_0..u_d-1)
+int scatter_slabs(lbm_ctx* c, const SlabPlan& sp, const double* const* comps, int ncomp,
+                  bool df_mode) {
+  const int64_t cap = sp.unit_cells * sp.per;
+  int rc = io_ready(c, size_t(cap) * ncomp);
+  if (rc != LBM_OK) return rc;
+  if (c->p.streaming != LBM_PULL) c->parity = 0;
+  bool ok = true;
+  // the copies start after the work already queued on the context's stream
+  // (a staging buffer may still be read by an earlier call's kernel)
+  ok = ok && cudaEventRecord(c->io_done[0], c->stream) == cudaSuccess;
+  ok = ok && cudaStreamWaitEvent(c->io_stream, c->io_done[0], 0) == cudaSuccess;
+  for (int k = 0, u0 = 0; ok && u0 < sp.nunits; ++k, u0 += sp.per) {
+    const int nu = sp.per < sp.nunits - u0 ? sp.per : sp.nunits - u0;
+    const int64_t c0 = int64_t(u0) * sp.unit_cells, cells = int64_t(nu) * sp.unit_cells;
+    const int b = k & 1;
+    double* sb = c->io_buf[b];
+    if (k >= 2) ok = ok && cudaStreamWaitEvent(c->io_stream, c->io_done[b], 0) == cudaSuccess;
+    for (int j = 0; j < ncomp && ok; ++j)
+      if (comps[j])
+        ok = cudaMemcpyAsync(sb + j * cells, comps[j] + c0, size_t(cells) * sizeof(double),
+                             cudaMemcpyHostToDevice, c->io_stream) == cudaSuccess;
+    ok = ok && cudaEventRecord(c->io_ready[b], c->io_stream) == cudaSuccess;
+    ok = ok && cudaStreamWaitEvent(c->stream, c->io_ready[b], 0) == cudaSuccess;
+    if (!ok) break;
+    AuxArgs a = aux_base(c, lbm::AUX_SCATTER);
+    a.gather_mode = scatter_layout(c);
+    set_slab(a, sp, u0, nu, cells);
+    if (df_mode) {
+      a.df_in = sb;
+    } else {
+      a.rho_in = comps[0] ? sb : nullptr;
+      a.u_in = sb + cells;
+    }
+    kAux[c->p.stencil][c->p.storage](a);
+    ok = cudaGetLastError() == cudaSuccess;
+    ok = ok && cudaEventRecord(c->io_done[b], c->stream) == cudaSuccess;
+  }
+  if (cudaStreamSynchronize(c->io_stream) != cudaSuccess) ok = false;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) ok = false;
+  return ok ? LBM_OK : LBM_ERR_CUDA;
+}
+
+// device -> host: outs[k] is the host array of component k or NULL
+int gather_slabs(lbm_ctx* c, const SlabPlan& sp, double* const* outs, int ncomp, bool df_mode) {
+  const int64_t cap = sp.unit_cells * sp.per;
+  int rc = io_ready(c, size_t(cap) * ncomp);
+  if (rc != LBM_OK) return rc;
+  bool ok = true;
+  for (int k = 0, u0 = 0; ok && u0 < sp.nunits; ++k, u0 += sp.per) {
+    const int nu = sp.per < sp.nunits - u0 ? sp.per : sp.nunits - u0;
+    const int64_t c0 = int64_t(u0) * sp.unit_cells, cells = int64_t(nu) * sp.unit_cells;
+    const int b = k & 1;
+    double* sb = c->io_buf[b];
+    if (k >= 2) ok = cudaStreamWaitEvent(c->stream, c->io_done[b], 0) == cudaSuccess;
+    if (!ok) break;
+    AuxArgs a = aux_base(c, lbm::AUX_GATHER);
+    set_slab(a, sp, u0, nu, cells);
+    if (df_mode) {
+      a.df = sb;
+    } else {
+      a.rho = outs[0] ? sb : nullptr;
+      a.u = outs[1] ? sb + cells : nullptr;
+    }
+    kAux[c->p.stencil][c->p.storage](a);
+    ok = cudaGetLastError() == cudaSuccess;
+    ok = ok && cudaEventRecord(c->io_ready[b], c->stream) == cudaSuccess;
+    ok = ok && cudaStreamWaitEvent(c->io_stream, c->io_ready[b], 0) == cudaSuccess;
+    for (int j = 0; j < ncomp && ok; ++j)
+      if (outs[j])
+        ok = cudaMemcpyAsync(outs[j] + c0, sb + j * cells, size_t(cells) * sizeof(double),
+                             cudaMemcpyDeviceToHost, c->io_stream) == cudaSuccess;
+    ok = ok && cudaEventRecord(c->io_done[b], c->io_stream) == cudaSuccess;
+  }
+  if (cudaStreamSynchronize(c->io_stream) != cudaSuccess) ok = false;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) ok = false;
+  if (!ok) return LBM_ERR_CUDA;
+  return read_status(c);
+}
+
+}  // namespace
+
 int lbm_init_velocity(lbm_ctx* c, const double* rho, const double* u, int on_device) {
   if (!c || !u) return LBM_ERR_INVALID;
   const size_t N = size_t(c->g.N);
+  SlabPlan sp;
+  if (!on_device && c->swe_g == 0.0 && slab_plan(c, 1 + c->d, &sp)) {
+    const double* comps[4] = {rho, u, u + N, c->d > 2 ? u + 2 * N : nullptr};
+    c->t = 0;
+    return scatter_slabs(c, sp, comps, 1 + c->d, false);
+  }
   const double *drho = nullptr, *du = nullptr;
   double *trho = nullptr, *tu = nullptr;
   int rc = stage_in(c, rho, N, on_device, &drho, &trho);
@@ -431,6 +622,12 @@ int lbm_init_velocity(lbm_ctx* c, const double* rho, const double* u, int on_dev
 
 int lbm_set_populations(lbm_ctx* c, const double* df, int on_device) {
   if (!c || !df) return LBM_ERR_INVALID;
+  SlabPlan sp;
+  if (!on_device && slab_plan(c, c->q, &sp)) {
+    const double* comps[27];
+    for (int i = 0; i < c->q; ++i) comps[i] = df + size_t(i) * size_t(c->g.N);
+    return scatter_slabs(c, sp, comps, c->q, true);
+  }
   const double* ddf = nullptr;
   double* tmp = nullptr;
   int rc = stage_in(c, df, size_t(c->g.N) * c->q, on_device, &ddf, &tmp);
@@ -525,6 +722,16 @@ int lbm_step(lbm_ctx* c, int64_t n) {
 
 static int gather(lbm_ctx* c, double* df, double* rho, double* u, int on_device) {
   const size_t N = size_t(c->g.N);
+  SlabPlan sp;
+  if (!on_device && df && slab_plan(c, c->q, &sp)) {
+    double* outs[27];
+    for (int i = 0; i < c->q; ++i) outs[i] = df + size_t(i) * N;
+    return gather_slabs(c, sp, outs, c->q, true);
+  }
+  if (!on_device && !df && slab_plan(c, 1 + c->d, &sp)) {
+    double* outs[4] = {rho, u, u ? u + N : nullptr, (u && c->d > 2) ? u + 2 * N : nullptr};
+    return gather_slabs(c, sp, outs, 1 + c->d, false);
+  }
   double *tdf = nullptr, *trho = nullptr, *tu = nullptr;
   int rc = LBM_OK;
   if (!on_device) {

@@ -147,6 +147,7 @@ AuxArgs aux_of(const lbm_batch* b, int k, int op) {
   a.space = b->space;
   a.gather_mode = 0;  // pull
   a.stream = b->stream;
+  lbm::whole_slab(a);
   return a;
 }
 

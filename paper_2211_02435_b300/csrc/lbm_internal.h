@@ -81,8 +81,24 @@ struct AuxArgs {
   double force[3];
   const void* force_field;
   double swe_g;  // scatter from (h, u): the shallow-water equilibrium
+  // gather / scatter over a slab of the lattice (chunked host transfers):
+  // z-planes [z0, z0 + nzc) and rows [y0, y0 + nyc); the staged arrays hold
+  // the slab's cells only, component k of cell c at k * stride + (c - c0).
+  // Whole lattice: y0 = z0 = 0, nyc = Ny, nzc = Nz, c0 = 0, stride = N.
+  int y0, z0, nyc, nzc;
+  int64_t c0, stride;
   cudaStream_t stream;
 };
+
+// the whole lattice as the slab of a read-out / set-up launch
+inline void whole_slab(AuxArgs& a) {
+  a.y0 = 0;
+  a.z0 = 0;
+  a.nyc = a.g.ny;
+  a.nzc = a.g.nz;
+  a.c0 = 0;
+  a.stride = a.g.N;
+}
 
 // one pair of entry points per (stencil, storage) object file
 #define LBM_DECL(ST, SO)                           \
@@ -160,5 +176,11 @@ struct lbm_ctx {
   double force[3];    // uniform body force (zeros when unset)
   void* force_field;  // device [D][N] in the compute type, or NULL
   double swe_g;       // > 0: shallow-water method (lbm_set_shallow_water)
+  // host transfers in slabs (created on first use): a copy stream, two
+  // staging buffers and the events that order them against c->stream
+  cudaStream_t io_stream;
+  cudaEvent_t io_ready[2], io_done[2];
+  double* io_buf[2];
+  size_t io_cap;  // doubles per staging buffer
 };
 

@@ -7,7 +7,8 @@
 // buf[i * N + c] with c = (z * Ny + y) * Nx + x (x fastest), so a warp of
 // 32 consecutive x reads 32 consecutive elements of each population plane.
 // One thread updates one cell; a block covers LBM_BX consecutive x of one
-// (y, z) row; the grid is (ceil(Nx / LBM_BX), Ny, Nz).
+// (y, z) row (LBM_PULL_BX for the pull step kernel); the grid is
+// (ceil(Nx / block), Ny, Nz).
 #pragma once
 
 #include "lbm_device.cuh"
@@ -19,6 +20,13 @@ namespace lbm {
 
 #ifndef LBM_BX
 #define LBM_BX 128
+#endif
+// block of the scalar pull step kernel k_pull: measured on B300 at 512^3
+// (D3Q27 cumulant FP32) 31.58 GLUPS with 256 threads against 31.11 with 128
+// and 31.17 with 64; the other kernels keep LBM_BX (the in-place patterns
+// split between the two sizes, the packed FP16 / BF16 kernel lost 1.4 %)
+#ifndef LBM_PULL_BX
+#define LBM_PULL_BX 256
 #endif
 // minimum resident CTAs per SM asked of the packed FP16 / BF16 step kernel
 // (a compile-time tuning knob; 0 leaves the register budget to the compiler,
@@ -183,9 +191,9 @@ struct PullPtrs {
 
 // pull: read f_i from x - xi_i of src, collide, write f*_i at x of dst
 template <int ST, class S, class T, int SPACE, bool REG, int FORM = FORM_DEV, int FORCE = FORCE_NONE>
-__global__ void __launch_bounds__(LBM_BX) k_pull(const __grid_constant__ PullPtrs<S> P, Geo g,
-                                                 Rates<T> keep, ForceArg<T> fa = {}) {
-  const int x = blockIdx.x * LBM_BX + threadIdx.x;
+__global__ void __launch_bounds__(LBM_PULL_BX) k_pull(const __grid_constant__ PullPtrs<S> P, Geo g,
+                                                      Rates<T> keep, ForceArg<T> fa = {}) {
+  const int x = blockIdx.x * LBM_PULL_BX + threadIdx.x;
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
   const int c = (z * g.ny + y) * g.nx + x;
@@ -430,18 +438,27 @@ void launch_inplace(const StepArgs& a, const Rates<T>& keep, const dim3& grid,
 
 // ------------------------------------------------------ read-out kernels
 // canonical populations -> FP64 SoA df[i * N + c] and / or macroscopic
+// Slab of a read-out / set-up launch: block (bx, by, bz) covers row
+// (y0 + by, z0 + bz); the staged arrays hold component k of cell c at
+// k * stride + (c - c0).
+struct Slab {
+  int y0, z0;
+  int64_t c0, stride;
+};
+
 template <int ST, class S, class T, int MODE>
 __global__ void __launch_bounds__(LBM_BX) k_gather(const S* buf, Geo g, double* df, double* rho,
-                                                   double* u, ForceArg<T> fa = {}) {
+                                                   double* u, Slab sl, ForceArg<T> fa = {}) {
   const int x = blockIdx.x * LBM_BX + threadIdx.x;
   if (x >= g.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = sl.y0 + blockIdx.y, z = sl.z0 + blockIdx.z;
   const Nbr n = neighbours(x, y, z, g);
   const int c = (z * g.ny + y) * g.nx + x;
+  const int64_t s = c - sl.c0;  // index in the staged arrays
   T f[q_of(ST)];
   load_pops<ST, S, T, MODE>(buf, g, n, c, f);
   if (df) {
-    sfor<q_of(ST)>([&](auto I) { df[(int64_t)CI(I) * g.N + c] = double(f[CI(I)]); });
+    sfor<q_of(ST)>([&](auto I) { df[(int64_t)CI(I) * sl.stride + s] = double(f[CI(I)]); });
   }
   if (rho || u) {
     double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
@@ -454,13 +471,13 @@ __global__ void __launch_bounds__(LBM_BX) k_gather(const S* buf, Geo g, double* 
       if constexpr (vel(ST, i, 2) != 0) j[2] += vel(ST, i, 2) * v;
     });
     const double r = 1.0 + dr;
-    if (rho) rho[c] = r;
+    if (rho) rho[s] = r;
     if (u) {
       // under a body force the fluid velocity is (j + F/2) / rho
       for (int d = 0; d < dim_of(ST); ++d) {
         double Fd = double(fa.F[d]);
         if (fa.field) Fd += double(fa.field[(int64_t)d * g.N + c]);
-        u[(int64_t)d * g.N + c] = (j[d] + 0.5 * Fd) / r;
+        u[(int64_t)d * sl.stride + s] = (j[d] + 0.5 * Fd) / r;
       }
     }
   }
@@ -472,19 +489,20 @@ __global__ void __launch_bounds__(LBM_BX) k_gather(const S* buf, Geo g, double* 
 // gather of cell x looks), AA -> buf[i][x] (even parity).
 template <int ST, class S, class T, int SPACE, int LAYOUT>
 __global__ void __launch_bounds__(LBM_BX) k_scatter(S* buf, Geo g, const double* df,
-                                                    const double* rho, const double* u) {
+                                                    const double* rho, const double* u, Slab sl) {
   const int x = blockIdx.x * LBM_BX + threadIdx.x;
   if (x >= g.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = sl.y0 + blockIdx.y, z = sl.z0 + blockIdx.z;
   const Nbr n = neighbours(x, y, z, g);
   const int c = (z * g.ny + y) * g.nx + x;
+  const int64_t s = c - sl.c0;  // index in the staged arrays
   T f[q_of(ST)];
   if (df) {
-    sfor<q_of(ST)>([&](auto I) { f[CI(I)] = T(df[(int64_t)CI(I) * g.N + c]); });
+    sfor<q_of(ST)>([&](auto I) { f[CI(I)] = T(df[(int64_t)CI(I) * sl.stride + s]); });
   } else {
-    const T dr = rho ? T(rho[c] - 1.0) : T(0);
+    const T dr = rho ? T(rho[s] - 1.0) : T(0);
     T uu[3] = {T(0), T(0), T(0)};
-    for (int d = 0; d < dim_of(ST); ++d) uu[d] = T(u[(int64_t)d * g.N + c]);
+    for (int d = 0; d < dim_of(ST); ++d) uu[d] = T(u[(int64_t)d * sl.stride + s]);
     equilibrium<ST, T, SPACE>(dr, uu, f);
   }
   sfor<q_of(ST)>([&](auto I) {
@@ -656,6 +674,9 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS)
 
 // --------------------------------------------------------------- launchers
 inline dim3 step_grid(const Geo& g) { return dim3((g.nx + LBM_BX - 1) / LBM_BX, g.ny, g.nz); }
+inline dim3 pull_grid(const Geo& g) {
+  return dim3((g.nx + LBM_PULL_BX - 1) / LBM_PULL_BX, g.ny, g.nz);
+}
 
 // forced steps (FP32 / FP64 storage, deviation arithmetic)
 template <int ST, class S, class T, int SPACE, bool REG>
@@ -676,7 +697,7 @@ void launch_forced(const StepArgs& a, const Rates<T>& keep, const dim3& grid) {
         P.src[i] = i < q_of(ST) ? (const S*)a.src + (int64_t(i) * a.g.N + delta) : nullptr;
         P.dst[i] = i < q_of(ST) ? (S*)a.dst + int64_t(i) * a.g.N : nullptr;
       }
-      k_pull<ST, S, T, SPACE, REG, FORM_DEV, FC><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep, fa);
+      k_pull<ST, S, T, SPACE, REG, FORM_DEV, FC><<<pull_grid(a.g), LBM_PULL_BX, 0, a.stream>>>(P, a.g, keep, fa);
     } else {
       launch_inplace<ST, S, T, SPACE, REG, FC>(a, keep, grid, fa);
     }
@@ -729,11 +750,11 @@ void launch_step_typed(const StepArgs& a) {
       }
       // absolute forms serve SRT and the moment spaces (TRT is refused at create)
       if constexpr (SPACE != SP_TRT)
-        k_pull<ST, S, T, SPACE, REG, FORM_ABS_STORE><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep);
+        k_pull<ST, S, T, SPACE, REG, FORM_ABS_STORE><<<pull_grid(a.g), LBM_PULL_BX, 0, a.stream>>>(P, a.g, keep);
       return;
     } else if constexpr (std::is_same<S, double>::value && SPACE != SP_TRT) {
       if (a.form == FORM_ABS_EQ) {
-        k_pull<ST, S, T, SPACE, REG, FORM_ABS_EQ><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep);
+        k_pull<ST, S, T, SPACE, REG, FORM_ABS_EQ><<<pull_grid(a.g), LBM_PULL_BX, 0, a.stream>>>(P, a.g, keep);
         return;
       }
     }
@@ -747,7 +768,7 @@ void launch_step_typed(const StepArgs& a) {
         return;
       }
     }
-    k_pull<ST, S, T, SPACE, REG><<<grid, LBM_BX, 0, a.stream>>>(P, a.g, keep);
+    k_pull<ST, S, T, SPACE, REG><<<pull_grid(a.g), LBM_PULL_BX, 0, a.stream>>>(P, a.g, keep);
   }
   else
     launch_inplace<ST, S, T, SPACE, REG>(a, keep, grid);
@@ -773,6 +794,8 @@ void launch_step_space(const StepArgs& a) {
 template <int ST, class S, class T>
 void launch_aux_typed(const AuxArgs& a) {
   const dim3 grid = step_grid(a.g);
+  const dim3 sgrid((a.g.nx + LBM_BX - 1) / LBM_BX, a.nyc, a.nzc);  // the slab
+  const Slab sl{a.y0, a.z0, a.c0, a.stride};
   const int gm = a.gather_mode;
   switch (a.op) {
     case AUX_GATHER: {
@@ -781,7 +804,7 @@ void launch_aux_typed(const AuxArgs& a) {
       fa.field = a.force_mode == FORCE_FIELD ? (const T*)a.force_field : nullptr;
       with_gather_mode(gm, [&](auto mode) {
         k_gather<ST, S, T, decltype(mode)::value>
-            <<<grid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, fa);
+            <<<sgrid, LBM_BX, 0, a.stream>>>((const S*)a.buf, a.g, a.df, a.rho, a.u, sl, fa);
       });
       break;
     }
@@ -800,9 +823,9 @@ void launch_aux_typed(const AuxArgs& a) {
       auto go = [&](auto layout) {
         constexpr int LY = decltype(layout)::value;
         if (raw)
-          k_scatter<ST, S, T, SP_RAW, LY><<<grid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in);
+          k_scatter<ST, S, T, SP_RAW, LY><<<sgrid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in, sl);
         else
-          k_scatter<ST, S, T, SP_CENTRAL, LY><<<grid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in);
+          k_scatter<ST, S, T, SP_CENTRAL, LY><<<sgrid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in, sl);
       };
       switch (gm) {  // scatter writes the even-parity layout of each pattern
         case G_PULL: go(std::integral_constant<int, G_PULL>{}); break;
