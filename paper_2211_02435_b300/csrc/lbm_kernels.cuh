@@ -361,12 +361,25 @@ struct InPlaceMap {
 #define LBM_INPLACE_REV_MASK ((1 << MODE_EPULL_EVEN) | (1 << MODE_EPULL_ODD))
 #endif
 
+// Block size of the in-place kernel per mode: 256 threads for Esoteric Twist
+// and Pull, 128 for AA and Esoteric Push (measured at 512^3, MLUPS with 128
+// -> 256 threads: Twist 30,297 -> 30,866, Pull 29,850 -> 30,549, AA
+// 30,273 -> 29,946, Push 30,332 -> 29,228).
+LBM_HD constexpr int inplace_bx(int mode) {
+  return (mode == MODE_ET_EVEN || mode == MODE_ET_ODD || mode == MODE_EPULL_EVEN ||
+          mode == MODE_EPULL_ODD)
+             ? 256
+             : LBM_BX;
+}
+
 template <int ST, class S, class T, int SPACE, bool REG, int MODE, int FORCE = FORCE_NONE>
-__global__ void __launch_bounds__(LBM_BX) k_inplace(const __grid_constant__ InPlacePtrs<S> P, Geo g,
-                                                    Rates<T> keep, ForceArg<T> fa = {}) {
+__global__ void __launch_bounds__(inplace_bx(MODE)) k_inplace(const __grid_constant__ InPlacePtrs<S> P,
+                                                              Geo g, Rates<T> keep,
+                                                              ForceArg<T> fa = {}) {
   constexpr bool REV = (LBM_INPLACE_REV_MASK >> MODE) & 1;
+  constexpr int BX = inplace_bx(MODE);
   const int bx = REV ? int(gridDim.x) - 1 - int(blockIdx.x) : int(blockIdx.x);
-  const int x = bx * LBM_BX + threadIdx.x;
+  const int x = bx * BX + threadIdx.x;
   if (x >= g.nx) return;
   const int y = REV ? g.ny - 1 - int(blockIdx.y) : int(blockIdx.y);
   const int z = REV ? g.nz - 1 - int(blockIdx.z) : int(blockIdx.z);
@@ -419,10 +432,13 @@ template <int ST, class S, class T, int SPACE, bool REG, int FORCE = FORCE_NONE>
 void launch_inplace(const StepArgs& a, const Rates<T>& keep, const dim3& grid,
                     const ForceArg<T>& fa = {}) {
   S* buf = (S*)a.dst;
+  (void)grid;
   auto go = [&](auto mode_tag) {
     constexpr int MODE = decltype(mode_tag)::value;
+    constexpr int BX = inplace_bx(MODE);
+    const dim3 igrid((a.g.nx + BX - 1) / BX, a.g.ny, a.g.nz);
     k_inplace<ST, S, T, SPACE, REG, MODE, FORCE>
-        <<<grid, LBM_BX, 0, a.stream>>>(inplace_ptrs<ST, MODE>(buf, a.g), a.g, keep, fa);
+        <<<igrid, BX, 0, a.stream>>>(inplace_ptrs<ST, MODE>(buf, a.g), a.g, keep, fa);
   };
   switch (a.mode) {
     case MODE_AA_EVEN: go(std::integral_constant<int, MODE_AA_EVEN>{}); break;
