@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_HERE, "liblbm_oracle.so")
 D2Q9, D3Q19, D3Q27 = 0, 1, 2
 SPACE_POPULATIONS, SPACE_RAW, SPACE_CENTRAL, SPACE_CUMULANT, SPACE_TRT = 0, 1, 2, 3, 4
 SPACE_RAW_WEIGHTED, SPACE_NONE = 5, 6
-EQ_DELTA, EQ_ABSOLUTE = 0, 1
+EQ_DELTA, EQ_ABSOLUTE, EQ_DISCRETE2 = 0, 1, 2
 GROUP_CONSERVED, GROUP_SHEAR, GROUP_BULK = -1, 0, 1
 Q_OF = {D2Q9: 9, D3Q19: 19, D3Q27: 27}
 

@@ -321,6 +321,17 @@ static double maxwell_central_moment(const int* e, double rho) {
   return rho * gauss_moment(e[0]) * gauss_moment(e[1]) * gauss_moment(e[2]);
 }
 
+/* The discrete second-order equilibrium as populations (Sec. 2.4, an
+ * equilibrium prescribed as a discrete distribution):
+ * f_eq_i = w_i rho (1 + 3 xi.u + 9/2 (xi.u)^2 - 3/2 u.u), c_s^2 = 1/3. */
+static void discrete_feq(const lattice_t* L, double rho, const double* u, double* feq) {
+  const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  for (int i = 0; i < L->q; ++i) {
+    const double xu = L->xi[i][0] * u[0] + L->xi[i][1] * u[1] + L->xi[i][2] * u[2];
+    feq[i] = L->w[i] * rho * (1.0 + 3.0 * xu + 4.5 * xu * xu - 1.5 * uu);
+  }
+}
+
 /* ------------------------------------------------------------------ */
 /* cumulants (Eq. 2.11): c(S) = sum over set partitions pi of S of      */
 /* (-1)^(|pi|-1) (|pi|-1)! prod_{B in pi} mu(B)  -- the coefficient     */
@@ -485,6 +496,8 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
     matvec(q, L->M, S, sF);
   }
   const int delta = m->equilibrium == LBM_ORACLE_EQ_DELTA;
+  const int disc = m->equilibrium == LBM_ORACLE_EQ_DISCRETE2; /* absolute path */
+  if (disc && (forced || swe_g > 0.0)) return -1; /* not defined with a force */
   double f[QMAX] = {0}, tmp[QMAX] = {0}, tmp2[QMAX] = {0}, veq[QMAX] = {0},
          vout[QMAX] = {0};
   static const double zero_u[3] = {0, 0, 0};
@@ -497,10 +510,14 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
       /* two relaxation times: the even part f+_i = (f_i + f_ibar)/2 relaxes
        * with w+ = rates[0], the odd part f-_i = (f_i - f_ibar)/2 with
        * w- = rates[2]; equilibrium and Guo source split the same way */
-      for (int k = 0; k < q; ++k)
-        veq[k] = maxwell_raw_moment(L->expo[k], rho, u, 1) -
-                 (delta ? maxwell_raw_moment(L->expo[k], 1.0, zero_u, 1) : 0.0);
-      matvec(q, L->Minv, veq, tmp); /* delta: df_eq ; absolute: f_eq */
+      if (disc) {
+        discrete_feq(L, rho, u, tmp);
+      } else {
+        for (int k = 0; k < q; ++k)
+          veq[k] = maxwell_raw_moment(L->expo[k], rho, u, 1) -
+                   (delta ? maxwell_raw_moment(L->expo[k], 1.0, zero_u, 1) : 0.0);
+        matvec(q, L->Minv, veq, tmp); /* delta: df_eq ; absolute: f_eq */
+      }
       const double wp = m->rates[0], wm = m->rates[2];
       for (int i = 0; i < q; ++i) {
         const int ib = L->opp[i];
@@ -517,11 +534,16 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
       return 0;
     }
     case LBM_ORACLE_SPACE_POPULATIONS: {
-      /* SRT: f* = f + w (f_eq - f), f_eq = M^-1 m_eq (truncated) */
-      for (int k = 0; k < q; ++k)
-        veq[k] = maxwell_raw_moment(L->expo[k], rho, u, 1) -
-                 (delta ? maxwell_raw_moment(L->expo[k], 1.0, zero_u, 1) : 0.0);
-      matvec(q, L->Minv, veq, tmp); /* delta: df_eq ; absolute: f_eq */
+      /* SRT: f* = f + w (f_eq - f), f_eq = M^-1 m_eq (truncated), or the
+       * discrete f_eq itself */
+      if (disc) {
+        discrete_feq(L, rho, u, tmp);
+      } else {
+        for (int k = 0; k < q; ++k)
+          veq[k] = maxwell_raw_moment(L->expo[k], rho, u, 1) -
+                   (delta ? maxwell_raw_moment(L->expo[k], 1.0, zero_u, 1) : 0.0);
+        matvec(q, L->Minv, veq, tmp); /* delta: df_eq ; absolute: f_eq */
+      }
       const double om = m->rates[0];
       for (int i = 0; i < q; ++i) {
         if (delta)
@@ -550,8 +572,14 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
       } else { /* Eq. 2.6 */
         for (int i = 0; i < q; ++i) f[i] = df[i] + L->w[i];
         matvec(q, L->M, f, tmp);
-        for (int k = 0; k < q; ++k)
-          veq[k] = maxwell_raw_moment(L->expo[k], rho, u, 1);
+        if (disc) { /* q_eq = T(f_eq) */
+          double fd[QMAX];
+          discrete_feq(L, rho, u, fd);
+          matvec(q, L->M, fd, veq);
+        } else {
+          for (int k = 0; k < q; ++k)
+            veq[k] = maxwell_raw_moment(L->expo[k], rho, u, 1);
+        }
         relax_forced(L, m, PR, PRinv, tmp, veq, sF, vout);
         matvec(q, L->Minv, vout, tmp2);
         for (int i = 0; i < q; ++i) out[i] = tmp2[i] - L->w[i];
@@ -584,6 +612,10 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
           double fz[QMAX];
           swe_zhou_feq(L, rho, u, swe_g, fz);
           matvec(q, K, fz, veq);
+        } else if (disc) { /* q_eq = K(u) f_eq */
+          double fd[QMAX];
+          discrete_feq(L, rho, u, fd);
+          matvec(q, K, fd, veq);
         } else {
           for (int k = 0; k < q; ++k)
             veq[k] = maxwell_central_moment(L->expo[k], rho);
@@ -613,6 +645,17 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
         const int* e = L->expo[k];
         mu[e[0]][e[1]][e[2]] = tmp[k] / rho_a;
       }
+      double mueq[3][3][3]; /* discrete equilibrium: its own cumulants */
+      if (disc) {
+        double fd[QMAX], md[QMAX];
+        for (int a = 0; a < 27; ++a) (&mueq[0][0][0])[a] = NAN;
+        discrete_feq(L, rho, u, fd);
+        matvec(q, L->M, fd, md);
+        for (int k = 0; k < q; ++k) {
+          const int* e = L->expo[k];
+          mueq[e[0]][e[1]][e[2]] = md[k] / md[0];
+        }
+      }
       for (int k = 0; k < q; ++k) {
         const int* e = L->expo[k];
         if (L->deg[k] == 0)
@@ -625,6 +668,8 @@ static int collide_cell_f(const lattice_t* L, const lbm_oracle_method* m,
          * of order 2, zero above; orders 0 and 1 are conserved */
         if (L->deg[k] <= 1)
           veq[k] = v[k];
+        else if (disc)
+          veq[k] = rho_a * cumulant_from_mu(L->part[k], L->npart[k], mueq);
         else
           veq[k] = (L->deg[k] == 2 && (e[0] == 2 || e[1] == 2 || e[2] == 2))
                        ? rho_a * (swe_g > 0.0 ? 0.5 * swe_g * rho_a : 1.0 / 3.0)
@@ -661,7 +706,8 @@ static int check_method(const lbm_oracle_method* m) {
   if (!m || build_lattice(m->stencil)) return -1;
   if (m->space < 0 || m->space > 6) return -1;
   if (m->equilibrium != LBM_ORACLE_EQ_DELTA &&
-      m->equilibrium != LBM_ORACLE_EQ_ABSOLUTE)
+      m->equilibrium != LBM_ORACLE_EQ_ABSOLUTE &&
+      m->equilibrium != LBM_ORACLE_EQ_DISCRETE2)
     return -1;
   if (m->space == LBM_ORACLE_SPACE_CUMULANT &&
       m->equilibrium == LBM_ORACLE_EQ_DELTA)
@@ -816,6 +862,11 @@ static void equilibrium_cell(const lattice_t* L, const lbm_oracle_method* m,
                     m->space == LBM_ORACLE_SPACE_POPULATIONS ||
                     m->space == LBM_ORACLE_SPACE_TRT ||
                     m->space == LBM_ORACLE_SPACE_NONE;
+  if (m->equilibrium == LBM_ORACLE_EQ_DISCRETE2) { /* the discrete f_eq - w */
+    discrete_feq(L, rho, u, out);
+    for (int i = 0; i < L->q; ++i) out[i] -= L->w[i];
+    return;
+  }
   double dm[QMAX];
   for (int k = 0; k < L->q; ++k)
     dm[k] = maxwell_raw_moment(L->expo[k], rho, u, trunc) -

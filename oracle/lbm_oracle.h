@@ -61,6 +61,12 @@ extern "C" {
 /* equilibrium format: deviation-only (Eq. 2.5) or absolute (Eq. 2.6) */
 #define LBM_ORACLE_EQ_DELTA 0
 #define LBM_ORACLE_EQ_ABSOLUTE 1
+/* the discrete second-order polynomial equilibrium given as populations,
+ * f_eq_i = w_i rho (1 + 3 xi.u + 9/2 (xi.u)^2 - 3/2 u.u), whose collision-
+ * space quantities are q_eq = T(f_eq) (Sec. 2.4: an equilibrium may be
+ * prescribed as a discrete population vector and transformed); absolute
+ * collision (Eq. 2.6) */
+#define LBM_ORACLE_EQ_DISCRETE2 2
 /* rate groups (row groups of the polynomial bases) */
 #define LBM_ORACLE_GROUP_CONSERVED -1
 #define LBM_ORACLE_GROUP_SHEAR 0
