@@ -99,8 +99,25 @@ typedef enum {
  * Cumulant space admits only LBM_EQ_ABSOLUTE (Sec. 2.4): the other is
  * rejected with LBM_ERR_INADMISSIBLE.  Raw-moment methods use the
  * continuous Maxwellian truncated at second order in u (Sec. 4.2);
- * central-moment and cumulant methods the untruncated Maxwellian. */
-typedef enum { LBM_EQ_DELTA = 0, LBM_EQ_ABSOLUTE = 1 } lbm_equilibrium;
+ * central-moment and cumulant methods the untruncated Maxwellian.
+ *
+ * LBM_EQ_DISCRETE2: the equilibrium prescribed as a discrete population
+ * vector (Sec. 2.4), the second-order polynomial
+ *   f_eq_i = w_i rho (1 + 3 xi.u + 9/2 (xi.u)^2 - 3/2 u.u),
+ * transformed into the collision space, q_eq = T(f_eq), in every space
+ * (SRT and TRT relax against f_eq itself).  Its raw moments equal the
+ * truncated Maxwellian's on D2Q9 and D3Q27 and differ on D3Q19 in the
+ * x^2 y^2-type moments (by -rho u_k^2 / 6), so raw-moment MRT with equal
+ * rates is the textbook BGK there; its central moments and cumulants of
+ * order >= 3 are nonzero (central and cumulant methods run their general
+ * instance).  lbm_init_velocity sets f_eq.  Served for LBM_STORE_F64 /
+ * LBM_STORE_F32, pull streaming and LBM_ARITH_DEVIATION, without a body
+ * force or a closure; otherwise LBM_ERR_UNSUPPORTED. */
+typedef enum {
+  LBM_EQ_DELTA = 0,
+  LBM_EQ_ABSOLUTE = 1,
+  LBM_EQ_DISCRETE2 = 2
+} lbm_equilibrium;
 
 /* Population storage.  F64 computes in FP64, the others in FP32.  The
  * *_DELTA forms store h_i = round_rn(df_i * 2^s_i) in FP16 / BF16 with the

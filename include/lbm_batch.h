@@ -15,9 +15,10 @@
  *
  * Conventions are those of include/lbm.h (return codes, ownership, field
  * layouts, velocity order, canonical pre-collision state f(n)).  Only pull
- * streaming, zero-centered storage and deviation arithmetic are served
- * (in-place patterns, LBM_STORE_F64_ABSOLUTE or LBM_ARITH_AS_WRITTEN ->
- * LBM_ERR_UNSUPPORTED); every collision space is.  Instance k stores
+ * streaming, zero-centered storage, deviation arithmetic and the Maxwellian
+ * equilibria are served (in-place patterns, LBM_STORE_F64_ABSOLUTE,
+ * LBM_ARITH_AS_WRITTEN or LBM_EQ_DISCRETE2 -> LBM_ERR_UNSUPPORTED); every
+ * collision space is.  Instance k stores
  * its populations as a structure of arrays at element offset off_k of one
  * device buffer per pull buffer (the library owns them).
  */

@@ -109,6 +109,7 @@ AuxArgs aux_base(const lbm_ctx* c, int op) {
   for (int d = 0; d < 3; ++d) a.force[d] = c->force[d];
   a.force_field = c->force_field;
   a.swe_g = c->swe_g;
+  a.disc = c->p.equilibrium == LBM_EQ_DISCRETE2;
   a.stream = c->stream;
   lbm::whole_slab(a);
   return a;
@@ -194,7 +195,8 @@ int lbm_create(lbm_ctx** out, const lbm_params* p) {
   *out = nullptr;
   if (p->stencil < 0 || p->stencil > 2 || p->space < 0 || p->space > 5 || p->storage < 0 ||
       p->storage > 4 || p->streaming < 0 || p->streaming > 4 ||
-      (p->equilibrium != LBM_EQ_DELTA && p->equilibrium != LBM_EQ_ABSOLUTE) ||
+      (p->equilibrium != LBM_EQ_DELTA && p->equilibrium != LBM_EQ_ABSOLUTE &&
+       p->equilibrium != LBM_EQ_DISCRETE2) ||
       (p->arithmetic != LBM_ARITH_DEVIATION && p->arithmetic != LBM_ARITH_AS_WRITTEN))
     return LBM_ERR_INVALID;
   // Sec. 3: no zero-centered cumulants; delta-equilibria need zero-centered storage
@@ -202,6 +204,11 @@ int lbm_create(lbm_ctx** out, const lbm_params* p) {
     return LBM_ERR_INADMISSIBLE;
   if (p->storage == LBM_STORE_F64_ABSOLUTE && p->equilibrium == LBM_EQ_DELTA)
     return LBM_ERR_INADMISSIBLE;
+  // the discrete equilibrium: FP64 / FP32 deviations, pull streaming
+  if (p->equilibrium == LBM_EQ_DISCRETE2 &&
+      ((p->storage != LBM_STORE_F64 && p->storage != LBM_STORE_F32) ||
+       p->streaming != LBM_PULL || p->arithmetic != LBM_ARITH_DEVIATION))
+    return LBM_ERR_UNSUPPORTED;
   if ((p->storage == LBM_STORE_F64_ABSOLUTE || p->arithmetic == LBM_ARITH_AS_WRITTEN) &&
       (p->streaming != LBM_PULL || p->space == LBM_SPACE_TRT ||
        (p->storage != LBM_STORE_F64 && p->storage != LBM_STORE_F64_ABSOLUTE)))
@@ -299,7 +306,8 @@ __global__ void k_f64_to_f32(const double* in, float* out, int64_t n) {
 
 bool force_served(const lbm_ctx* c) {
   return (c->p.storage == LBM_STORE_F64 || c->p.storage == LBM_STORE_F32) &&
-         c->p.arithmetic == LBM_ARITH_DEVIATION && !c->closure && !(c->swe_g > 0.0);
+         c->p.arithmetic == LBM_ARITH_DEVIATION && !c->closure && !(c->swe_g > 0.0) &&
+         c->p.equilibrium != LBM_EQ_DISCRETE2;
 }
 
 void update_force_mode(lbm_ctx* c) {
@@ -644,6 +652,7 @@ static bool staged_ok(const lbm_ctx* c) {
   const int64_t row = int64_t(c->g.nx) * c->eb;
   return c->p.streaming == LBM_PULL && c->p.storage != LBM_STORE_F64_ABSOLUTE &&
          c->p.arithmetic == LBM_ARITH_DEVIATION && !c->force_mode && row % 16 == 0 &&
+         c->p.equilibrium != LBM_EQ_DISCRETE2 &&
          lbm::staged_stages(c->q, c->g.nx, c->eb) >= lbm::STG_MIN_STAGES;
 }
 
@@ -681,6 +690,12 @@ int lbm_step(lbm_ctx* c, int64_t n) {
   a.reg = c->reg;
   a.storage = c->p.storage;
   a.form = (c->p.arithmetic == LBM_ARITH_AS_WRITTEN && c->p.equilibrium == LBM_EQ_ABSOLUTE) ? 1 : 0;
+  if (c->p.equilibrium == LBM_EQ_DISCRETE2) {
+    a.form = 3;  // FORM_DISC
+    // central moments / cumulants: the general instance (nonzero equilibria
+    // of order >= 3)
+    if (c->space == LBM_SPACE_CENTRAL || c->space == LBM_SPACE_CUMULANT) a.reg = 0;
+  }
   a.variant = use_staged(c) ? lbm::VARIANT_STAGED : lbm::VARIANT_DIRECT;
   a.status = c->status;
   a.force_mode = c->force_mode;

@@ -160,8 +160,10 @@ int lbm_batch_create(lbm_batch** out, const lbm_params* p, int n, const int64_t*
   if (!out || !p || n < 1 || !dims) return LBM_ERR_INVALID;
   *out = nullptr;
   if (p->stencil < 0 || p->stencil > 2 || p->space < 0 || p->space > 5 || p->storage < 0 ||
-      p->storage > 4 || (p->equilibrium != LBM_EQ_DELTA && p->equilibrium != LBM_EQ_ABSOLUTE))
+      p->storage > 4 || (p->equilibrium != LBM_EQ_DELTA && p->equilibrium != LBM_EQ_ABSOLUTE &&
+                         p->equilibrium != LBM_EQ_DISCRETE2))
     return LBM_ERR_INVALID;
+  if (p->equilibrium == LBM_EQ_DISCRETE2) return LBM_ERR_UNSUPPORTED;
   if (p->space == LBM_SPACE_CUMULANT && p->equilibrium == LBM_EQ_DELTA)
     return LBM_ERR_INADMISSIBLE;
   if (p->boundary != LBM_PERIODIC || p->streaming != LBM_PULL ||

@@ -482,9 +482,58 @@ LBM_D void cumulant_bwd(const T (&C)[3][3][3], T (&K)[3][3][3]) {
 template <int ST, class T, int SPACE>
 LBM_D void equilibrium(T drho, const T (&u)[3], T (&f)[q_of(ST)]);
 
+// ---------------------------------- discrete second-order equilibrium
+// An equilibrium prescribed as populations (Sec. 2.4): f_eq_i = w_i rho
+// (1 + P_i), P_i = 3 xi.u + 9/2 (xi.u)^2 - 3/2 u.u; its collision-space
+// quantities are q_eq = T(f_eq).  As deviations: df_eq_i = w_i (drho +
+// rho P_i).
+template <int ST, int i, class T>
+LBM_D T disc_poly(const T (&u)[3], T uu) {
+  T xu = T(0);
+  if constexpr (vel(ST, i, 0) != 0) xu += T(vel(ST, i, 0)) * u[0];
+  if constexpr (vel(ST, i, 1) != 0) xu += T(vel(ST, i, 1)) * u[1];
+  if constexpr (vel(ST, i, 2) != 0) xu += T(vel(ST, i, 2)) * u[2];
+  return T(3) * xu + T(4.5) * (xu * xu) - T(1.5) * uu;
+}
+template <int ST, class T>
+LBM_D void disc_feq(T drho, T rho, const T (&u)[3], T (&f)[q_of(ST)]) {
+  const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    f[i] = T(weight(ST, i)) * (drho + rho * disc_poly<ST, i, T>(u, uu));
+  });
+}
+// Raw moments of f_eq differ from the truncated Maxwellian's only on D3Q19,
+// in the fourth-order x^2 y^2-type moments: by -rho u_k^2 / 6, k the third
+// axis (D2Q9 and D3Q27 have product weights, for which they agree).
+template <int ST, class T>
+LBM_D T disc_raw_corr(int a, int b, int c, T rho, const T (&u)[3]) {
+  if (ST != D3Q19 || a + b + c != 4 || a == 1 || b == 1 || c == 1) return T(0);
+  const int k = a == 0 ? 0 : (b == 0 ? 1 : 2);
+  return -rho * u[k] * u[k] * T(1.0 / 6.0);
+}
+// Normalised central-moment deviations of f_eq (they depend on u only:
+// f_eq / rho = w (1 + P)): the same Chimera passes as for f, applied to
+// w_i P_i, whose sum is zero.
+template <int ST, class T>
+LBM_D void disc_central_eq(const T (&u)[3], const T (&u2)[3], T (&E)[3][3][3]) {
+  T g[q_of(ST)];
+  const T uu = u2[0] + u2[1] + u2[2];
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    g[i] = T(weight(ST, i)) * disc_poly<ST, i, T>(u, uu);
+  });
+  fwd_raw_chimera<ST, T>(g, E);
+  E[0][0][0] = T(0);
+  binomial<ST, -1, T>(E, u, u2);
+}
+
 // ------------------------------------------------------------ collision
 // In: zero-centered pre-collision populations f.  Out: zero-centered
 // post-collision populations f*.  keep.om[g] = 1 - omega_g.
+// DISC: relax toward the discrete second-order equilibrium (q_eq = T(f_eq))
+// instead of the Maxwellian's moments (general instance for central moments
+// and cumulants, whose equilibria of order >= 3 are then nonzero).
 // population-space collisions under DEFER: scale population i by
 // 2^(|xi_i|^2) as the deferred backward transform would have left it
 template <int ST, class T>
@@ -537,9 +586,11 @@ LBM_D void he_source(T drho, T inv, const T (&u)[3], const T (&F)[3], T (&S)[q_o
 //   cumulant: cumulants relax about the mean j / rho; the mean leaves as
 //             (j + F) / rho (cumulants of order >= 2 are shift invariant).
 template <int ST, class T, int SPACE, bool REG, bool DEFER = false, bool FORCED = false,
-          bool HE = false>
+          bool HE = false, bool DISC = false>
 LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr) {
   static_assert(!(HE && SPACE == SP_CUMULANT), "He's model is not defined for cumulants");
+  static_assert(!(DISC && (FORCED || (REG && (SPACE == SP_CENTRAL || SPACE == SP_CUMULANT)))),
+                "the discrete equilibrium runs unforced; central / cumulant: general path");
   static_assert(!(FORCED && REG && (SPACE == SP_RAW || SPACE == SP_RAW_W)),
                 "forced raw moments use the general path");
   constexpr bool WO = SPACE == SP_RAW_W;
@@ -568,7 +619,8 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
   if constexpr (SPACE == SP_SRT) {
     // single relaxation time in population space against f_eq = M^-1 m_eq
     T feq[q_of(ST)];
-    equilibrium<ST, T, SP_RAW>(drho, u, feq);
+    if constexpr (DISC) disc_feq<ST, T>(drho, rho, u, feq);
+    else equilibrium<ST, T, SP_RAW>(drho, u, feq);
     if constexpr (FORCED) {
       T S[q_of(ST)];
       force_source(S);
@@ -589,7 +641,8 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
     // two relaxation times: per opposite pair the even part relaxes with
     // keep.om[0] = 1 - w+, the odd part with keep.om[2] = 1 - w-
     T feq[q_of(ST)], S[q_of(ST)];
-    equilibrium<ST, T, SP_RAW>(drho, u, feq);
+    if constexpr (DISC) disc_feq<ST, T>(drho, rho, u, feq);
+    else equilibrium<ST, T, SP_RAW>(drho, u, feq);
     if constexpr (FORCED) force_source(S);
     const T kp = keep.om[0], km = keep.om[2];
     sfor<q_of(ST)>([&](auto I) {
@@ -624,6 +677,8 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
       constexpr int o = a + b + c;
       if constexpr (has_mono(ST, a, b, c)) {
         E[a][b][c] = raw_eq_dev<T>(a, b, c, drho, rho, u);
+        if constexpr (DISC && ST == D3Q19 && a + b + c == 4)
+          E[a][b][c] += disc_raw_corr<ST, T>(a, b, c, rho, u);
         // forced: the first-order non-equilibrium part is -F/2
         if constexpr (o == 0 || (o == 1 && !FORCED) || (REG && o != 2)) N[a][b][c] = T(0);
         else N[a][b][c] = A[a][b][c] - E[a][b][c];
@@ -679,8 +734,20 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
         Kn[a][b][c] = T(0);
       }
     });
+    // DISC: the equilibrium's normalised deviations Eq; the Maxwellian's are 0
+    T Eq[3][3][3];
+    if constexpr (DISC) disc_central_eq<ST, T>(u, u2, Eq);
+    auto shift_eq = [&](T (&X)[3][3][3], T sign) {
+      if constexpr (DISC) {
+        sfor<27>([&](auto K) {
+          constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+          if constexpr (has_mono(ST, a, b, c) && a + b + c >= 2) X[a][b][c] += sign * Eq[a][b][c];
+        });
+      }
+    };
     if constexpr (SPACE == SP_CENTRAL) {
-      // equilibrium of every normalised deviation is 0: dk* = (1 - w) dk
+      // dk* = dk_eq + (1 - w) (dk - dk_eq), dk_eq = 0 for the Maxwellian
+      shift_eq(Kn, T(-1));
       relax_order2<ST, T, REG>(Kn, keep.om[0], keep.om[1]);
       sfor<27>([&](auto K) {
         constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
@@ -690,6 +757,7 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
           else Kn[a][b][c] *= keep.om[o - 1];
         }
       });
+      shift_eq(Kn, T(1));
       if constexpr (FORCED && HE) {
         // q^F = (I - S/2) K(u) S: central moments of He's source about u,
         // scaled per rate group, added to the normalised deviations
@@ -729,12 +797,32 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
         Cm[a][b][c] = Kn[a][b][c];
       });
       if constexpr (!REG) cumulant_fwd<ST, T>(Kn, Cm);
+      // DISC: relax about the cumulants of f_eq (those of its normalised
+      // central moments Eq)
+      T Ceq[3][3][3];
+      if constexpr (DISC) {
+        sfor<27>([&](auto K) {
+          constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+          Ceq[a][b][c] = Eq[a][b][c];
+        });
+        cumulant_fwd<ST, T>(Eq, Ceq);
+        sfor<27>([&](auto K) {
+          constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+          if constexpr (has_mono(ST, a, b, c) && a + b + c >= 2) Cm[a][b][c] -= Ceq[a][b][c];
+        });
+      }
       relax_order2<ST, T, REG>(Cm, keep.om[0], keep.om[1]);
       if constexpr (!REG) {
         sfor<27>([&](auto K) {
           constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
           constexpr int o = a + b + c;
           if constexpr (has_mono(ST, a, b, c) && o >= 3) Cm[a][b][c] *= keep.om[o - 1];
+        });
+      }
+      if constexpr (DISC) {
+        sfor<27>([&](auto K) {
+          constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, c = CI(K) % 3;
+          if constexpr (has_mono(ST, a, b, c) && a + b + c >= 2) Cm[a][b][c] += Ceq[a][b][c];
         });
       }
       // orders 2 and 3: central = cumulant; 4..6 from the inverse relations

@@ -51,7 +51,7 @@ struct StepArgs {
   int reg;    // bulk and orders >= 3 relaxed with rate 1 (compile-time)
   int storage;
   int mode;
-  int form;     // FORM_DEV / FORM_ABS_EQ (Eq. 2.6 arithmetic, FP64 storage)
+  int form;     // FORM_DEV / FORM_ABS_EQ (Eq. 2.6 arithmetic, FP64 storage) / FORM_DISC
   int variant;  // VARIANT_DIRECT / VARIANT_STAGED (pull only)
   int* status;  // device word set by a kernel whose bounded wait ran out
   int force_mode;           // FORCE_NONE / FORCE_UNIFORM / FORCE_FIELD
@@ -81,6 +81,7 @@ struct AuxArgs {
   double force[3];
   const void* force_field;
   double swe_g;  // scatter from (h, u): the shallow-water equilibrium
+  int disc;      // scatter from (rho, u): the discrete second-order equilibrium
   // gather / scatter over a slab of the lattice (chunked host transfers):
   // z-planes [z0, z0 + nzc) and rows [y0, y0 + nyc); the staged arrays hold
   // the slab's cells only, component k of cell c at k * stride + (c - c0).

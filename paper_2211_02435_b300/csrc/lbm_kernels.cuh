@@ -111,8 +111,9 @@ LBM_D S enc_pop(T f) {
 }
 
 // arithmetic form of the step kernel: deviations (default), Eq. 2.6 from
-// zero-centered storage, Eq. 2.4 on absolute storage
-enum { FORM_DEV = 0, FORM_ABS_EQ = 1, FORM_ABS_STORE = 2 };
+// zero-centered storage, Eq. 2.4 on absolute storage, deviations with the
+// discrete second-order equilibrium (q_eq = T(f_eq), Sec. 2.4)
+enum { FORM_DEV = 0, FORM_ABS_EQ = 1, FORM_ABS_STORE = 2, FORM_DISC = 3 };
 
 // body force of a step: the uniform part F plus, for FORCE_FIELD, the cell's
 // entry of a per-cell field field[d * N + c] in the compute type
@@ -218,6 +219,8 @@ __global__ void __launch_bounds__(LBM_PULL_BX) k_pull(const __grid_constant__ Pu
     collide<ST, T, SPACE, REG, false, true, (FORCE >= FORCE_UNIFORM_HE)>(f, keep, Fc);
   } else if constexpr (FORM == FORM_DEV) {
     collide<ST, T, SPACE, REG>(f, keep);
+  } else if constexpr (FORM == FORM_DISC) {
+    collide<ST, T, SPACE, REG, false, false, false, true>(f, keep);
   } else {
     collide_abs<ST, T, SPACE, REG, FORM == FORM_ABS_EQ>(f, keep);
   }
@@ -503,7 +506,7 @@ __global__ void __launch_bounds__(LBM_BX) k_gather(const S* buf, Geo g, double* 
 // rho / u when df is NULL) into the storage so that the next gather returns
 // them: pull -> buf[i][x - xi_i] (moved back upstream, where the pull
 // gather of cell x looks), AA -> buf[i][x] (even parity).
-template <int ST, class S, class T, int SPACE, int LAYOUT>
+template <int ST, class S, class T, int SPACE, int LAYOUT, bool DISC = false>
 __global__ void __launch_bounds__(LBM_BX) k_scatter(S* buf, Geo g, const double* df,
                                                     const double* rho, const double* u, Slab sl) {
   const int x = blockIdx.x * LBM_BX + threadIdx.x;
@@ -519,7 +522,8 @@ __global__ void __launch_bounds__(LBM_BX) k_scatter(S* buf, Geo g, const double*
     const T dr = rho ? T(rho[s] - 1.0) : T(0);
     T uu[3] = {T(0), T(0), T(0)};
     for (int d = 0; d < dim_of(ST); ++d) uu[d] = T(u[(int64_t)d * sl.stride + s]);
-    equilibrium<ST, T, SPACE>(dr, uu, f);
+    if constexpr (DISC) disc_feq<ST, T>(dr, T(1) + dr, uu, f);
+    else equilibrium<ST, T, SPACE>(dr, uu, f);
   }
   sfor<q_of(ST)>([&](auto I) {
     constexpr int i = CI(I);
@@ -774,6 +778,13 @@ void launch_step_typed(const StepArgs& a) {
         return;
       }
     }
+    if constexpr ((std::is_same<S, float>::value || std::is_same<S, double>::value) &&
+                  !(REG && (SPACE == SP_CENTRAL || SPACE == SP_CUMULANT))) {
+      if (a.form == FORM_DISC) {
+        k_pull<ST, S, T, SPACE, REG, FORM_DISC><<<pull_grid(a.g), LBM_PULL_BX, 0, a.stream>>>(P, a.g, keep);
+        return;
+      }
+    }
     constexpr bool half = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
     if constexpr (half) {
       if (a.g.nx % 2 == 0) {
@@ -838,7 +849,9 @@ void launch_aux_typed(const AuxArgs& a) {
                        a.space == SP_RAW_W;
       auto go = [&](auto layout) {
         constexpr int LY = decltype(layout)::value;
-        if (raw)
+        if (a.disc)
+          k_scatter<ST, S, T, SP_RAW, LY, true><<<sgrid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in, sl);
+        else if (raw)
           k_scatter<ST, S, T, SP_RAW, LY><<<sgrid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in, sl);
         else
           k_scatter<ST, S, T, SP_CENTRAL, LY><<<sgrid, LBM_BX, 0, a.stream>>>((S*)a.buf, a.g, a.df_in, a.rho_in, a.u_in, sl);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "liblbm.so")
 D2Q9, D3Q19, D3Q27 = 0, 1, 2
 SPACE_POPULATIONS, SPACE_RAW, SPACE_CENTRAL, SPACE_CUMULANT, SPACE_TRT = 0, 1, 2, 3, 4
 SPACE_RAW_WEIGHTED = 5
-EQ_DELTA, EQ_ABSOLUTE = 0, 1
+EQ_DELTA, EQ_ABSOLUTE, EQ_DISCRETE2 = 0, 1, 2
 STORE_F64, STORE_F32, STORE_F16_DELTA, STORE_BF16_DELTA, STORE_F64_ABSOLUTE = 0, 1, 2, 3, 4
 ARITH_DEVIATION, ARITH_AS_WRITTEN = 0, 1
 STEP_AUTO, STEP_DIRECT, STEP_STAGED = 0, 1, 2

@@ -66,6 +66,12 @@ def _params(**kw):
     (dict(storage=L.STORE_F64_ABSOLUTE, streaming=L.AA), -2),
     (dict(arithmetic=L.ARITH_AS_WRITTEN, storage=L.STORE_F32), -2),
     (dict(arithmetic=L.ARITH_AS_WRITTEN, storage=L.STORE_F64, streaming=L.AA), -2),
+    # the discrete equilibrium: FP64 / FP32 deviations with pull streaming only
+    (dict(equilibrium=L.EQ_DISCRETE2, storage=L.STORE_F16_DELTA), -2),
+    (dict(equilibrium=L.EQ_DISCRETE2, streaming=L.ESOTERIC_PULL), -2),
+    (dict(equilibrium=L.EQ_DISCRETE2, storage=L.STORE_F64_ABSOLUTE), -2),
+    (dict(equilibrium=L.EQ_DISCRETE2, storage=L.STORE_F64, arithmetic=L.ARITH_AS_WRITTEN), -2),
+    (dict(equilibrium=3), -1),
 ])
 def test_create_rejects_bad_parameters(lib, kw, code):
     h = ctypes.c_void_p()
