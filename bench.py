@@ -498,6 +498,62 @@ STEP_KERNELS = {"auto": 0, "direct": 1, "staged": 2}  # LBM_STEP_* of include/lb
 STREAMINGS = {"pull": 0, "aa": 1, "et": 2, "epull": 3, "epush": 4}
 
 
+def run_method_survey(args):
+    """Throughput of the pull step for every stencil, collision space and
+    storage (not the headline): D3Q19 / D3Q27 at 512^3, D2Q9 at 8192^2, the
+    regularised (R-) rates with shear from nu = 1e-3, Taylor-Green start; one
+    JSON line with MLUPS and the fraction of the measured copy bandwidth at
+    2 q b bytes per cell update."""
+    import torch
+    from paper_2211_02435_b300 import build as B
+    from paper_2211_02435_b300 import lbm as L
+
+    B.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = measured_peaks()
+    rates = [I.shear_viscosity_rate(1e-3)] + [1.0] * 5
+    spaces = [("SRT", L.SPACE_POPULATIONS, L.EQ_DELTA), ("TRT", L.SPACE_TRT, L.EQ_DELTA),
+              ("R-O-MRT", L.SPACE_RAW, L.EQ_DELTA), ("R-WO-MRT", L.SPACE_RAW_WEIGHTED, L.EQ_DELTA),
+              ("R-CM", L.SPACE_CENTRAL, L.EQ_ABSOLUTE), ("R-K", L.SPACE_CUMULANT, L.EQ_ABSOLUTE)]
+    stores = [("f32", L.STORE_F32, 4), ("f16_delta", L.STORE_F16_DELTA, 2)]
+    rows = []
+    for st, name, dims in ((L.D2Q9, "D2Q9", (8192, 8192, 1)), (L.D3Q19, "D3Q19", (512,) * 3),
+                           (L.D3Q27, "D3Q27", (512,) * 3)):
+        d = 2 if st == L.D2Q9 else 3
+        rho, u = I.taylor_green(dims, 0.05, d=d)
+        rho_d = torch.from_numpy(np.ascontiguousarray(rho.reshape(-1))).cuda()
+        u_d = torch.from_numpy(np.ascontiguousarray(u.reshape(-1))).cuda()
+        del rho, u
+        N = int(np.prod(dims))
+        for sname, space, eq in spaces:
+            r = [1.6] * 6 if space == L.SPACE_POPULATIONS else (
+                [rates[0], 1.0, 1.75, 1.0, 1.0, 1.0] if space == L.SPACE_TRT else rates)
+            for kname, storage, eb in stores:
+                with L.Lattice(st, space, eq, storage, L.PULL, r, dims, stream=stream) as lat:
+                    lat.init_velocity(rho_d, u_d)
+                    lat.step(args.warmup)
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    lat.step(args.steps)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / args.steps
+                bpc = 2 * lat.q * eb
+                rows.append({"stencil": name, "method": sname, "storage": kname,
+                             "cells": N, "mlups": N / ms / 1e3,
+                             "bytes_per_cell": bpc, "roofline_frac": bpc * N / ms / 1e6 / peak})
+        del rho_d, u_d
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "pull-step MLUPS per stencil, collision space and storage",
+                      "unit": UNIT, "peak_gbs": peak, "peak_kind": peak_kind,
+                      "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+                      "rows": rows}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -514,6 +570,8 @@ def main():
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="storage of the headline form (default FP32)")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--method-survey", action="store_true",
+                    help="time the pull step of every stencil / space / storage instead")
     ap.add_argument("--learned-fine", type=int, default=512)
     ap.add_argument("--batch-n", type=int, default=4096)
     ap.add_argument("--step-kernel", choices=list(STEP_KERNELS), default="auto",
@@ -525,6 +583,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "cuda":
         args.warmup = 3
+    if args.method_survey:
+        return run_method_survey(args)
     return run_reference(args) if args.impl == "reference" else run_cuda(args)
 
 
