@@ -512,36 +512,6 @@ LBM_D T disc_raw_corr(int a, int b, int c, T rho, const T (&u)[3]) {
   const int k = a == 0 ? 0 : (b == 0 ? 1 : 2);
   return -rho * u[k] * u[k] * T(1.0 / 6.0);
 }
-// Population-space equilibrium deviations of SRT / TRT.  DISC: the
-// polynomial.  Otherwise f_eq = M^-1 m_eq with the truncated Maxwellian's
-// raw moments, which on D2Q9 / D3Q27 is the same polynomial; on D3Q19 those
-// moments exceed the polynomial's by rho u_k^2 / 6 in the x^2 y^2-type
-// moments, and M^-1 maps that onto the rest population (+rho u.u / 6), the
-// faces normal to axis a (-rho (u.u - u_a^2) / 12) and the edges in the
-// plane normal to axis k (+rho u_k^2 / 24).
-template <int ST, class T, bool DISC>
-LBM_D void pop_feq(T drho, T rho, const T (&u)[3], T (&f)[q_of(ST)]) {
-  disc_feq<ST, T>(drho, rho, u, f);
-  if constexpr (!DISC && ST == D3Q19) {
-    const T u2[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
-    const T uu = u2[0] + u2[1] + u2[2];
-    sfor<q_of(ST)>([&](auto I) {
-      constexpr int i = CI(I);
-      constexpr int ax = vel(ST, i, 0) * vel(ST, i, 0), ay = vel(ST, i, 1) * vel(ST, i, 1),
-                    az = vel(ST, i, 2) * vel(ST, i, 2);
-      if constexpr (ax + ay + az == 0) {
-        f[i] += rho * uu * T(1.0 / 6.0);
-      } else if constexpr (ax + ay + az == 1) {
-        const T ua2 = ax ? u2[0] : (ay ? u2[1] : u2[2]);
-        f[i] -= rho * (uu - ua2) * T(1.0 / 12.0);
-      } else {
-        const T uk2 = !ax ? u2[0] : (!ay ? u2[1] : u2[2]);
-        f[i] += rho * uk2 * T(1.0 / 24.0);
-      }
-    });
-  }
-}
-
 // Normalised central-moment deviations of f_eq (they depend on u only:
 // f_eq / rho = w (1 + P)): the same Chimera passes as for f, applied to
 // w_i P_i, whose sum is zero.
@@ -646,11 +616,18 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
     else guo_source<ST, T>(u, Fv, S);
   };
 
+  // population-space equilibrium f_eq = M^-1 m_eq.  On D3Q27 (product
+  // weights) the truncated Maxwellian's raw moments are those of the
+  // second-order polynomial, so f_eq is that polynomial, evaluated in closed
+  // form; on D2Q9 / D3Q19 the backward transform of m_eq measured faster in
+  // the packed FP16 kernel (D3Q27 SRT 47.6 -> 51.6 GLUPS, D2Q9 163.7 ->
+  // 154.0, D3Q19 75.1 -> 66.3 with the closed form)
+  constexpr bool POLY = DISC || ST == D3Q27;
   if constexpr (SPACE == SP_SRT) {
-    // single relaxation time in population space against f_eq = M^-1 m_eq,
-    // evaluated in closed form (pop_feq)
+    // single relaxation time in population space against f_eq
     T feq[q_of(ST)];
-    pop_feq<ST, T, DISC>(drho, rho, u, feq);
+    if constexpr (POLY) disc_feq<ST, T>(drho, rho, u, feq);
+    else equilibrium<ST, T, SP_RAW>(drho, u, feq);
     if constexpr (FORCED) {
       T S[q_of(ST)];
       force_source(S);
@@ -671,7 +648,8 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
     // two relaxation times: per opposite pair the even part relaxes with
     // keep.om[0] = 1 - w+, the odd part with keep.om[2] = 1 - w-
     T feq[q_of(ST)], S[q_of(ST)];
-    pop_feq<ST, T, DISC>(drho, rho, u, feq);
+    if constexpr (POLY) disc_feq<ST, T>(drho, rho, u, feq);
+    else equilibrium<ST, T, SP_RAW>(drho, u, feq);
     if constexpr (FORCED) force_source(S);
     const T kp = keep.om[0], km = keep.om[2];
     sfor<q_of(ST)>([&](auto I) {
