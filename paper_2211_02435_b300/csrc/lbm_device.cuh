@@ -652,6 +652,7 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
     else equilibrium<ST, T, SP_RAW>(drho, u, feq);
     if constexpr (FORCED) force_source(S);
     const T kp = keep.om[0], km = keep.om[2];
+    const T hp = T(0.5) * kp, hm = T(0.5) * km;
     sfor<q_of(ST)>([&](auto I) {
       constexpr int i = CI(I);
       constexpr int b = opp(i);
@@ -659,11 +660,11 @@ LBM_D void collide(T (&f)[q_of(ST)], const Rates<T>& keep, const T* F = nullptr)
         f[i] = feq[i] + kp * (f[i] - feq[i]);
         if constexpr (FORCED) f[i] += T(0.5) * (T(1) + kp) * S[i];
       } else if constexpr (i < b) {
-        const T np = (f[i] + f[b]) - (feq[i] + feq[b]);
-        const T nm = (f[i] - f[b]) - (feq[i] - feq[b]);
-        const T ep = T(0.5) * (feq[i] + feq[b]), em = T(0.5) * (feq[i] - feq[b]);
-        const T rp = T(0.5) * (kp * np), rm = T(0.5) * (km * nm);
-        T fi = ep + em + rp + rm, fb = ep - em + rp - rm;
+        // with d = f - f_eq: f*_i = f_eq_i + (1 - w+)(d_i + d_b)/2 +
+        // (1 - w-)(d_i - d_b)/2, f*_b the same with the odd part negated
+        const T di = f[i] - feq[i], db = f[b] - feq[b];
+        const T a = hp * (di + db), c = hm * (di - db);
+        T fi = feq[i] + (a + c), fb = feq[b] + (a - c);
         if constexpr (FORCED) {
           const T sp = T(0.25) * (T(1) + kp) * (S[i] + S[b]);
           const T sm = T(0.25) * (T(1) + km) * (S[i] - S[b]);
