@@ -455,6 +455,77 @@ void launch_inplace(const StepArgs& a, const Rates<T>& keep, const dim3& grid,
   }
 }
 
+// In-place step for FP16 / BF16 delta storage with even Nx: two cells (x,
+// x + 1) per thread on packed FP32 pairs, the arithmetic of k_pull2 over the
+// addressing of k_inplace.  An element offset of 0 along x keeps the pair's
+// access one aligned 4-byte access; -1 or +1 splits it into two 2-byte
+// accesses, of which the one at the row's end wraps.
+template <int ST, class S, int SPACE, bool REG, int MODE>
+__global__ void LBM_PULL2_BOUNDS k_inplace2(const __grid_constant__ InPlacePtrs<S> P, Geo g,
+                                            Rates<P2> keep) {
+  constexpr bool REV = (LBM_INPLACE_REV_MASK >> MODE) & 1;
+  const int bx = REV ? int(gridDim.x) - 1 - int(blockIdx.x) : int(blockIdx.x);
+  const int x = 2 * (bx * LBM_BX + threadIdx.x);
+  if (x >= g.nx) return;
+  const int y = REV ? g.ny - 1 - int(blockIdx.y) : int(blockIdx.y);
+  const int z = REV ? g.nz - 1 - int(blockIdx.z) : int(blockIdx.z);
+  const int c = (z * g.ny + y) * g.nx + x;
+  const int nxy = g.nx * g.ny;
+  const int wx0 = x == 0 ? g.nx : 0;           // cell x at offset -1
+  const int wx1 = x + 2 == g.nx ? -g.nx : 0;   // cell x + 1 at offset +1
+  const int wyp = y == 0 ? nxy : 0, wym = y == g.ny - 1 ? -nxy : 0;
+  const int wzp = z == 0 ? int(g.N) : 0, wzm = z == g.nz - 1 ? -int(g.N) : 0;
+  auto wyz = [&](int oy, int oz) {
+    return (oy < 0 ? wyp : (oy > 0 ? wym : 0)) + (oz < 0 ? wzp : (oz > 0 ? wzm : 0));
+  };
+  P2 f[q_of(ST)];
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    using Mp = InPlaceMap<ST, MODE, i>;
+    const S* p = P.rd[i] + (c + wyz(Mp::ry, Mp::rz));
+    P2 v;
+    if constexpr (Mp::rx == 0) v = Pack<S>::load2(p);
+    else if constexpr (Mp::rx < 0) v = Pack<S>::load11(p + wx0, p + 1);
+    else v = Pack<S>::load11(p, p + 1 + wx1);
+    f[i] = v * P2(1.0f / float(1u << scale_exp(ST, i)));
+  });
+  // the backward transform leaves population i multiplied by 2^|xi_i|^2;
+  // the storage scale 2^s_i absorbs it exactly
+  collide<ST, P2, SPACE, REG, true>(f, keep);
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    using Mp = InPlaceMap<ST, MODE, i>;
+    constexpr int k = vel(ST, i, 0) * vel(ST, i, 0) + vel(ST, i, 1) * vel(ST, i, 1) +
+                      vel(ST, i, 2) * vel(ST, i, 2);
+    const P2 v = f[i] * P2(float(1u << (scale_exp(ST, i) - k)));
+    S* p = P.wr[i] + (c + wyz(Mp::wy, Mp::wz));
+    if constexpr (Mp::wx == 0) Pack<S>::store2(p, v);
+    else if constexpr (Mp::wx < 0) Pack<S>::store11(p + wx0, p + 1, v);
+    else Pack<S>::store11(p, p + 1 + wx1, v);
+  });
+}
+
+template <int ST, class S, int SPACE, bool REG>
+void launch_inplace2(const StepArgs& a, const Rates<P2>& keep) {
+  S* buf = (S*)a.dst;
+  const dim3 grid2((a.g.nx / 2 + LBM_BX - 1) / LBM_BX, a.g.ny, a.g.nz);
+  auto go = [&](auto mode_tag) {
+    constexpr int MODE = decltype(mode_tag)::value;
+    k_inplace2<ST, S, SPACE, REG, MODE>
+        <<<grid2, LBM_BX, 0, a.stream>>>(inplace_ptrs<ST, MODE>(buf, a.g), a.g, keep);
+  };
+  switch (a.mode) {
+    case MODE_AA_EVEN: go(std::integral_constant<int, MODE_AA_EVEN>{}); break;
+    case MODE_AA_ODD: go(std::integral_constant<int, MODE_AA_ODD>{}); break;
+    case MODE_ET_EVEN: go(std::integral_constant<int, MODE_ET_EVEN>{}); break;
+    case MODE_ET_ODD: go(std::integral_constant<int, MODE_ET_ODD>{}); break;
+    case MODE_EPULL_EVEN: go(std::integral_constant<int, MODE_EPULL_EVEN>{}); break;
+    case MODE_EPULL_ODD: go(std::integral_constant<int, MODE_EPULL_ODD>{}); break;
+    case MODE_EPUSH_EVEN: go(std::integral_constant<int, MODE_EPUSH_EVEN>{}); break;
+    default: go(std::integral_constant<int, MODE_EPUSH_ODD>{}); break;
+  }
+}
+
 // ------------------------------------------------------ read-out kernels
 // canonical populations -> FP64 SoA df[i * N + c] and / or macroscopic
 // Slab of a read-out / set-up launch: block (bx, by, bz) covers row
@@ -797,8 +868,18 @@ void launch_step_typed(const StepArgs& a) {
     }
     k_pull<ST, S, T, SPACE, REG><<<pull_grid(a.g), LBM_PULL_BX, 0, a.stream>>>(P, a.g, keep);
   }
-  else
+  else {
+    // FP16 / BF16 with even Nx: the packed two-cells-per-thread kernel
+    if constexpr (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) {
+      if (a.g.nx % 2 == 0) {
+        Rates<P2> k2;
+        for (int k = 0; k < 6; ++k) k2.om[k] = P2(1.0 - a.rates[k]);
+        launch_inplace2<ST, S, SPACE, REG>(a, k2);
+        return;
+      }
+    }
     launch_inplace<ST, S, T, SPACE, REG>(a, keep, grid);
+  }
 }
 
 template <int ST, class S, class T>

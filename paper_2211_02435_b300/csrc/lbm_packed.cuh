@@ -99,6 +99,10 @@ struct Pack<__half> {
   P2F static void store2(__half* p, P2 v) {
     *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v);
   }
+  P2F static void store11(__half* p0, __half* p1, P2 v) {
+    *p0 = __float2half_rn(v.v.x);
+    *p1 = __float2half_rn(v.v.y);
+  }
 };
 template <>
 struct Pack<__nv_bfloat16> {
@@ -110,6 +114,10 @@ struct Pack<__nv_bfloat16> {
   }
   P2F static void store2(__nv_bfloat16* p, P2 v) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v.v);
+  }
+  P2F static void store11(__nv_bfloat16* p0, __nv_bfloat16* p1, P2 v) {
+    *p0 = __float2bfloat16_rn(v.v.x);
+    *p1 = __float2bfloat16_rn(v.v.y);
   }
 };
 

@@ -2,8 +2,9 @@
 times, on sampled outputs the FP64 oracle computes one by one.
 
 * D3Q27 cumulant (R-) on the 512^3 Taylor-Green vortex u0 = 0.05 with 1e-3
-  noise: FP32 storage with pull streaming (the headline kernel), the four
-  in-place patterns, and FP16 / BF16 delta storage (the packed kernel).
+  noise: FP32 storage with pull streaming (the headline kernel) and the four
+  in-place patterns, and FP16 / BF16 delta storage (the packed kernels),
+  pull and in place.
 * D3Q27 central moments (R-) on the 512^3 8-mode Fourier flow, FP16 / BF16
   delta storage.
 * The 4096-domain D3Q19 O-MRT ensemble with the autotuned launch shape.
@@ -129,17 +130,28 @@ def test_fp32_cumulant_512_sampled(tgv_fields, streaming):
         assert np.array_equal(df, _fp32_pull["df"])
 
 
+_half_pull = {}
+
+
+@pytest.mark.parametrize("streaming", L.STREAMING_PATTERNS,
+                         ids=["pull", "aa", "et", "epull", "epush"])
 @pytest.mark.parametrize("storage,p", [(L.STORE_F16_DELTA, 10), (L.STORE_BF16_DELTA, 7)],
                          ids=["f16", "bf16"])
-def test_half_cumulant_512_sampled(tgv_fields, storage, p):
-    """Packed FP16 / BF16 kernel: within (n + 1) 2^-(p+1) of max |df| (one
-    rounding of each scaled deviation per store, the initial encode included)."""
+def test_half_cumulant_512_sampled(tgv_fields, storage, p, streaming):
+    """Packed FP16 / BF16 kernels (pull and in place): within (n + 1)
+    2^-(p+1) of max |df| (one rounding of each scaled deviation per store,
+    the initial encode included); the in-place patterns equal pull bit for
+    bit."""
     cells = sample_cells()
-    df, uu = run_case(L.SPACE_CUMULANT, storage, L.PULL, *tgv_fields, cells)
+    df, uu = run_case(L.SPACE_CUMULANT, storage, streaming, *tgv_fields, cells)
     ref_df, ref_u = tgv_reference(tgv_fields, cells)
     bound = (STEPS + 1) * 2.0 ** -(p + 1)
     assert rel_linf(df, ref_df) < bound
     assert rel_linf(uu, ref_u) < 4 * bound
+    if streaming == L.PULL:
+        _half_pull[storage] = df
+    elif storage in _half_pull:
+        assert np.array_equal(df, _half_pull[storage])
 
 
 @pytest.mark.parametrize("storage,p", [(L.STORE_F16_DELTA, 10), (L.STORE_BF16_DELTA, 7)],

@@ -274,13 +274,14 @@ def test_taylor_green_config_d3q19_omrt_fp64():
 EVEN_DIMS = {0: (134, 37, 1), 1: (134, 6, 5), 2: (134, 6, 5)}
 
 
+@pytest.mark.parametrize("streaming", L.STREAMING_PATTERNS)
 @pytest.mark.parametrize("storage,p", [(L.STORE_F16_DELTA, 10), (L.STORE_BF16_DELTA, 7)])
 @pytest.mark.parametrize("method", METHODS, ids=lambda m: f"sp{m[0]}eq{m[1]}reg{int(m[2])}")
 @pytest.mark.parametrize("st", [0, 1, 2], ids=["D2Q9", "D3Q19", "D3Q27"])
-def test_packed_half_kernel_error_bound(st, method, storage, p):
-    """Even Nx routes FP16 / BF16 pull steps to the two-cells-per-thread
-    kernel with packed FP32 arithmetic; same rounding bound as the scalar
-    kernel (see test_half_storage_error_bound)."""
+def test_packed_half_kernel_error_bound(st, method, storage, p, streaming):
+    """Even Nx routes FP16 / BF16 steps, pull and in place, to the
+    two-cells-per-thread kernels with packed FP32 arithmetic; same rounding
+    bound as the scalar kernel (see test_half_storage_error_bound)."""
     space, eq, reg = method
     dims = EVEN_DIMS[st]
     d = 2 if st == 0 else 3
@@ -292,9 +293,29 @@ def test_packed_half_kernel_error_bound(st, method, storage, p):
     pert = I.random_deviations(len(w), int(np.prod(dims)), 2e-3, seed=12)
     df0 = df0 + (w[:, None] * pert).reshape(df0.shape)
     n = 4
-    with L.Lattice(st, space, eq, storage, L.PULL, rates_of(space, reg), dims) as lat:
+    with L.Lattice(st, space, eq, storage, streaming, rates_of(space, reg), dims) as lat:
         lat.set_populations(df0)
         lat.step(n)
         got = lat.get_populations()
     ref = O.step(m, dims, df0, n)
     assert rel_linf(got, ref) < (n + 1) * 2.0 ** -(p + 1)
+
+
+@pytest.mark.parametrize("storage", [L.STORE_F16_DELTA, L.STORE_BF16_DELTA], ids=["f16", "bf16"])
+@pytest.mark.parametrize("st", [0, 1, 2], ids=["D2Q9", "D3Q19", "D3Q27"])
+def test_packed_half_pull_and_in_place_are_bitwise_identical(st, storage):
+    """The packed in-place kernel runs the packed pull kernel's arithmetic:
+    identical FP16 / BF16 states after odd and even step counts."""
+    space, eq, reg = L.SPACE_CUMULANT, L.EQ_ABSOLUTE, True
+    dims = EVEN_DIMS[st]
+    rho, u = I.taylor_green(dims, 0.05, d=2 if st == 0 else 3)
+    u = I.add_uniform_noise(u, 1e-3, seed=11)
+    for n in (4, 5):
+        out = []
+        for streaming in L.STREAMING_PATTERNS:
+            with L.Lattice(st, space, eq, storage, streaming, rates_of(space, reg), dims) as lat:
+                lat.init_velocity(rho.reshape(-1), u.reshape(-1))
+                lat.step(n)
+                out.append(lat.get_populations())
+        for k in range(1, len(out)):
+            assert np.array_equal(out[0], out[k]), (n, k)
