@@ -389,17 +389,19 @@ def run_cuda(args):
                            "u_rel_linf_vs_f64": uerr(uu),
                            "vs_f32_mlups": (N * args.steps / (ms / 1e3)) / (N * args.steps / (ms32 / 1e3))}
             del uu
-        # in-place patterns (one buffer), FP32, even number of steps
+        # in-place patterns (one buffer), FP32 and FP16 delta, even number of steps
         st_ip = 2 * (args.steps // 2)
-        for name in ("aa", "et", "epull", "epush"):
-            lat, ms = time_form(L.STORE_F32, st_ip, args.warmup + args.warmup % 2,
-                                streaming=STREAMINGS[name])
-            lat.close()
-            del lat
-            ach = BYTES_PER_CELL["f32"] * N / (ms / 1e3 / st_ip) / 1e9
-            forms[f"f32_{name}"] = {"mlups": N * st_ip / (ms / 1e3) / 1e6, "achieved_gbs": ach,
-                                    "roofline_frac": ach / peak, "buffers": 1,
-                                    "note": "same per-cell arithmetic as pull (bitwise equal states)"}
+        for key, store in (("f32", L.STORE_F32), ("f16_delta", L.STORE_F16_DELTA)):
+            for name in ("aa", "et", "epull", "epush"):
+                lat, ms = time_form(store, st_ip, args.warmup + args.warmup % 2,
+                                    streaming=STREAMINGS[name])
+                lat.close()
+                del lat
+                ach = BYTES_PER_CELL[key] * N / (ms / 1e3 / st_ip) / 1e9
+                forms[f"{key}_{name}"] = {
+                    "mlups": N * st_ip / (ms / 1e3) / 1e6, "achieved_gbs": ach,
+                    "roofline_frac": ach / peak, "buffers": 1,
+                    "note": "same per-cell arithmetic as pull (bitwise equal states)"}
         # body force (Guo): uniform, and a per-cell field (+12 B/cell of reads)
         for name, force, bpc in (
                 ("f32_force_uniform", np.array([1e-6, 0.0, 0.0]), BYTES_PER_CELL["f32"]),
