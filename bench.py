@@ -428,22 +428,22 @@ def run_cuda(args):
         u_out = torch.empty(3 * N, dtype=torch.float64).pin_memory()
         lat = L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F32, L.PULL, rates,
                         (n, n, n), stream=stream)
-        lat.init_velocity(rho_p.numpy(), u_p.numpy())  # warm the path once
-        lat.step(args.warmup)
+        # one call: host fields in, the steps, host fields out; the library
+        # overlaps the copies and the steps of different slabs of z-planes
+        lat.run_host(rho_p.numpy(), u_p.numpy(), args.warmup, rho_out.numpy(), u_out.numpy())
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
-        lat.init_velocity(rho_p.numpy(), u_p.numpy())
-        lat.step(args.steps)
-        lat.macroscopic(rho_out.numpy(), u_out.numpy())
+        lat.run_host(rho_p.numpy(), u_p.numpy(), args.steps, rho_out.numpy(), u_out.numpy())
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         lat.close()
         e2e = {"value": job_mlups(world, N, args.steps, dt), "unit": UNIT,
                "h2d_bytes_per_step": 4 * N * 8 / args.steps,
                "d2h_bytes_per_step": 4 * N * 8 / args.steps,
-               "job": f"host rho,u (FP64, pinned) -> init -> {args.steps} steps -> host rho,u"}
+               "job": f"lbm_run_host: host rho,u (FP64, pinned) -> init -> {args.steps} steps "
+                      "-> host rho,u, pipelined by slabs of z-planes"}
 
     batched = None
     if not args.no_batched:

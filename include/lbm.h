@@ -223,6 +223,23 @@ int lbm_step(lbm_ctx* ctx, int64_t n);
  * Either pointer may be NULL.  Errors: INVALID, CUDA. */
 int lbm_macroscopic(lbm_ctx* ctx, double* rho, double* u, int on_device);
 
+/* One job from host memory to host memory: f(0) from rho[N] (NULL: 1) and
+ * u[D*N] as lbm_init_velocity, n >= 0 steps as lbm_step, then rho_out[N]
+ * and u_out[D*N] of f(n) as lbm_macroscopic (either may be NULL), all host
+ * FP64 arrays in the field layout above; synchronises.  The result equals
+ * that sequence bit for bit.  With pull streaming, zero-centered storage,
+ * deviation arithmetic, no body force or closure, the direct step kernel
+ * and Nz >= 3, the job runs pipelined: the lattice is cut into `slabs` runs
+ * of z-planes (0: about 64 MB of rho and u each, at least 3; capped at Nz)
+ * and the host-to-device copies, the steps (Eq. 2.1, a slab taking step
+ * k + 1 once both neighbouring slabs have taken step k) and the
+ * device-to-host copies of different slabs overlap, on two copy streams
+ * the library creates for the call and the context's stream.  Otherwise
+ * (or with fewer than 3 slabs) the three calls run one after the other.
+ * Errors: INVALID, OOM, CUDA. */
+int lbm_run_host(lbm_ctx* ctx, const double* rho, const double* u, int64_t n,
+                 double* rho_out, double* u_out, int slabs);
+
 /* Read / write the canonical zero-centered populations df[q*N] of f(n)
  * in FP64 (writing encodes them into the storage type and resets the AA
  * parity; the step counter is kept).  Errors: INVALID, CUDA. */

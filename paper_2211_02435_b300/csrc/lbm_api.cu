@@ -3,9 +3,11 @@
 // the per-(stencil, storage) kernel instantiations.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "lbm.h"
 #include "lbm_internal.h"
@@ -680,8 +682,8 @@ static int read_status(lbm_ctx* c) {
   return st ? LBM_ERR_TIMEOUT : LBM_OK;
 }
 
-int lbm_step(lbm_ctx* c, int64_t n) {
-  if (!c || n < 0) return LBM_ERR_INVALID;
+// the step launch arguments of a context (every slab / the whole lattice)
+static StepArgs step_args(const lbm_ctx* c) {
   StepArgs a;
   std::memset(&a, 0, sizeof(a));
   a.g = c->g;
@@ -709,6 +711,12 @@ int lbm_step(lbm_ctx* c, int64_t n) {
   a.swe_g = c->swe_g;
   if (c->swe_g > 0.0) a.reg = 0;  // shallow water: the general instantiation
   a.stream = c->stream;
+  return a;
+}
+
+int lbm_step(lbm_ctx* c, int64_t n) {
+  if (!c || n < 0) return LBM_ERR_INVALID;
+  StepArgs a = step_args(c);
   const step_fn fn = kStep[c->p.stencil][c->p.storage];
   for (int64_t s = 0; s < n; ++s) {
     if (c->p.streaming == LBM_PULL) {
@@ -791,6 +799,218 @@ int lbm_macroscopic(lbm_ctx* c, double* rho, double* u, int on_device) {
 int lbm_get_populations(lbm_ctx* c, double* df, int on_device) {
   if (!c || !df) return LBM_ERR_INVALID;
   return gather(c, df, nullptr, nullptr, on_device);
+}
+
+// ------------------------------------------- pipelined host job (run_host)
+// Set-up from host fields, n pull steps and read-out to host as one job:
+// the lattice is cut into S slabs of z-planes, and the copies in, the steps
+// and the copies out of different slabs overlap as a wavefront.  Slab s may
+// take step k + 1 once its neighbours s - 1 and s + 1 (periodic) have
+// taken step k: step k + 1 reads their post-collision values of step k and
+// overwrites the buffer their step k read.  Step 1 needs only the slab's
+// own set-up (the pull layout stores a cell's initial populations where
+// that cell's first gather reads them).  A slab is read out once it and
+// both neighbours have taken all n steps.  The order is fixed on the host
+// in advance (greedy: after each arriving slab, every step that has become
+// possible); the context's stream runs it in order, and events tie it to
+// one copy stream per direction with a ring of staging buffers each.
+namespace {
+
+constexpr int RUN_RING = 4;
+
+bool run_pipelined_ok(const lbm_ctx* c) {
+  return c->p.streaming == LBM_PULL && c->p.storage != LBM_STORE_F64_ABSOLUTE &&
+         c->p.arithmetic == LBM_ARITH_DEVIATION && !c->force_mode && !c->closure &&
+         c->swe_g == 0.0 && !use_staged(c) && c->g.nz >= 3;
+}
+
+}  // namespace
+
+int lbm_run_host(lbm_ctx* c, const double* rho, const double* u, int64_t n, double* rho_out,
+                 double* u_out, int slabs) {
+  if (!c || !u || n < 0 || slabs < 0) return LBM_ERR_INVALID;
+  const size_t N = size_t(c->g.N);
+  const int nz = c->g.nz, d = c->d;
+  const int64_t plane = int64_t(c->g.nx) * c->g.ny;
+  // slab count: about 64 MB of (rho, u) per slab, at least 3
+  int S = slabs;
+  if (S == 0) {
+    const size_t per = size_t(plane) * (1 + d) * sizeof(double);
+    S = int((size_t(nz) * per + IO_SLAB_BYTES - 1) / IO_SLAB_BYTES);
+  }
+  if (S > nz) S = nz;
+  if (!run_pipelined_ok(c) || S < 3) {  // one job after the other
+    int rc = lbm_init_velocity(c, rho, u, 0);
+    if (rc == LBM_OK) rc = lbm_step(c, n);
+    if (rc == LBM_OK && (rho_out || u_out)) rc = lbm_macroscopic(c, rho_out, u_out, 0);
+    return rc;
+  }
+  std::vector<int> z0(S + 1);
+  for (int k = 0; k <= S; ++k) z0[k] = int(int64_t(nz) * k / S);
+  int maxp = 0;
+  for (int k = 0; k < S; ++k) maxp = std::max(maxp, z0[k + 1] - z0[k]);
+  const int64_t cap = int64_t(maxp) * plane;  // cells of the largest slab
+  const int ncomp = 1 + d;
+  double* ring_in[RUN_RING] = {nullptr};
+  double* ring_out[RUN_RING] = {nullptr};
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  std::vector<cudaEvent_t> ev;
+  auto new_event = [&]() {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return (cudaEvent_t) nullptr;
+    ev.push_back(e);
+    return e;
+  };
+  int rc = LBM_OK;
+  bool ok = cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking) == cudaSuccess;
+  for (int r = 0; r < RUN_RING && ok; ++r)
+    ok = cudaMalloc((void**)&ring_in[r], size_t(cap) * ncomp * sizeof(double)) == cudaSuccess &&
+         cudaMalloc((void**)&ring_out[r], size_t(cap) * ncomp * sizeof(double)) == cudaSuccess;
+  std::vector<cudaEvent_t> arrived(S), in_free(RUN_RING), out_ready(S), out_free(RUN_RING);
+  for (int k = 0; k < S && ok; ++k) ok = (arrived[k] = new_event()) && (out_ready[k] = new_event());
+  for (int r = 0; r < RUN_RING && ok; ++r) ok = (in_free[r] = new_event()) && (out_free[r] = new_event());
+  cudaEvent_t start = ok ? new_event() : nullptr;
+  ok = ok && start;
+  if (!ok) {
+    cudaGetLastError();
+    rc = LBM_ERR_OOM;
+  }
+  std::vector<int> step(S, -1);       // steps taken by slab (-1: not set up)
+  std::vector<char> emitted(S, 0);    // read-out issued
+  std::vector<int> in_use(RUN_RING, -1), out_use(RUN_RING, -1);
+  const int cur0 = c->cur;
+  StepArgs sa = step_args(c);
+  sa.mode = lbm::MODE_PULL;
+  const step_fn fn = kStep[c->p.stencil][c->p.storage];
+  int out_count = 0;
+  auto slab_cells = [&](int k) { return int64_t(z0[k + 1] - z0[k]) * plane; };
+  auto set_slab_aux = [&](AuxArgs& a, int k) {
+    a.z0 = z0[k];
+    a.nzc = z0[k + 1] - z0[k];
+    a.c0 = int64_t(z0[k]) * plane;
+    a.stride = slab_cells(k);
+  };
+  // read-out of slab k into ring slot out_count % RUN_RING, then its copy
+  auto emit = [&](int k) {
+    const int r = out_count % RUN_RING;
+    const int64_t cells = slab_cells(k), c0 = int64_t(z0[k]) * plane;
+    if (out_count >= RUN_RING) ok = ok && cudaStreamWaitEvent(c->stream, out_free[r], 0) == cudaSuccess;
+    AuxArgs a = aux_base(c, lbm::AUX_GATHER);
+    a.buf = c->buf[(cur0 + n) % 2];
+    a.gather_mode = G_PULL;
+    set_slab_aux(a, k);
+    a.rho = rho_out ? ring_out[r] : nullptr;
+    a.u = u_out ? ring_out[r] + cells : nullptr;
+    if (ok && (rho_out || u_out)) {
+      kAux[c->p.stencil][c->p.storage](a);
+      ok = cudaGetLastError() == cudaSuccess;
+    }
+    ok = ok && cudaEventRecord(out_ready[k], c->stream) == cudaSuccess;
+    ok = ok && cudaStreamWaitEvent(s_out, out_ready[k], 0) == cudaSuccess;
+    if (rho_out)
+      ok = ok && cudaMemcpyAsync(rho_out + c0, ring_out[r], size_t(cells) * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s_out) == cudaSuccess;
+    if (u_out)
+      for (int j = 0; j < d; ++j)
+        ok = ok && cudaMemcpyAsync(u_out + size_t(j) * N + c0, ring_out[r] + (1 + j) * cells,
+                                   size_t(cells) * sizeof(double), cudaMemcpyDeviceToHost,
+                                   s_out) == cudaSuccess;
+    ok = ok && cudaEventRecord(out_free[r], s_out) == cudaSuccess;
+    emitted[k] = 1;
+    ++out_count;
+  };
+  // every step (and read-out) that has become possible, in slab order, until none
+  auto advance = [&]() {
+    bool any = true;
+    while (any && ok) {
+      any = false;
+      for (int k = 0; k < S && ok; ++k) {
+        const int km = (k + S - 1) % S, kp = (k + 1) % S;
+        const int t = step[k];
+        if (t >= 0 && t < n && (t == 0 || (step[km] >= t && step[kp] >= t))) {
+          sa.src = c->buf[(cur0 + t) % 2];
+          sa.dst = c->buf[(cur0 + t + 1) % 2];
+          sa.z0 = z0[k];
+          sa.nzc = z0[k + 1] - z0[k];
+          fn(sa);
+          ok = cudaGetLastError() == cudaSuccess;
+          step[k] = t + 1;
+          any = true;
+        }
+      }
+      for (int k = 0; k < S && ok; ++k) {
+        const int km = (k + S - 1) % S, kp = (k + 1) % S;
+        if (!emitted[k] && step[k] == n && step[km] == n && step[kp] == n) {
+          emit(k);
+          any = true;
+        }
+      }
+    }
+  };
+  // copy of slab k into ring slot k % RUN_RING; a slot is refilled only after
+  // the set-up of the slab before in it, whose event is recorded first (a
+  // wait on an event not yet recorded would not wait)
+  auto copy_in = [&](int k) {
+    const int r = k % RUN_RING;
+    const int64_t cells = slab_cells(k), c0 = int64_t(z0[k]) * plane;
+    if (k >= RUN_RING) ok = ok && cudaStreamWaitEvent(s_in, in_free[r], 0) == cudaSuccess;
+    if (rho)
+      ok = ok && cudaMemcpyAsync(ring_in[r], rho + c0, size_t(cells) * sizeof(double),
+                                 cudaMemcpyHostToDevice, s_in) == cudaSuccess;
+    for (int j = 0; j < d; ++j)
+      ok = ok && cudaMemcpyAsync(ring_in[r] + (1 + j) * cells, u + size_t(j) * N + c0,
+                                 size_t(cells) * sizeof(double), cudaMemcpyHostToDevice,
+                                 s_in) == cudaSuccess;
+    ok = ok && cudaEventRecord(arrived[k], s_in) == cudaSuccess;
+  };
+  if (ok) {
+    // the copies start after the work already queued on the context's stream
+    ok = cudaEventRecord(start, c->stream) == cudaSuccess &&
+         cudaStreamWaitEvent(s_in, start, 0) == cudaSuccess &&
+         cudaStreamWaitEvent(s_out, start, 0) == cudaSuccess;
+    for (int k = 0; k < S && k < RUN_RING; ++k) copy_in(k);
+    // the compute order: set up each arriving slab, then every step it enables
+    for (int k = 0; k < S && ok; ++k) {
+      const int r = k % RUN_RING;
+      ok = cudaStreamWaitEvent(c->stream, arrived[k], 0) == cudaSuccess;
+      AuxArgs a = aux_base(c, lbm::AUX_SCATTER);
+      a.buf = c->buf[cur0];
+      a.gather_mode = G_PULL;
+      set_slab_aux(a, k);
+      a.rho_in = rho ? ring_in[r] : nullptr;
+      a.u_in = ring_in[r] + slab_cells(k);
+      if (ok) {
+        kAux[c->p.stencil][c->p.storage](a);
+        ok = cudaGetLastError() == cudaSuccess;
+      }
+      ok = ok && cudaEventRecord(in_free[r], c->stream) == cudaSuccess;
+      if (k + RUN_RING < S) copy_in(k + RUN_RING);
+      step[k] = 0;
+      advance();
+    }
+    advance();
+    for (int k = 0; k < S && ok; ++k)
+      if (!emitted[k]) ok = false;  // the schedule always completes
+  }
+  if (s_in && cudaStreamSynchronize(s_in) != cudaSuccess) ok = false;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) ok = false;
+  if (s_out && cudaStreamSynchronize(s_out) != cudaSuccess) ok = false;
+  if (rc == LBM_OK && !ok) rc = LBM_ERR_CUDA;
+  if (rc == LBM_OK) {
+    c->t = n;
+    c->cur = int((cur0 + n) % 2);
+    rc = read_status(c);
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  for (int r = 0; r < RUN_RING; ++r) {
+    if (ring_in[r]) cudaFree(ring_in[r]);
+    if (ring_out[r]) cudaFree(ring_out[r]);
+  }
+  if (s_in) cudaStreamDestroy(s_in);
+  if (s_out) cudaStreamDestroy(s_out);
+  return rc;
 }
 
 int lbm_invariants(lbm_ctx* c, double out[8]) {

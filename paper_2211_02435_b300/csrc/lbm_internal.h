@@ -59,6 +59,8 @@ struct StepArgs {
   double force[3];          // uniform body force
   const void* force_field;  // per-cell force [D][N] in the compute type (FORCE_FIELD)
   double swe_g;             // > 0: shallow-water method with this gravity (D2Q9)
+  // pull steps over a slab of z-planes [z0, z0 + nzc) only (nzc = 0: all)
+  int z0, nzc;
   cudaStream_t stream;
 };
 

@@ -193,10 +193,11 @@ struct PullPtrs {
 // pull: read f_i from x - xi_i of src, collide, write f*_i at x of dst
 template <int ST, class S, class T, int SPACE, bool REG, int FORM = FORM_DEV, int FORCE = FORCE_NONE>
 __global__ void __launch_bounds__(LBM_PULL_BX) k_pull(const __grid_constant__ PullPtrs<S> P, Geo g,
-                                                      Rates<T> keep, ForceArg<T> fa = {}) {
+                                                      Rates<T> keep, ForceArg<T> fa = {},
+                                                      int z0 = 0) {
   const int x = blockIdx.x * LBM_PULL_BX + threadIdx.x;
   if (x >= g.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = blockIdx.y, z = z0 + int(blockIdx.z);
   const int c = (z * g.ny + y) * g.nx + x;
   const int nxy = g.nx * g.ny;
   // wrap corrections for a read at x - xi (xi = +1 reads x-1, -1 reads x+1)
@@ -282,10 +283,10 @@ __global__ void __launch_bounds__(LBM_BX) k_scatter_swe(AbsF64* buf, Geo g, cons
 // are aligned 2-element stores.
 template <int ST, class S, int SPACE, bool REG>
 __global__ void LBM_PULL2_BOUNDS k_pull2(const __grid_constant__ PullPtrs<S> P, Geo g,
-                                                  Rates<P2> keep) {
+                                                  Rates<P2> keep, int z0 = 0) {
   const int x = 2 * (blockIdx.x * LBM_BX + threadIdx.x);
   if (x >= g.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = blockIdx.y, z = z0 + int(blockIdx.z);
   const int c = (z * g.ny + y) * g.nx + x;
   const int nxy = g.nx * g.ny;
   const int wxp0 = x == 0 ? g.nx : 0;           // cell x reading x - 1
@@ -765,8 +766,8 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS)
 
 // --------------------------------------------------------------- launchers
 inline dim3 step_grid(const Geo& g) { return dim3((g.nx + LBM_BX - 1) / LBM_BX, g.ny, g.nz); }
-inline dim3 pull_grid(const Geo& g) {
-  return dim3((g.nx + LBM_PULL_BX - 1) / LBM_PULL_BX, g.ny, g.nz);
+inline dim3 pull_grid(const Geo& g, int nzc = 0) {
+  return dim3((g.nx + LBM_PULL_BX - 1) / LBM_PULL_BX, g.ny, nzc > 0 ? nzc : g.nz);
 }
 
 // forced steps (FP32 / FP64 storage, deviation arithmetic)
@@ -849,10 +850,12 @@ void launch_step_typed(const StepArgs& a) {
         return;
       }
     }
+    // a.nzc > 0: the slab of z-planes [a.z0, a.z0 + a.nzc) only
     if constexpr ((std::is_same<S, float>::value || std::is_same<S, double>::value) &&
                   !(REG && (SPACE == SP_CENTRAL || SPACE == SP_CUMULANT))) {
       if (a.form == FORM_DISC) {
-        k_pull<ST, S, T, SPACE, REG, FORM_DISC><<<pull_grid(a.g), LBM_PULL_BX, 0, a.stream>>>(P, a.g, keep);
+        k_pull<ST, S, T, SPACE, REG, FORM_DISC><<<pull_grid(a.g, a.nzc), LBM_PULL_BX, 0, a.stream>>>(
+            P, a.g, keep, ForceArg<T>{}, a.z0);
         return;
       }
     }
@@ -861,12 +864,13 @@ void launch_step_typed(const StepArgs& a) {
       if (a.g.nx % 2 == 0) {
         Rates<P2> k2;
         for (int k = 0; k < 6; ++k) k2.om[k] = P2(1.0 - a.rates[k]);
-        const dim3 grid2((a.g.nx / 2 + LBM_BX - 1) / LBM_BX, a.g.ny, a.g.nz);
-        k_pull2<ST, S, SPACE, REG><<<grid2, LBM_BX, 0, a.stream>>>(P, a.g, k2);
+        const dim3 grid2((a.g.nx / 2 + LBM_BX - 1) / LBM_BX, a.g.ny, a.nzc > 0 ? a.nzc : a.g.nz);
+        k_pull2<ST, S, SPACE, REG><<<grid2, LBM_BX, 0, a.stream>>>(P, a.g, k2, a.z0);
         return;
       }
     }
-    k_pull<ST, S, T, SPACE, REG><<<pull_grid(a.g), LBM_PULL_BX, 0, a.stream>>>(P, a.g, keep);
+    k_pull<ST, S, T, SPACE, REG><<<pull_grid(a.g, a.nzc), LBM_PULL_BX, 0, a.stream>>>(
+        P, a.g, keep, ForceArg<T>{}, a.z0);
   }
   else {
     // FP16 / BF16 with even Nx: the packed two-cells-per-thread kernel

@@ -82,6 +82,7 @@ def lib():
         L.lbm_init_velocity.argtypes = [vp, vp, vp, c_int]
         L.lbm_step.argtypes = [vp, i64]
         L.lbm_macroscopic.argtypes = [vp, vp, vp, c_int]
+        L.lbm_run_host.argtypes = [vp, vp, vp, i64, vp, vp, c_int]
         L.lbm_get_populations.argtypes = [vp, vp, c_int]
         L.lbm_set_populations.argtypes = [vp, vp, c_int]
         L.lbm_invariants.argtypes = [vp, d]
@@ -261,6 +262,18 @@ class Lattice:
             nx, ny, nz = self.dims
             return rho.reshape(nz, ny, nx), u.reshape(self.d, nz, ny, nx)
         return rho, u
+
+    def run_host(self, rho, u, n, rho_out=None, u_out=None, slabs=0):
+        """lbm_run_host: host fields in, n steps, host fields out, pipelined
+        by slabs of z-planes (numpy float64 arrays; rho / outputs may be None)."""
+        for a in (rho, u, rho_out, u_out):
+            if a is not None and not isinstance(a, np.ndarray):
+                raise TypeError("lbm_run_host takes host (numpy) arrays")
+        pr, _ = _ptr(rho, self.N)
+        pu, _ = _ptr(u, self.d * self.N)
+        po, _ = _ptr(rho_out, self.N, True)
+        pv, _ = _ptr(u_out, self.d * self.N, True)
+        _check(lib().lbm_run_host(self._h, pr, pu, int(n), po, pv, int(slabs)), "lbm_run_host")
 
     def get_populations(self, out=None):
         alloc = out is None
