@@ -292,6 +292,7 @@ void lbm_destroy(lbm_ctx* c) {
     if (c->io_buf[b]) cudaFree(c->io_buf[b]);
     if (c->buf[b]) cudaFree(c->buf[b]);
   }
+  if (c->run_buf) cudaFree(c->run_buf);
   if (c->part) cudaFree(c->part);
   if (c->closure) lbm::free_closure(c->closure);
   if (c->force_field) cudaFree(c->force_field);
@@ -816,7 +817,7 @@ int lbm_get_populations(lbm_ctx* c, double* df, int on_device) {
 // one copy stream per direction with a ring of staging buffers each.
 namespace {
 
-constexpr int RUN_RING = 4;
+constexpr int RUN_RING = 4;  // staging slots per direction when memory is short
 
 bool run_pipelined_ok(const lbm_ctx* c) {
   return c->p.streaming == LBM_PULL && c->p.storage != LBM_STORE_F64_ABSOLUTE &&
@@ -851,8 +852,34 @@ int lbm_run_host(lbm_ctx* c, const double* rho, const double* u, int64_t n, doub
   for (int k = 0; k < S; ++k) maxp = std::max(maxp, z0[k + 1] - z0[k]);
   const int64_t cap = int64_t(maxp) * plane;  // cells of the largest slab
   const int ncomp = 1 + d;
-  double* ring_in[RUN_RING] = {nullptr};
-  double* ring_out[RUN_RING] = {nullptr};
+  // one staging slot per slab and direction when the device has room (no
+  // copy or step ever waits for a slot), else a ring of RUN_RING slots
+  size_t free_b = 0, total_b = 0;
+  const size_t slot_b = size_t(cap) * ncomp * sizeof(double);
+  int R = RUN_RING;
+  if (c->run_cap >= 2 * size_t(S) * slot_b ||
+      (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
+       2 * size_t(S) * slot_b + c->run_cap + (size_t(1) << 30) < free_b))
+    R = S;
+  cudaGetLastError();
+  std::vector<double*> ring_in(R, nullptr), ring_out(R, nullptr);
+  // the slots live in one block kept by the context between calls
+  const size_t need = 2 * size_t(R) * slot_b;
+  if (c->run_cap < need) {
+    if (c->run_buf) cudaFree(c->run_buf);
+    c->run_buf = nullptr;
+    c->run_cap = 0;
+    if (cudaMalloc((void**)&c->run_buf, need) != cudaSuccess) {
+      cudaGetLastError();
+      c->run_buf = nullptr;
+      return LBM_ERR_OOM;
+    }
+    c->run_cap = need;
+  }
+  for (int r = 0; r < R; ++r) {
+    ring_in[r] = c->run_buf + size_t(r) * (slot_b / sizeof(double));
+    ring_out[r] = c->run_buf + size_t(R + r) * (slot_b / sizeof(double));
+  }
   cudaStream_t s_in = nullptr, s_out = nullptr;
   std::vector<cudaEvent_t> ev;
   auto new_event = [&]() {
@@ -864,12 +891,9 @@ int lbm_run_host(lbm_ctx* c, const double* rho, const double* u, int64_t n, doub
   int rc = LBM_OK;
   bool ok = cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking) == cudaSuccess;
-  for (int r = 0; r < RUN_RING && ok; ++r)
-    ok = cudaMalloc((void**)&ring_in[r], size_t(cap) * ncomp * sizeof(double)) == cudaSuccess &&
-         cudaMalloc((void**)&ring_out[r], size_t(cap) * ncomp * sizeof(double)) == cudaSuccess;
-  std::vector<cudaEvent_t> arrived(S), in_free(RUN_RING), out_ready(S), out_free(RUN_RING);
+  std::vector<cudaEvent_t> arrived(S), in_free(R), out_ready(S), out_free(R);
   for (int k = 0; k < S && ok; ++k) ok = (arrived[k] = new_event()) && (out_ready[k] = new_event());
-  for (int r = 0; r < RUN_RING && ok; ++r) ok = (in_free[r] = new_event()) && (out_free[r] = new_event());
+  for (int r = 0; r < R && ok; ++r) ok = (in_free[r] = new_event()) && (out_free[r] = new_event());
   cudaEvent_t start = ok ? new_event() : nullptr;
   ok = ok && start;
   if (!ok) {
@@ -878,7 +902,6 @@ int lbm_run_host(lbm_ctx* c, const double* rho, const double* u, int64_t n, doub
   }
   std::vector<int> step(S, -1);       // steps taken by slab (-1: not set up)
   std::vector<char> emitted(S, 0);    // read-out issued
-  std::vector<int> in_use(RUN_RING, -1), out_use(RUN_RING, -1);
   const int cur0 = c->cur;
   StepArgs sa = step_args(c);
   sa.mode = lbm::MODE_PULL;
@@ -891,11 +914,11 @@ int lbm_run_host(lbm_ctx* c, const double* rho, const double* u, int64_t n, doub
     a.c0 = int64_t(z0[k]) * plane;
     a.stride = slab_cells(k);
   };
-  // read-out of slab k into ring slot out_count % RUN_RING, then its copy
+  // read-out of slab k into slot out_count % R, then its copy
   auto emit = [&](int k) {
-    const int r = out_count % RUN_RING;
+    const int r = out_count % R;
     const int64_t cells = slab_cells(k), c0 = int64_t(z0[k]) * plane;
-    if (out_count >= RUN_RING) ok = ok && cudaStreamWaitEvent(c->stream, out_free[r], 0) == cudaSuccess;
+    if (out_count >= R) ok = ok && cudaStreamWaitEvent(c->stream, out_free[r], 0) == cudaSuccess;
     AuxArgs a = aux_base(c, lbm::AUX_GATHER);
     a.buf = c->buf[(cur0 + n) % 2];
     a.gather_mode = G_PULL;
@@ -948,13 +971,13 @@ int lbm_run_host(lbm_ctx* c, const double* rho, const double* u, int64_t n, doub
       }
     }
   };
-  // copy of slab k into ring slot k % RUN_RING; a slot is refilled only after
-  // the set-up of the slab before in it, whose event is recorded first (a
-  // wait on an event not yet recorded would not wait)
+  // copy of slab k into slot k % R; a slot is refilled only after the
+  // set-up of the slab before in it, whose event is recorded first (a wait
+  // on an event not yet recorded would not wait)
   auto copy_in = [&](int k) {
-    const int r = k % RUN_RING;
+    const int r = k % R;
     const int64_t cells = slab_cells(k), c0 = int64_t(z0[k]) * plane;
-    if (k >= RUN_RING) ok = ok && cudaStreamWaitEvent(s_in, in_free[r], 0) == cudaSuccess;
+    if (k >= R) ok = ok && cudaStreamWaitEvent(s_in, in_free[r], 0) == cudaSuccess;
     if (rho)
       ok = ok && cudaMemcpyAsync(ring_in[r], rho + c0, size_t(cells) * sizeof(double),
                                  cudaMemcpyHostToDevice, s_in) == cudaSuccess;
@@ -969,10 +992,10 @@ int lbm_run_host(lbm_ctx* c, const double* rho, const double* u, int64_t n, doub
     ok = cudaEventRecord(start, c->stream) == cudaSuccess &&
          cudaStreamWaitEvent(s_in, start, 0) == cudaSuccess &&
          cudaStreamWaitEvent(s_out, start, 0) == cudaSuccess;
-    for (int k = 0; k < S && k < RUN_RING; ++k) copy_in(k);
+    for (int k = 0; k < S && k < R; ++k) copy_in(k);
     // the compute order: set up each arriving slab, then every step it enables
     for (int k = 0; k < S && ok; ++k) {
-      const int r = k % RUN_RING;
+      const int r = k % R;
       ok = cudaStreamWaitEvent(c->stream, arrived[k], 0) == cudaSuccess;
       AuxArgs a = aux_base(c, lbm::AUX_SCATTER);
       a.buf = c->buf[cur0];
@@ -985,7 +1008,7 @@ int lbm_run_host(lbm_ctx* c, const double* rho, const double* u, int64_t n, doub
         ok = cudaGetLastError() == cudaSuccess;
       }
       ok = ok && cudaEventRecord(in_free[r], c->stream) == cudaSuccess;
-      if (k + RUN_RING < S) copy_in(k + RUN_RING);
+      if (k + R < S) copy_in(k + R);
       step[k] = 0;
       advance();
     }
@@ -1004,10 +1027,6 @@ int lbm_run_host(lbm_ctx* c, const double* rho, const double* u, int64_t n, doub
   }
   for (cudaEvent_t e : ev)
     if (e) cudaEventDestroy(e);
-  for (int r = 0; r < RUN_RING; ++r) {
-    if (ring_in[r]) cudaFree(ring_in[r]);
-    if (ring_out[r]) cudaFree(ring_out[r]);
-  }
   if (s_in) cudaStreamDestroy(s_in);
   if (s_out) cudaStreamDestroy(s_out);
   return rc;

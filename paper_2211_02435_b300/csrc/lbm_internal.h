@@ -185,5 +185,8 @@ struct lbm_ctx {
   cudaEvent_t io_ready[2], io_done[2];
   double* io_buf[2];
   size_t io_cap;  // doubles per staging buffer
+  // staging of lbm_run_host (kept between calls): bytes at run_buf
+  double* run_buf;
+  size_t run_cap;
 };
 
