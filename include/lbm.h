@@ -234,7 +234,10 @@ int lbm_macroscopic(lbm_ctx* ctx, double* rho, double* u, int on_device);
  * and the host-to-device copies, the steps (Eq. 2.1, a slab taking step
  * k + 1 once both neighbouring slabs have taken step k) and the
  * device-to-host copies of different slabs overlap, on two copy streams
- * the library creates for the call and the context's stream.  Otherwise
+ * the library creates for the call and the context's stream.  The device
+ * staging (one slot per slab and direction, 2 x 8 (1 + D) N bytes, or a
+ * ring of 4 slots per direction when the device lacks the room) is kept
+ * by the context for the next call and freed by lbm_destroy.  Otherwise
  * (or with fewer than 3 slabs) the three calls run one after the other.
  * Errors: INVALID, OOM, CUDA. */
 int lbm_run_host(lbm_ctx* ctx, const double* rho, const double* u, int64_t n,
