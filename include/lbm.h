@@ -215,8 +215,9 @@ int lbm_create(lbm_ctx** out, const lbm_params* params);
 int lbm_init_velocity(lbm_ctx* ctx, const double* rho, const double* u,
                       int on_device);
 
-/* Advance n >= 0 steps on the context's stream (asynchronous).
- * Errors: INVALID, CUDA. */
+/* Advance n >= 0 steps on the context's stream (asynchronous unless the
+ * divergence watch of lbm_set_divergence_check is on).
+ * Errors: INVALID, CUDA, DIVERGED (watch on). */
 int lbm_step(lbm_ctx* ctx, int64_t n);
 
 /* Density rho[N] and velocity u[D*N] of f(n), Eq. 2.3, written as FP64.
@@ -238,7 +239,8 @@ int lbm_macroscopic(lbm_ctx* ctx, double* rho, double* u, int on_device);
  * staging (one slot per slab and direction, 2 x 8 (1 + D) N bytes, or a
  * ring of 4 slots per direction when the device lacks the room) is kept
  * by the context for the next call and freed by lbm_destroy.  Otherwise
- * (or with fewer than 3 slabs) the three calls run one after the other.
+ * (or with fewer than 3 slabs, or with the divergence watch of
+ * lbm_set_divergence_check on) the three calls run one after the other.
  * Errors: INVALID, OOM, CUDA. */
 int lbm_run_host(lbm_ctx* ctx, const double* rho, const double* u, int64_t n,
                  double* rho_out, double* u_out, int slabs);
@@ -384,6 +386,14 @@ int lbm_set_shallow_water(lbm_ctx* ctx, double g);
 #define LBM_STEP_DIRECT 1
 #define LBM_STEP_STAGED 2
 int lbm_set_step_kernel(lbm_ctx* ctx, int kernel);
+
+/* Divergence watch of lbm_step: every `every` >= 1 steps (counted by the
+ * context's step counter) the step call runs the FP64 invariants of f(n)
+ * (as lbm_invariants, which synchronises the stream) and returns
+ * LBM_ERR_DIVERGED, with the step counter at that step, as soon as a cell
+ * holds a non-finite population; 0 turns the watch off (default).
+ * Errors: INVALID. */
+int lbm_set_divergence_check(lbm_ctx* ctx, int64_t every);
 
 /* Free the context and its device memory.  NULL is ignored. */
 void lbm_destroy(lbm_ctx* ctx);

@@ -9,6 +9,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbm.h"
 #include "lbm_internal.h"
 
@@ -436,6 +438,12 @@ static int scatter(lbm_ctx* c, const double* df, const double* rho, const double
   return cuda_err(cudaGetLastError());
 }
 
+// NVTX range over a host entry point (visible in Nsight timelines)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 static int read_status(lbm_ctx* c);
 
 // ------------------------------------------------ host transfers in slabs
@@ -608,6 +616,7 @@ int gather_slabs(lbm_ctx* c, const SlabPlan& sp, double* const* outs, int ncomp,
 
 int lbm_init_velocity(lbm_ctx* c, const double* rho, const double* u, int on_device) {
   if (!c || !u) return LBM_ERR_INVALID;
+  NvtxRange range("lbm_init_velocity");
   const size_t N = size_t(c->g.N);
   SlabPlan sp;
   if (!on_device && c->swe_g == 0.0 && slab_plan(c, 1 + c->d, &sp)) {
@@ -666,6 +675,12 @@ static bool use_staged(const lbm_ctx* c) {
   return false;
 }
 
+int lbm_set_divergence_check(lbm_ctx* c, int64_t every) {
+  if (!c || every < 0) return LBM_ERR_INVALID;
+  c->watch = every;
+  return LBM_OK;
+}
+
 int lbm_set_step_kernel(lbm_ctx* c, int kernel) {
   if (!c || kernel < LBM_STEP_AUTO || kernel > LBM_STEP_STAGED) return LBM_ERR_INVALID;
   if (kernel == LBM_STEP_STAGED && !staged_ok(c)) return LBM_ERR_UNSUPPORTED;
@@ -717,6 +732,7 @@ static StepArgs step_args(const lbm_ctx* c) {
 
 int lbm_step(lbm_ctx* c, int64_t n) {
   if (!c || n < 0) return LBM_ERR_INVALID;
+  NvtxRange range("lbm_step");
   StepArgs a = step_args(c);
   const step_fn fn = kStep[c->p.stencil][c->p.storage];
   for (int64_t s = 0; s < n; ++s) {
@@ -740,11 +756,17 @@ int lbm_step(lbm_ctx* c, int64_t n) {
       c->parity ^= 1;
     }
     c->t++;
+    if (c->watch > 0 && c->t % c->watch == 0) {
+      double inv[8];
+      const int rc = lbm_invariants(c, inv);  // LBM_ERR_DIVERGED on a non-finite cell
+      if (rc != LBM_OK) return rc;
+    }
   }
   return cuda_err(cudaGetLastError());
 }
 
 static int gather(lbm_ctx* c, double* df, double* rho, double* u, int on_device) {
+  NvtxRange range(df ? "lbm_get_populations" : "lbm_macroscopic");
   const size_t N = size_t(c->g.N);
   SlabPlan sp;
   if (!on_device && df && slab_plan(c, c->q, &sp)) {
@@ -830,6 +852,7 @@ bool run_pipelined_ok(const lbm_ctx* c) {
 int lbm_run_host(lbm_ctx* c, const double* rho, const double* u, int64_t n, double* rho_out,
                  double* u_out, int slabs) {
   if (!c || !u || n < 0 || slabs < 0) return LBM_ERR_INVALID;
+  NvtxRange range("lbm_run_host");
   const size_t N = size_t(c->g.N);
   const int nz = c->g.nz, d = c->d;
   const int64_t plane = int64_t(c->g.nx) * c->g.ny;
@@ -840,7 +863,7 @@ int lbm_run_host(lbm_ctx* c, const double* rho, const double* u, int64_t n, doub
     S = int((size_t(nz) * per + IO_SLAB_BYTES - 1) / IO_SLAB_BYTES);
   }
   if (S > nz) S = nz;
-  if (!run_pipelined_ok(c) || S < 3) {  // one job after the other
+  if (!run_pipelined_ok(c) || S < 3 || c->watch > 0) {  // one job after the other
     int rc = lbm_init_velocity(c, rho, u, 0);
     if (rc == LBM_OK) rc = lbm_step(c, n);
     if (rc == LBM_OK && (rho_out || u_out)) rc = lbm_macroscopic(c, rho_out, u_out, 0);

@@ -188,5 +188,6 @@ struct lbm_ctx {
   // staging of lbm_run_host (kept between calls): bytes at run_buf
   double* run_buf;
   size_t run_cap;
+  int64_t watch;  // divergence watch period of lbm_step (0: off)
 };
 

@@ -83,6 +83,7 @@ def lib():
         L.lbm_step.argtypes = [vp, i64]
         L.lbm_macroscopic.argtypes = [vp, vp, vp, c_int]
         L.lbm_run_host.argtypes = [vp, vp, vp, i64, vp, vp, c_int]
+        L.lbm_set_divergence_check.argtypes = [vp, i64]
         L.lbm_get_populations.argtypes = [vp, vp, c_int]
         L.lbm_set_populations.argtypes = [vp, vp, c_int]
         L.lbm_invariants.argtypes = [vp, d]
@@ -350,6 +351,11 @@ class Lattice:
         """Switch a D2Q9 absolute-storage CENTRAL / CUMULANT context to the
         shallow-water method with gravity g (0 switches back); include/lbm.h."""
         _check(lib().lbm_set_shallow_water(self._h, float(g)), "lbm_set_shallow_water")
+
+    def set_divergence_check(self, every):
+        """lbm_set_divergence_check: lbm_step checks f(n) for non-finite
+        populations every `every` steps (0: off) and raises DIVERGED."""
+        _check(lib().lbm_set_divergence_check(self._h, int(every)), "lbm_set_divergence_check")
 
     def set_step_kernel(self, kernel):
         """STEP_AUTO, STEP_DIRECT or STEP_STAGED (include/lbm.h)."""

@@ -86,6 +86,7 @@ def test_null_arguments(lib):
     assert lib.lbm_invariants(None, None) == -1
     assert lib.lbm_set_step_kernel(None, 0) == -1
     assert lib.lbm_run_host(None, None, None, 1, None, None, 0) == -1
+    assert lib.lbm_set_divergence_check(None, 1) == -1
     lib.lbm_destroy(None)
     for c in (0, -1, -2, -3, -4, -5, -6, -7, -8):
         assert lib.lbm_error_string(c)

@@ -206,6 +206,34 @@ def test_nonfinite_population_is_reported():
         assert inv["nonfinite"] == 1
 
 
+@pytest.mark.parametrize("streaming", [L.PULL, L.AA])
+def test_divergence_watch_stops_the_step(streaming):
+    """A poisoned population (host-made) spreads through the collision; the
+    step call with the watch on returns DIVERGED at the first watched step,
+    and without the watch it runs on."""
+    st = 1
+    dims = DIMS[st]
+    df = np.zeros((19, int(np.prod(dims))))
+    df[4, 17] = np.nan
+    with L.Lattice(st, L.SPACE_RAW, L.EQ_DELTA, L.STORE_F32, streaming, RATES_GEN, dims) as lat:
+        lat.set_populations(df)
+        lat.step(3)  # watch off
+        assert lat.time()[0] == 3
+        lat.set_divergence_check(2)
+        with pytest.raises(L.LBMError) as e:
+            lat.step(5)
+        assert e.value.code == -6
+        assert lat.time()[0] == 4  # stopped at the first watched step
+        lat.set_divergence_check(0)
+        lat.step(2)
+        assert lat.time()[0] == 6
+    with L.Lattice(st, L.SPACE_RAW, L.EQ_DELTA, L.STORE_F32, streaming, RATES_GEN, dims) as lat:
+        lat.set_populations(np.zeros_like(df))
+        lat.set_divergence_check(1)
+        lat.step(4)  # finite: no error
+        assert lat.time()[0] == 4
+
+
 def test_device_pointer_path_matches_host_path():
     torch = pytest.importorskip("torch")
     st, space, eq, reg = 2, L.SPACE_CENTRAL, L.EQ_ABSOLUTE, True
