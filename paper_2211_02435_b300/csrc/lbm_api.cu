@@ -966,24 +966,37 @@ int lbm_run_host(lbm_ctx* c, const double* rho, const double* u, int64_t n, doub
     emitted[k] = 1;
     ++out_count;
   };
-  // every step (and read-out) that has become possible, in slab order, until none
+  // every step (and read-out) that has become possible, until none: the
+  // slabs able to advance are found first, then each run of adjacent ones
+  // at the same step goes as one launch over their z-planes (a neighbour
+  // advancing in between only adds to what they may do)
+  std::vector<char> elig(S, 0);
   auto advance = [&]() {
     bool any = true;
     while (any && ok) {
       any = false;
-      for (int k = 0; k < S && ok; ++k) {
+      for (int k = 0; k < S; ++k) {
         const int km = (k + S - 1) % S, kp = (k + 1) % S;
-        const int t = step[k];
-        if (t >= 0 && t < n && (t == 0 || (step[km] >= t && step[kp] >= t))) {
-          sa.src = c->buf[(cur0 + t) % 2];
-          sa.dst = c->buf[(cur0 + t + 1) % 2];
-          sa.z0 = z0[k];
-          sa.nzc = z0[k + 1] - z0[k];
-          fn(sa);
-          ok = cudaGetLastError() == cudaSuccess;
-          step[k] = t + 1;
-          any = true;
+        const int64_t t = step[k];
+        elig[k] = t >= 0 && t < n && (t == 0 || (step[km] >= t && step[kp] >= t));
+      }
+      for (int k = 0; k < S && ok;) {
+        if (!elig[k]) {
+          ++k;
+          continue;
         }
+        int e = k;
+        while (e + 1 < S && elig[e + 1] && step[e + 1] == step[k]) ++e;
+        const int64_t t = step[k];
+        sa.src = c->buf[(cur0 + t) % 2];
+        sa.dst = c->buf[(cur0 + t + 1) % 2];
+        sa.z0 = z0[k];
+        sa.nzc = z0[e + 1] - z0[k];
+        fn(sa);
+        ok = cudaGetLastError() == cudaSuccess;
+        for (int j = k; j <= e; ++j) step[j] = int(t + 1);
+        any = true;
+        k = e + 1;
       }
       for (int k = 0; k < S && ok; ++k) {
         const int km = (k + S - 1) % S, kp = (k + 1) % S;
