@@ -2,8 +2,9 @@
 and read-out to host with the copies and the steps of different slabs of
 z-planes overlapping.  Every result equals lbm_init_velocity + lbm_step +
 lbm_macroscopic bit for bit: 3 to many slabs (one plane per slab
-included), uneven slabs, n = 0, 1, 2 and more steps, FP32 / FP16 / FP64
-storage, with and without rho; the unsupported cases run the sequence."""
+included), uneven slabs, n = 0, 1, 2 and more steps, FP32 / FP16 / BF16
+(packed and, for odd Nx, scalar) / FP64 storage, the discrete equilibrium,
+with and without rho; the unsupported cases run the sequence."""
 import numpy as np
 import pytest
 
@@ -40,12 +41,15 @@ CASES = [
     ((L.D3Q19, L.SPACE_RAW, L.EQ_DELTA, L.STORE_F16_DELTA, L.PULL, RATES), (34, 10, 17)),
     ((L.D3Q27, L.SPACE_CENTRAL, L.EQ_ABSOLUTE, L.STORE_F64, L.PULL, RATES), (19, 7, 9)),
     ((L.D3Q19, L.SPACE_TRT, L.EQ_DELTA, L.STORE_F32, L.PULL, [1.3, 1, 1.75, 1, 1, 1]), (21, 9, 11)),
+    ((L.D3Q19, L.SPACE_CUMULANT, L.EQ_DISCRETE2, L.STORE_F64, L.PULL, RATES), (23, 8, 10)),
+    ((L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_BF16_DELTA, L.PULL, RATES), (33, 8, 12)),
 ]
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 7])
 @pytest.mark.parametrize("case", CASES, ids=["d3q27-k-f32", "d3q19-raw-f16", "d3q27-cm-f64",
-                                             "d3q19-trt-f32"])
+                                             "d3q19-trt-f32", "d3q19-k-disc-f64",
+                                             "d3q27-k-bf16-odd-nx"])
 def test_run_host_equals_the_sequence(case, n):
     args, dims = case
     rho, u = fields(dims)
