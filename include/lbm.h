@@ -20,13 +20,17 @@
  *  - Return value: LBM_OK (0) or a negative LBM_ERR_* code.  No C++
  *    exception crosses the ABI.  lbm_error_string() names a code.
  *  - Ownership: the library owns the device state it allocates in
- *    lbm_create (freed by lbm_destroy).  The caller owns every buffer it
- *    passes in; the library keeps no pointer to it after the call returns.
+ *    lbm_create and the staging buffers it keeps for host transfers (all
+ *    freed by lbm_destroy).  The caller owns every buffer it passes in; the
+ *    library keeps no pointer to it after the call returns.
  *  - on_device = 1: the pointer is device memory of the context's GPU (e.g.
  *    torch tensor.data_ptr()); 0: host memory.  Host-pointer calls copy
- *    through the context's stream and synchronise it before returning.
+ *    (large arrays in slabs, on copy streams the context owns, ordered
+ *    after the work already queued on its stream) and synchronise before
+ *    returning.
  *  - All device work is enqueued on params.stream (a cudaStream_t; NULL =
- *    legacy default stream).  lbm_step returns without synchronising.
+ *    legacy default stream).  lbm_step returns without synchronising
+ *    (unless its divergence watch is on).
  *  - There is no CPU fallback: without a usable CUDA device every call that
  *    needs one returns LBM_ERR_CUDA.
  *  - Populations read or written through this interface are always the
