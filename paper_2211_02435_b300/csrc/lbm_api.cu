@@ -923,7 +923,7 @@ int lbm_run_host(lbm_ctx* c, const double* rho, const double* u, int64_t n, doub
     cudaGetLastError();
     rc = LBM_ERR_OOM;
   }
-  std::vector<int> step(S, -1);       // steps taken by slab (-1: not set up)
+  std::vector<int64_t> step(S, -1);   // steps taken by slab (-1: not set up)
   std::vector<char> emitted(S, 0);    // read-out issued
   const int cur0 = c->cur;
   StepArgs sa = step_args(c);
@@ -994,7 +994,7 @@ int lbm_run_host(lbm_ctx* c, const double* rho, const double* u, int64_t n, doub
         sa.nzc = z0[e + 1] - z0[k];
         fn(sa);
         ok = cudaGetLastError() == cudaSuccess;
-        for (int j = k; j <= e; ++j) step[j] = int(t + 1);
+        for (int j = k; j <= e; ++j) step[j] = t + 1;
         any = true;
         k = e + 1;
       }
