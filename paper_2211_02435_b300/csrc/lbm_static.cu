@@ -73,10 +73,13 @@ extern "C" int lbm_invariants_noalloc(int stencil, int storage, const void* df,
     return LBM_ERR_INVALID;
   if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || (stencil == LBM_D2Q9 && dims[2] != 1))
     return LBM_ERR_INVALID;
-  if (dims[0] > LBM_STATIC_MAX_CELLS || dims[1] > LBM_STATIC_MAX_CELLS ||
-      dims[0] * dims[1] > LBM_STATIC_MAX_CELLS ||
-      dims[0] * dims[1] * dims[2] > LBM_STATIC_MAX_CELLS)
-    return LBM_ERR_INVALID;  // more cells than one call serves
+  // more cells than one call serves; every extent is bounded before any
+  // product is formed (Nx * Ny < 2^62 then fits), and Nz is compared by
+  // division, so no size wraps around int64
+  constexpr int64_t kLim = LBM_STATIC_MAX_CELLS;
+  if (dims[0] > kLim || dims[1] > kLim || dims[2] > kLim) return LBM_ERR_INVALID;
+  const int64_t nxy = dims[0] * dims[1];
+  if (nxy > kLim || dims[2] > kLim / nxy) return LBM_ERR_INVALID;
   double* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc != LBM_OK) return rc;

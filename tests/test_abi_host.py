@@ -92,6 +92,27 @@ def test_null_arguments(lib):
         assert lib.lbm_error_string(c)
 
 
+@pytest.mark.parametrize("dims", [
+    (4, 1, (1 << 62) + 1),        # the int64 product would wrap to 4
+    (1 << 40, 1 << 40, 1),        # Nx * Ny alone overflows
+    ((1 << 62) + 1, 1, 4),
+    (1, (1 << 63) - 1, 1),
+    (1 << 16, 1 << 15, 2),        # exactly 2^32 cells
+    (1, 1, 1 << 31),              # 2^31 cells: one more than a call serves
+    (46341, 46341, 1),            # 2^31 + 1 cells in the xy plane
+    (3, 3, -1),
+])
+def test_noalloc_rejects_wrapping_sizes_before_any_launch(lib, dims):
+    # the size check runs before the library touches a device, so these
+    # calls return LBM_ERR_INVALID on a machine without a GPU as well; the
+    # population pointer is never dereferenced
+    d = (ctypes.c_int64 * 3)(*dims)
+    out = (ctypes.c_double * 8)()
+    rc = lib.lbm_invariants_noalloc(L.D3Q27, L.STORE_F32, ctypes.c_void_p(1 << 20), d,
+                                    ctypes.addressof(out), 0, None)
+    assert rc == -1
+
+
 def test_python_binding_raises_on_error(lib):
     with pytest.raises(L.LBMError) as e:
         L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_DELTA, L.STORE_F32, L.PULL, [1.9], (8, 8, 8))
