@@ -100,6 +100,9 @@ def lib():
         L.lbm_oracle_closure_step.argtypes = [m, i64, d, d, d, d, ctypes.c_int]
         L.lbm_oracle_closure_loss.argtypes = [m, i64, d, d, d, d, d, ctypes.c_int]
         L.lbm_oracle_closure_loss.restype = ctypes.c_double
+        L.lbm_oracle_closure_rollout_loss.argtypes = [m, i64, d, ctypes.c_int, d, d, d,
+                                                      ctypes.c_int]
+        L.lbm_oracle_closure_rollout_loss.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -362,3 +365,14 @@ def closure_loss(m, dims, df_s, df_t, params, shift, scale, nthreads=0):
     return lib().lbm_oracle_closure_loss(ctypes.byref(m), dm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                          _dp(_f64(df_s)), _dp(_f64(df_t)), _dp(_f64(params)),
                                          _dp(_f64(shift)), _dp(_f64(scale)), int(nthreads))
+
+
+def closure_rollout_loss(m, dims, states, params, shift, scale, nthreads=0):
+    """K-step rollout loss from states[0] against targets states[1..K]
+    (states: K + 1 SoA populations, stacked along the first axis)."""
+    dm = _dims(dims)
+    st = np.ascontiguousarray(np.asarray(states, dtype=np.float64))
+    K = st.shape[0] - 1
+    return lib().lbm_oracle_closure_rollout_loss(
+        ctypes.byref(m), dm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(st), int(K),
+        _dp(_f64(params)), _dp(_f64(shift)), _dp(_f64(scale)), int(nthreads))

@@ -1022,17 +1022,23 @@ static int features_cell(const lattice_t* L, const double* df, double omega_s,
       S[a][b] = -1.5 * omega_s * Pi[a][b];
     }
   const double trP = Pi[0][0] + Pi[1][1] + Pi[2][2];
-  double fro = 0.0;
+  double fro = 0.0, nS2 = 0.0, nD2 = 0.0;
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) {
       D[a][b] = Pi[a][b] - (a == b ? trP / 3.0 : 0.0);
       fro += Pi[a][b] * Pi[a][b];
+      nS2 += S[a][b] * S[a][b];
+      nD2 += D[a][b] * D[a][b];
     }
+  /* conditioning: an invariant of degree k in its tensor is divided by the
+   * (k-1)-th power of that tensor's Frobenius norm (0 where the norm is 0),
+   * so every feature but drho is of degree 1 in Pi and Lipschitz */
+  const double nS = sqrt(nS2), nD = sqrt(nD2);
   out[0] = S[0][0] + S[1][1] + S[2][2];
-  out[1] = inv2(S);
-  out[2] = det3(S);
-  out[3] = inv2(D);
-  out[4] = det3(D);
+  out[1] = nS > 0.0 ? inv2(S) / nS : 0.0;
+  out[2] = nS > 0.0 ? det3(S) / nS2 : 0.0;
+  out[3] = nD > 0.0 ? inv2(D) / nD : 0.0;
+  out[4] = nD > 0.0 ? det3(D) / nD2 : 0.0;
   out[5] = sqrt(fro);
   out[6] = drho;
   return 0;
@@ -1145,6 +1151,42 @@ double lbm_oracle_closure_loss(const lbm_oracle_method* base,
       for (int64_t k = 0; k < 3 * N; ++k) s += (u1[k] - u2[k]) * (u1[k] - u2[k]);
       loss = s / (double)N;
     }
+  }
+  free(work);
+  free(r1);
+  free(r2);
+  free(u1);
+  free(u2);
+  return loss;
+}
+
+double lbm_oracle_closure_rollout_loss(const lbm_oracle_method* base,
+                                       const int64_t* dims, const double* df,
+                                       int K, const double* params,
+                                       const double* shift, const double* scale,
+                                       int nthreads) {
+  if (check_method(base) || K < 1) return NAN;
+  const lattice_t* L = &g_lat[base->stencil];
+  const int64_t N = dims[0] * dims[1] * dims[2];
+  const int64_t QN = (int64_t)L->q * N;
+  double* work = (double*)malloc(sizeof(double) * QN);
+  double *r1 = (double*)malloc(sizeof(double) * N), *r2 = (double*)malloc(sizeof(double) * N);
+  double *u1 = (double*)malloc(sizeof(double) * 3 * N), *u2 = (double*)malloc(sizeof(double) * 3 * N);
+  double loss = NAN;
+  if (work && r1 && r2 && u1 && u2) {
+    memcpy(work, df, sizeof(double) * QN);
+    double s = 0.0;
+    int k = 1;
+    for (; k <= K; ++k) {
+      if (lbm_oracle_closure_step(base, dims, work, params, shift, scale, nthreads) != 0 ||
+          lbm_oracle_macroscopic(base, dims, work, r1, u1) != 0 ||
+          lbm_oracle_macroscopic(base, dims, df + k * QN, r2, u2) != 0)
+        break;
+      double sk = 0.0;
+      for (int64_t c = 0; c < 3 * N; ++c) sk += (u1[c] - u2[c]) * (u1[c] - u2[c]);
+      s += sk / (double)N;
+    }
+    if (k > K) loss = s / (double)K;
   }
   free(work);
   free(r1);

@@ -201,8 +201,11 @@ int lbm_oracle_swe_step(const lbm_oracle_method* m, double g,
 /* Raw features of one cell from its zero-centered populations df[q]:
  * with Pi = kappa_2 / rho - I/3 (second-order central moments, Sec. 2.3.2),
  * S = -(3 omega_shear / 2) Pi and D = Pi - tr(Pi)/3 I:
- * out = {tr S, I2(S), det S, I2(D), det D, |Pi|_F, rho - 1}, where
- * I2(A) = ((tr A)^2 - tr(A A)) / 2.  3-D stencils only. */
+ * out = {tr S, I2(S)/|S|, det S/|S|^2, I2(D)/|D|, det D/|D|^2, |Pi|, rho - 1},
+ * where I2(A) = ((tr A)^2 - tr(A A)) / 2, |.| is the Frobenius norm and a
+ * quotient is 0 where its norm is 0: the principal invariants, each divided
+ * by a power of its tensor's norm so that all but the last are of degree 1
+ * in Pi.  3-D stencils only. */
 int lbm_oracle_closure_features(int stencil, const double* df,
                                 double omega_shear, double out[7]);
 
@@ -228,6 +231,17 @@ double lbm_oracle_closure_loss(const lbm_oracle_method* base,
                                const double* df_t, const double* params,
                                const double* shift, const double* scale,
                                int nthreads);
+
+/* K-step rollout loss: starting from df[0] (K + 1 SoA states df[k][q][N]
+ * laid out one after the other, df[k] the target after k steps), run K
+ * learned-rate steps and return (1/K) sum_k mean over cells of
+ * |u(step^k(df[0])) - u(df[k])|^2.  K = 1 is lbm_oracle_closure_loss.
+ * Returns NaN on error. */
+double lbm_oracle_closure_rollout_loss(const lbm_oracle_method* base,
+                                       const int64_t* dims, const double* df,
+                                       int K, const double* params,
+                                       const double* shift, const double* scale,
+                                       int nthreads);
 
 #ifdef __cplusplus
 }
