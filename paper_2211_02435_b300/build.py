@@ -1,7 +1,9 @@
 """Build liblbm.so (the CUDA library behind include/lbm.h) in-tree for sm_103a.
 
-The twelve (stencil, storage) kernel units and the remaining units compile
-in parallel with nvcc; the shared library is linked next to this file.
+The fifteen (stencil, storage) kernel units and the remaining units compile
+in parallel with nvcc; a unit is recompiled only when a file its nvcc
+dependency list names (or its command line) changed.  The shared library is
+linked next to this file.
 Run as ``python -m paper_2211_02435_b300.build [--force] [-v]``.
 """
 from __future__ import annotations
@@ -49,6 +51,28 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+def _flags_of(extra):
+    return " ".join([NVCC] + FLAGS + extra)
+
+
+def _obj_current(src, out, extra):
+    """An object is current when it was compiled with the same command and is
+    newer than every file its dependency list (nvcc -MD) names."""
+    dep, cmdf = out + ".d", out + ".cmd"
+    if not (os.path.exists(out) and os.path.exists(dep) and os.path.exists(cmdf)):
+        return False
+    if open(cmdf).read() != _flags_of(extra):
+        return False
+    t = os.path.getmtime(out)
+    text = open(dep).read().replace("\\\n", " ")
+    files = text.split(":", 1)[1].split() if ":" in text else []
+    files.append(src)
+    for f in files:
+        if not os.path.exists(f) or os.path.getmtime(f) > t:
+            return False
+    return True
+
+
 def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
@@ -57,12 +81,16 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     def compile_one(u):
         src, obj, extra = u
         out = os.path.join(OBJ, obj)
-        cmd = [NVCC] + FLAGS + extra + ["-c", src, "-o", out]
+        if not force and _obj_current(src, out, extra):
+            return out
+        cmd = [NVCC] + FLAGS + extra + ["-MD", "-MF", out + ".d", "-c", src, "-o", out]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {obj}:\n{r.stderr}")
+        with open(out + ".cmd", "w") as fh:
+            fh.write(_flags_of(extra))
         return out
 
     with cf.ThreadPoolExecutor(max_workers=jobs or os.cpu_count() or 4) as ex:
