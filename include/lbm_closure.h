@@ -9,8 +9,11 @@
  * with Pi = kappa_2 / rho - I/3 (normalised second-order central moments,
  * Sec. 2.3.2), S = -(3 omega_shear / 2) Pi (the non-equilibrium estimate of
  * the strain rate) and D = Pi - tr(Pi)/3 I,
- *   raw = {tr S, I2(S), det S, I2(D), det D, |Pi|_F, rho - 1},
- *   I2(A) = ((tr A)^2 - tr(A A)) / 2,
+ *   raw = {tr S, I2(S)/|S|, det S/|S|^2, I2(D)/|D|, det D/|D|^2, |Pi|, rho - 1},
+ *   I2(A) = ((tr A)^2 - tr(A A)) / 2, |.| the Frobenius norm,
+ * each quotient 0 where its norm is 0: the principal invariants, divided by
+ * powers of the norm so that every input but the density is of degree 1 in
+ * Pi (same scale for all, Lipschitz, no amplified rounding near zero);
  * normalised x_i = (raw_i - shift_i) * scale_i.  Network:
  *   h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), z = W3 h2 + b3,
  *   omega_{3..6} = clamp(2 sigmoid(z), 1e-3, 1.999);
@@ -23,13 +26,17 @@
  *
  * Training target: with snapshots f_c(s) of a coarse lattice (typically the
  * 4^3 block average of a fine run, one snapshot every 4 fine steps), the
- * loss of pair s is L = mean over cells of |u(step_theta(f_c(s))) -
- * u(f_c(s+1))|^2, one coarse step with the network's rates (teacher
- * forcing).  Its gradient is computed by hand-written kernels: tangents of
- * the post-collision populations with respect to the four rates, the
- * adjoint of streaming and of the velocity, and the network's backward
- * pass; weight gradients are reduced per block and folded in a fixed order.
- * Adam updates FP32 master weights; the forward uses their BF16 rounding.
+ * loss of window s with unroll K is
+ *   L = (1/K) sum_{k=1..K} mean over cells of |u(step_theta^k(f_c(s))) - u(f_c(s+k))|^2,
+ * K coarse steps with the network's rates from snapshot s (K = 1: one-step
+ * teacher forcing).  Its gradient is computed by hand-written kernels,
+ * backwards through the K steps: the adjoint of streaming and of the
+ * velocity, tangents of the post-collision populations with respect to the
+ * four rates, the network's backward pass (weights and inputs), and the
+ * transposed per-cell Jacobian of the collision (27 forward-mode dual-number
+ * passes per cell) that carries dL/df to the step before; weight gradients
+ * are reduced per block and folded in a fixed order.  Adam updates FP32
+ * master weights; the forward uses their BF16 rounding.
  */
 #ifndef LBM_CLOSURE_H
 #define LBM_CLOSURE_H
@@ -44,6 +51,7 @@ extern "C" {
 #define LBM_CLOSURE_NHIDDEN 32
 #define LBM_CLOSURE_NOUT 4
 #define LBM_CLOSURE_NPARAM 1444
+#define LBM_CLOSURE_MAX_UNROLL 64
 
 typedef struct {
   float shift[LBM_CLOSURE_NIN];
@@ -89,11 +97,18 @@ int lbm_trainer_set_params(lbm_trainer* t, const float* params,
                            const float shift[7], const float scale[7]);
 int lbm_trainer_get_params(lbm_trainer* t, float* params);
 
-/* Loss of pair (s, s+1) and its gradient with respect to the parameters
+/* Steps K of the rollout loss (1 <= K <= LBM_CLOSURE_MAX_UNROLL, K + 1 <=
+ * max_snapshots; 1 at creation).  Allocates K post-collision fields and,
+ * for K > 1, two adjoint fields (27 N FP32 each).  Errors: INVALID, OOM (the
+ * previous K stays). */
+int lbm_trainer_set_unroll(lbm_trainer* t, int K);
+
+/* Loss of the window s .. s+K (snapshots s+1 .. s+K the targets; s + K <
+ * count) and its gradient with respect to the parameters
  * (grad[LBM_CLOSURE_NPARAM] FP64 host, or NULL).  Synchronises. */
 int lbm_trainer_loss_grad(lbm_trainer* t, int s, double* loss, double* grad);
 
-/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on pair (s, s+1) with
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on window s with
  * learning rate lr; returns the loss before the update.  Synchronises. */
 int lbm_trainer_adam_step(lbm_trainer* t, int s, double lr, double* loss);
 

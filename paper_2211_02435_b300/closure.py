@@ -2,11 +2,16 @@
 
 Data: a fine D3Q27 run of the plain regularised cumulant method on the
 seeded random-Fourier-mode flow, restricted by 4^3 block averages to the
-coarse lattice every 4 fine steps (acoustic scaling: one coarse step = four
-fine steps, equal lattice velocities, nu_coarse = nu_fine / 4).  Training:
-Adam on the one-step velocity loss of consecutive coarse snapshots, all in
-the library's GPU kernels.  Evaluation: one-step loss on held-out pairs and
-an a-posteriori rollout of the coarse method from a held-out snapshot,
+coarse lattice (acoustic scaling: one coarse step = four fine steps, equal
+lattice velocities, nu_coarse = nu_fine / 4).  The run spans `span` coarse
+steps; its first 80 % supplies the training windows (K + 1 consecutive
+coarse snapshots each), the last 20 % is held out.
+
+Training: Adam on the K-step rollout loss of the windows, all in the
+library's GPU kernels (forward, adjoint through the K steps, network
+backward, Adam).  Evaluation, held out: the K-step loss of a window that
+starts the held-out part, and a-posteriori rollouts of the coarse method
+from the first held-out snapshot (`rollout` steps and a shorter one),
 learned rates against the plain method (higher-order rates 1), both judged
 by the restricted fine solution.
 
@@ -22,22 +27,46 @@ from . import inputs as I
 from . import lbm as L
 
 
-def make_snapshots(trainer, fine_edge, nsnap, nu_fine, seed, umax=0.08, stream=None):
-    """Run the fine plain cumulant method (FP32, pull) and append nsnap
-    restricted snapshots, one every 4 fine steps.  Returns the fine MLUPS."""
+def schedule(span, unroll, windows, rollout, short):
+    """Coarse times to snapshot, sorted and distinct: `windows` training
+    windows of unroll + 1 consecutive times spread over the first 80 % of the
+    span, the held-out window at 80 %, and the held-out rollout targets.
+    Consecutive integer times sit at consecutive snapshot indices, so a
+    window starting at index s holds its targets at s + 1 .. s + unroll.
+    Returns (times, training window indices, held-out window index,
+    {"t0", "short", "long": index})."""
+    t_held = int(round(0.8 * span))
+    last = max(t_held - unroll - 1, 0)
+    starts = np.unique(np.linspace(0, last, windows).round().astype(int))
+    need = set()
+    for s in list(starts) + [t_held]:
+        need.update(range(int(s), int(s) + unroll + 1))
+    need.update((t_held + short, t_held + rollout))
+    times = sorted(need)
+    at = {t: k for k, t in enumerate(times)}
+    anchors = {"t0": at[t_held], "short": at[t_held + short], "long": at[t_held + rollout]}
+    return times, [at[int(s)] for s in starts], at[t_held], anchors
+
+
+def make_snapshots(trainer, fine_edge, times, nu_fine, seed, umax=0.08, stream=None):
+    """Run the fine plain cumulant method (FP32, pull) and append one
+    restricted snapshot at each coarse time of `times` (non-decreasing).
+    Returns the fine MLUPS."""
     n = fine_edge
     rates = [I.shear_viscosity_rate(nu_fine)] + [1.0] * 5
     rho, u = I.fourier_modes((n, n, n), n_modes=8, umax=umax, seed=seed)
     with L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F32, L.PULL, rates,
                    (n, n, n), stream=stream) as fine:
         fine.init_velocity(rho.reshape(-1), u.reshape(-1))
-        trainer.add_restricted(fine)
+        del rho, u
         t0 = time.perf_counter()
-        for _ in range(nsnap - 1):
-            fine.step(4)
+        t = 0
+        for T in times:
+            fine.step(4 * (T - t))
+            t = T
             trainer.add_restricted(fine)
         dt = time.perf_counter() - t0
-    return n ** 3 * 4 * (nsnap - 1) / dt / 1e6
+    return n ** 3 * 4 * times[-1] / dt / 1e6
 
 
 def feature_normalisation(trainer, snaps):
@@ -59,13 +88,14 @@ def init_params(seed, scale=0.2):
     return p
 
 
-def mean_loss(trainer, pairs):
-    return float(np.mean([trainer.loss_grad(s)[0] for s in pairs]))
+def mean_loss(trainer, windows):
+    return float(np.mean([trainer.loss_grad(s)[0] for s in windows]))
 
 
-def rollout_error(trainer, s0, steps, omega_c, weights, stream=None):
-    """Relative L2 velocity error of `steps` coarse steps from snapshot s0
-    against the restricted fine snapshot s0 + steps."""
+def rollout_error(trainer, s0, steps, s1, omega_c, weights, stream=None):
+    """Relative L2 and L-infinity velocity errors of `steps` coarse steps
+    from snapshot s0 against snapshot s1 (the restricted fine state `steps`
+    coarse steps later)."""
     dims = trainer.dims
     with L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F32, L.PULL,
                    [omega_c] + [1.0] * 5, dims, stream=stream) as lat:
@@ -76,46 +106,48 @@ def rollout_error(trainer, s0, steps, omega_c, weights, stream=None):
         _, u = lat.macroscopic()
     with L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F64, L.PULL,
                    [omega_c] + [1.0] * 5, dims) as ref:
-        ref.set_populations(trainer.snapshot(s0 + steps))
+        ref.set_populations(trainer.snapshot(s1))
         _, ut = ref.macroscopic()
     return float(np.sqrt(((u - ut) ** 2).sum() / (ut ** 2).sum())), \
         float(np.abs(u - ut).max() / np.abs(ut).max())
 
 
-def train_and_evaluate(fine_edge=512, nsnap=160, ntrain=128, epochs=8, lr=3e-3, rollout=32,
-                       nu_fine=2e-4, seed=5, stream=None, log=None):
+def train_and_evaluate(fine_edge=512, span=1280, unroll=8, windows=24, epochs=6, lr=3e-3,
+                       rollout=256, short=64, nu_fine=2e-4, seed=5, stream=None, log=None):
+    """Fine run, restriction, training on the first 80 % of the span, and the
+    held-out evaluation.  Times (span, rollout, short) are coarse steps."""
     coarse = fine_edge // 4
     omega_c = I.shear_viscosity_rate(nu_fine / 4)
+    times, win_idx, held_idx, anchors = schedule(span, unroll, windows, rollout, short)
     out = {"fine": f"{fine_edge}^3", "coarse": f"{coarse}^3", "nu_fine": nu_fine,
-           "snapshots": nsnap, "train_pairs": ntrain - 1}
-    with L.Trainer((coarse,) * 3, omega_c, 1.0, nsnap, stream=stream) as tr:
-        out["fine_mlups"] = make_snapshots(tr, fine_edge, nsnap, nu_fine, seed, stream=stream)
-        shift, scale = feature_normalisation(tr, list(range(0, ntrain, max(1, ntrain // 4))))
-        train_pairs = list(range(ntrain - 1))
-        held = list(range(ntrain, nsnap - 1))
+           "span_coarse_steps": span, "unroll": unroll, "train_windows": len(win_idx),
+           "heldout_from_step": times[held_idx], "snapshots": len(times)}
+    with L.Trainer((coarse,) * 3, omega_c, 1.0, len(times), stream=stream) as tr:
+        out["fine_mlups"] = make_snapshots(tr, fine_edge, times, nu_fine, seed, stream=stream)
+        tr.set_unroll(unroll)
+        shift, scale = feature_normalisation(tr, win_idx[::max(1, len(win_idx) // 4)])
         tr.set_params(np.zeros(L.CLOSURE_NPARAM), shift, scale)
-        out["heldout_loss_plain"] = mean_loss(tr, held)
-        out["train_loss_initial"] = mean_loss(tr, train_pairs)
+        out["heldout_loss_plain"] = mean_loss(tr, [held_idx])
+        out["train_loss_initial"] = mean_loss(tr, win_idx)
         tr.set_params(init_params(seed), shift, scale)
         rng = np.random.default_rng(seed)
         t0 = time.perf_counter()
         steps = 0
         for ep in range(epochs):
-            losses = [tr.adam_step(int(s), lr) for s in rng.permutation(train_pairs)]
+            losses = [tr.adam_step(int(s), lr) for s in rng.permutation(win_idx)]
             steps += len(losses)
             if log:
                 log(f"epoch {ep}: mean train loss {np.mean(losses):.4e}")
         out["train_seconds"] = time.perf_counter() - t0
         out["adam_steps"] = steps
-        out["train_loss_final"] = mean_loss(tr, train_pairs)
-        out["heldout_loss_learned"] = mean_loss(tr, held)
+        out["train_loss_final"] = mean_loss(tr, win_idx)
+        out["heldout_loss_learned"] = mean_loss(tr, [held_idx])
         w = tr.export()
-        s0 = ntrain
-        steps_r = min(rollout, nsnap - 1 - s0)
-        out["rollout_steps"] = steps_r
-        e_l = rollout_error(tr, s0, steps_r, omega_c, w, stream)
-        e_p = rollout_error(tr, s0, steps_r, omega_c, None, stream)
-        out["rollout_err_learned"], out["rollout_linf_learned"] = e_l
-        out["rollout_err_plain"], out["rollout_linf_plain"] = e_p
+        s0 = anchors["t0"]
+        for key, length in (("short", short), ("long", rollout)):
+            e_l = rollout_error(tr, s0, length, anchors[key], omega_c, w, stream)
+            e_p = rollout_error(tr, s0, length, anchors[key], omega_c, None, stream)
+            out[f"rollout{length}_err_learned"], out[f"rollout{length}_linf_learned"] = e_l
+            out[f"rollout{length}_err_plain"], out[f"rollout{length}_linf_plain"] = e_p
         out["weights"] = w
     return out

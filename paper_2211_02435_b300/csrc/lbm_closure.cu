@@ -18,10 +18,12 @@
 
 namespace lbm {
 
-// FP32 inference network: tensor cores (1) or CUDA cores (0); a compile-time
-// choice, measured on B300
-#ifndef LBM_CLOSURE_TC
-#define LBM_CLOSURE_TC 0
+// FP32 inference network of the fused step, a compile-time choice measured
+// on B300: 0 CUDA cores (packed FFMA2), 1 warp-level tensor-core MMAs
+// (mma.sync, activations in registers between layers), 2 CTA-level
+// tcgen05 MMAs with the accumulators in tensor memory
+#ifndef LBM_CLOSURE_NET
+#define LBM_CLOSURE_NET 1
 #endif
 // minimum resident CTAs per SM asked of the fused learned-rate step kernel
 // (0: the compiler's choice, measured fastest on B300; 4 and 5 spill)
@@ -70,6 +72,37 @@ template <class T>
 LBM_D T sqrt_t(T x) {
   if constexpr (std::is_same<T, float>::value) return sqrtf(x);
   else return sqrt(x);
+}
+
+// ------------------------------------------------ forward-mode dual number
+// A value and one tangent.  The collision's templates run on it unchanged,
+// so one pass seeded with the unit tangent on population j gives column j of
+// the per-cell Jacobian d f* / d f (and d features / d f) exactly, up to
+// FP32 rounding; the training backward pass takes 27 such passes per cell.
+struct Dual {
+  float v, d;
+  Dual() = default;
+  LBM_D constexpr Dual(double x) : v(float(x)), d(0.f) {}
+  LBM_D constexpr Dual(float a, float b) : v(a), d(b) {}
+};
+LBM_D Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+LBM_D Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+LBM_D Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+LBM_D Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+LBM_D Dual operator/(Dual a, Dual b) {
+  const float q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+LBM_D Dual& operator+=(Dual& a, Dual b) { return a = a + b; }
+LBM_D Dual& operator-=(Dual& a, Dual b) { return a = a - b; }
+LBM_D Dual& operator*=(Dual& a, Dual b) { return a = a * b; }
+LBM_D bool operator>(Dual a, Dual b) { return a.v > b.v; }
+LBM_D bool operator<(Dual a, Dual b) { return a.v < b.v; }
+// d sqrt(x) = dx / (2 sqrt(x)); the features only take it of a sum of
+// squares, whose zero is handled by the caller
+LBM_D Dual sqrt_t(Dual x) {
+  const float r = sqrtf(x.v);
+  return Dual(r, r > 0.f ? 0.5f * x.d / r : 0.f);
 }
 
 // ----------------------------------------------------------- network
@@ -153,23 +186,35 @@ LBM_D void mlp_forward(const T* P, const T (&raw)[NIN], T (&x)[NIN], T (&h1)[NH]
 
 // ----------------------------------------------------------- features
 // raw inputs from the normalised second-order central deviations
-// (Pi = kappa_2/rho - I/3) and the density deviation
+// (Pi = kappa_2/rho - I/3) and the density deviation: the principal
+// invariants of S = -(3 omega_s / 2) Pi and of its deviator D, each of degree
+// k divided by the (k-1)-th power of its tensor's Frobenius norm (0 where the
+// norm is 0), so that all but the density are of degree 1 in Pi and
+// Lipschitz:  {tr S, I2(S)/|S|, det S/|S|^2, I2(D)/|D|, det D/|D|^2, |Pi|, drho}.
+// With |S| = (3 omega_s / 2)|Pi| the S quotients are formed from Pi's.
 template <class T>
 LBM_D void closure_features(const T (&K)[3][3][3], T drho, T omega_s, T (&raw)[NIN]) {
   const T a = K[2][0][0], b = K[0][2][0], c = K[0][0][2];
   const T p = K[1][1][0], q = K[1][0][1], r = K[0][1][1];
-  const T s = T(-1.5) * omega_s;
+  const T s = T(-1.5) * omega_s;  // S = s Pi, s < 0
+  const T off = p * p + q * q + r * r;
   const T trP = a + b + c;
-  const T i2P = a * b + b * c + c * a - p * p - q * q - r * r;
+  const T i2P = a * b + b * c + c * a - off;
   const T detP = a * (b * c - r * r) - p * (p * c - r * q) + q * (p * r - b * q);
+  const T n2P = a * a + b * b + c * c + T(2) * off;
   const T t3 = trP * T(1.0 / 3.0);
   const T da = a - t3, db = b - t3, dc = c - t3;
+  const T i2D = da * db + db * dc + dc * da - off;
+  const T detD = da * (db * dc - r * r) - p * (p * dc - r * q) + q * (p * r - db * q);
+  const T n2D = da * da + db * db + dc * dc + T(2) * off;
+  const T nP = sqrt_t(n2P), nD = sqrt_t(n2D);
+  const bool zP = !(n2P > T(0)), zD = !(n2D > T(0));
   raw[0] = s * trP;
-  raw[1] = s * s * i2P;
-  raw[2] = s * s * s * detP;
-  raw[3] = da * db + db * dc + dc * da - p * p - q * q - r * r;
-  raw[4] = da * (db * dc - r * r) - p * (p * dc - r * q) + q * (p * r - db * q);
-  raw[5] = sqrt_t(a * a + b * b + c * c + T(2) * (p * p + q * q + r * r));
+  raw[1] = zP ? T(0) : -s * i2P / nP;    // s^2 I2(Pi) / (|s| |Pi|)
+  raw[2] = zP ? T(0) : s * detP / n2P;   // s^3 det(Pi) / (s^2 |Pi|^2)
+  raw[3] = zD ? T(0) : i2D / nD;
+  raw[4] = zD ? T(0) : detD / n2D;
+  raw[5] = nP;
   raw[6] = drho;
 }
 
@@ -358,7 +403,8 @@ __global__ void LBM_CLOSURE_BOUNDS
 constexpr int TC_K1 = 32, TC_K2 = 3 * NH, TC_N3 = 16;
 constexpr int TC_B1 = 0, TC_B2 = TC_B1 + NH * TC_K1, TC_B3 = TC_B2 + NH * TC_K2;
 constexpr int TC_BELEMS = TC_B3 + TC_N3 * TC_K2;
-constexpr int TC_BOFF_BYTES = ((NSMEM * 4 + 127) / 128) * 128;  // packed B after the floats
+// packed B operands after the floats and the lane table of the mma.sync network
+constexpr int TC_BOFF_BYTES = ((NSMEM * 4 + 127) / 128) * 128 + ((42 * 32 * 4 + 127) / 128) * 128;
 constexpr int TC_TMEM_COLS = 32;
 
 // Pack the weights (FP32 values of BF16 numbers) into the three B operands.
@@ -540,6 +586,296 @@ __global__ void __launch_bounds__(128)
   if (warp == 0) umma::tmem_dealloc(tmem, TC_TMEM_COLS);
 }
 
+// --------------------------------- warp-level tensor-core network (FP32)
+// A warp's 32 cells (one per lane) are two 16-row tiles.  Layer l computes
+// D = A B + bias with A the activations and B[k][n] = W_l[n][k] (BF16 weights)
+// by mma.sync (m16n8k8 for the 7 inputs padded to 8, m16n8k16 above), FP32
+// accumulation.  Each FP32 activation enters as two BF16 parts, hi = bf16(a)
+// and lo = bf16(a - hi) (|a - hi - lo| <= 2^-17 |a|), each multiplied by the
+// same B, so every product is exact.  The accumulator fragments of two
+// adjacent n8 tiles are, element for element, the A fragment of the next
+// layer's k16 tile: the hidden activations never leave the registers; only
+// the 7 inputs and the 4 outputs pass through shared memory.
+namespace wmn {
+// per-lane table, word w of lane l at [w * 32 + l]
+constexpr int L1_B = 0;       // layer 1, n-tiles 0..3: B (k 2t, 2t+1; n 8j + g)
+constexpr int L2_B = 4;       // layer 2, (k-tile kk, n-tile j): 2 words at 4 + 2 (4 kk + j)
+constexpr int L3_B = 20;      // layer 3, k-tile kk: 2 words at 20 + 2 kk
+constexpr int L1_BIAS = 24;   // layer 1 bias of columns 8j + 2t + e at 24 + 2j + e
+constexpr int L2_BIAS = 32;   // layer 2, same layout
+constexpr int L3_BIAS = 40;   // layer 3 bias of columns 2t + e (0 for t >= 2)
+constexpr int WORDS = 42;
+// byte offset of the table in the device parameter image (after the floats)
+constexpr int TAB_OFF_BYTES = ((NSMEM * 4 + 127) / 128) * 128;
+constexpr int TAB_BYTES = WORDS * 32 * 4;
+
+// two floats as BF16 pairs: first element in the low half (the lower k)
+__device__ __forceinline__ uint32_t bf16x2(float first, float second) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(second), "f"(first));
+  return r;
+}
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  hi = bf16x2(a, b);
+  lo = bf16x2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xffff0000u));
+}
+__device__ __forceinline__ void mma_k16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                        uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
+      "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
+      "{%4, %5}, {%6}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(b0));
+}
+// tanh x = 1 - 2 / (1 + e^(2x)): exact at +-infinity (e^(2x) -> inf, 0),
+// absolute error ~2e-7 from the approximate exponential and reciprocal
+__device__ __forceinline__ float tanh_mma(float x) {
+  float e, r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x * 2.8853900817779268f));  // 2 / ln 2
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
+  return fmaf(-2.0f, r, 1.0f);
+}
+// the next layer's A fragments (hi and lo parts) of k-tile kk from the
+// accumulators D[mt][n-tile][4]
+__device__ __forceinline__ void next_a(const float (&D)[4][4], int kk, uint32_t (&ah)[4],
+                                       uint32_t (&al)[4]) {
+  split2(D[2 * kk][0], D[2 * kk][1], ah[0], al[0]);
+  split2(D[2 * kk][2], D[2 * kk][3], ah[1], al[1]);
+  split2(D[2 * kk + 1][0], D[2 * kk + 1][1], ah[2], al[2]);
+  split2(D[2 * kk + 1][2], D[2 * kk + 1][3], ah[3], al[3]);
+}
+
+// The network of the warp's 32 cells: x this lane's normalised inputs (x[7]
+// = 0), tab the lane table (shared memory), st 256 words of per-warp shared
+// staging; z receives this lane's 4 outputs.  All 32 lanes must call it.
+__device__ __forceinline__ void mlp_warp(const float (&x)[8], const uint32_t* __restrict__ tab,
+                                         uint32_t* st, float (&z)[4]) {
+  const int lane = threadIdx.x & 31, t = lane & 3, g = lane >> 2;
+  const uint32_t* T = tab + lane;
+  // layer 1: the inputs of every row to the fragment layout
+  {
+    uint4 h, l;
+    split2(x[0], x[1], h.x, l.x);
+    split2(x[2], x[3], h.y, l.y);
+    split2(x[4], x[5], h.z, l.z);
+    split2(x[6], x[7], h.w, l.w);
+    reinterpret_cast<uint4*>(st)[2 * lane] = h;
+    reinterpret_cast<uint4*>(st)[2 * lane + 1] = l;
+  }
+  __syncwarp();
+  float D[2][4][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    const int r0 = 16 * mt + g, r1 = r0 + 8;
+    const uint32_t h0 = st[8 * r0 + t], h1 = st[8 * r1 + t];
+    const uint32_t l0 = st[8 * r0 + 4 + t], l1 = st[8 * r1 + 4 + t];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float b0 = __uint_as_float(T[32 * (L1_BIAS + 2 * j)]);
+      const float b1 = __uint_as_float(T[32 * (L1_BIAS + 2 * j + 1)]);
+      D[mt][j][0] = b0, D[mt][j][1] = b1, D[mt][j][2] = b0, D[mt][j][3] = b1;
+      const uint32_t B = T[32 * (L1_B + j)];
+      mma_k8(D[mt][j], h0, h1, B);
+      mma_k8(D[mt][j], l0, l1, B);
+    }
+  }
+  __syncwarp();  // st is reused below
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) D[mt][j][e] = tanh_mma(D[mt][j][e]);
+  // layer 2
+  float E[2][4][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float b0 = __uint_as_float(T[32 * (L2_BIAS + 2 * j)]);
+      const float b1 = __uint_as_float(T[32 * (L2_BIAS + 2 * j + 1)]);
+      E[mt][j][0] = b0, E[mt][j][1] = b1, E[mt][j][2] = b0, E[mt][j][3] = b1;
+    }
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      uint32_t ah[4], al[4];
+      next_a(D[mt], kk, ah, al);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t B0 = T[32 * (L2_B + 2 * (4 * kk + j))];
+        const uint32_t B1 = T[32 * (L2_B + 2 * (4 * kk + j) + 1)];
+        mma_k16(E[mt][j], ah, B0, B1);
+        mma_k16(E[mt][j], al, B0, B1);
+      }
+    }
+  }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) E[mt][j][e] = tanh_mma(E[mt][j][e]);
+  // layer 3 (outputs in columns 0..3 of one n8 tile)
+  float F[2][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    const float b0 = __uint_as_float(T[32 * L3_BIAS]), b1 = __uint_as_float(T[32 * (L3_BIAS + 1)]);
+    F[mt][0] = b0, F[mt][1] = b1, F[mt][2] = b0, F[mt][3] = b1;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      uint32_t ah[4], al[4];
+      next_a(E[mt], kk, ah, al);
+      const uint32_t B0 = T[32 * (L3_B + 2 * kk)], B1 = T[32 * (L3_B + 2 * kk + 1)];
+      mma_k16(F[mt], ah, B0, B1);
+      mma_k16(F[mt], al, B0, B1);
+    }
+  }
+  // back to one row per lane: lane (g, t) holds row g (F[..][0..1]) and row
+  // g + 8 (F[..][2..3]) at columns 2t, 2t + 1
+  float* sf = reinterpret_cast<float*>(st);
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) sf[8 * lane + 4 * mt + e] = F[mt][e];
+  __syncwarp();
+  {
+    const int mt = lane >> 4, r = lane & 15, gg = r & 7, hf = r >> 3;
+    const float* a = sf + 8 * (4 * gg) + 4 * mt + 2 * hf;      // t = 0: columns 0, 1
+    const float* b = sf + 8 * (4 * gg + 1) + 4 * mt + 2 * hf;  // t = 1: columns 2, 3
+    z[0] = a[0], z[1] = a[1], z[2] = b[0], z[3] = b[1];
+  }
+  __syncwarp();
+}
+}  // namespace wmn
+
+// Pack the weights (FP32 values of BF16 numbers) and biases into the lane
+// table of mlp_warp.
+inline void pack_lane_table(const float* P, uint32_t* tab) {
+  auto bits = [](float v) {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    return u >> 16;  // exact: v is a BF16 value
+  };
+  auto pair = [&](float first, float second) { return bits(first) | (bits(second) << 16); };
+  auto fbits = [](float v) {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    return u;
+  };
+  auto W1 = [&](int n, int k) { return k < NIN ? P[OW1 + n * NIN + k] : 0.f; };
+  auto W2 = [&](int n, int k) { return P[OW2 + n * NH + k]; };
+  auto W3 = [&](int n, int k) { return n < NOUT ? P[OW3 + n * NH + k] : 0.f; };
+  for (int l = 0; l < 32; ++l) {
+    const int g = l >> 2, t = l & 3;
+    auto at = [&](int w) -> uint32_t& { return tab[w * 32 + l]; };
+    for (int j = 0; j < 4; ++j) at(wmn::L1_B + j) = pair(W1(8 * j + g, 2 * t), W1(8 * j + g, 2 * t + 1));
+    for (int kk = 0; kk < 2; ++kk)
+      for (int j = 0; j < 4; ++j) {
+        const int n = 8 * j + g, k = 16 * kk + 2 * t;
+        at(wmn::L2_B + 2 * (4 * kk + j)) = pair(W2(n, k), W2(n, k + 1));
+        at(wmn::L2_B + 2 * (4 * kk + j) + 1) = pair(W2(n, k + 8), W2(n, k + 9));
+      }
+    for (int kk = 0; kk < 2; ++kk) {
+      const int k = 16 * kk + 2 * t;
+      at(wmn::L3_B + 2 * kk) = pair(W3(g, k), W3(g, k + 1));
+      at(wmn::L3_B + 2 * kk + 1) = pair(W3(g, k + 8), W3(g, k + 9));
+    }
+    for (int j = 0; j < 4; ++j)
+      for (int e = 0; e < 2; ++e) {
+        at(wmn::L1_BIAS + 2 * j + e) = fbits(P[OB1 + 8 * j + 2 * t + e]);
+        at(wmn::L2_BIAS + 2 * j + e) = fbits(P[OB2 + 8 * j + 2 * t + e]);
+      }
+    for (int e = 0; e < 2; ++e)
+      at(wmn::L3_BIAS + e) = fbits(2 * t + e < NOUT ? P[OB3 + 2 * t + e] : 0.f);
+  }
+}
+
+// fused pull step with the learned rates, FP32, the network on warp-level
+// MMAs; a persistent grid walks tiles of 128 cells of one x-row.  The
+// gather uses per-plane pointers pre-shifted by the interior stencil offset
+// (as the plain pull kernel), so a load is src_i[c + wrap_i].
+__global__ void LBM_CLOSURE_BOUNDS
+    k_closure_pull_mma(const __grid_constant__ PullPtrs<float> P, Geo g, Rates<float> keep,
+                       const float* __restrict__ params, int tiles_x, int ntiles) {
+  __shared__ __align__(16) uint32_t tab[wmn::WORDS * 32];
+  __shared__ __align__(16) uint32_t stage[4][256];
+  __shared__ float nrm[2 * NIN];
+  {
+    const uint32_t* gt = reinterpret_cast<const uint32_t*>(
+        reinterpret_cast<const char*>(params) + wmn::TAB_OFF_BYTES);
+    for (int k = threadIdx.x; k < wmn::WORDS * 32; k += 128) tab[k] = gt[k];
+    if (threadIdx.x < 2 * NIN) nrm[threadIdx.x] = params[NPARAM + threadIdx.x];
+  }
+  __syncthreads();
+  uint32_t* st = stage[threadIdx.x >> 5];
+  const float omega_s = 1.0f - keep.om[0];
+  const int nxy = g.nx * g.ny;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int x = (tile % tiles_x) * 128 + int(threadIdx.x);
+    const int row = tile / tiles_x;
+    const int y = row % g.ny, z = row / g.ny;
+    const bool active = x < g.nx;
+    const int c = row * g.nx + (active ? x : 0);
+    float f[27];
+    CumState<float> s;
+    float xin[8];
+    bool ok = true;
+    if (active) {
+      // wrap corrections for a read at x - xi (xi = +1 reads x - 1)
+      const int wxp = x == 0 ? g.nx : 0, wxm = x == g.nx - 1 ? -g.nx : 0;
+      const int wyp = y == 0 ? nxy : 0, wym = y == g.ny - 1 ? -nxy : 0;
+      const int wzp = z == 0 ? int(g.N) : 0, wzm = z == g.nz - 1 ? -int(g.N) : 0;
+      sfor<27>([&](auto I) {
+        constexpr int i = CI(I);
+        constexpr int cx = vel(D3Q27, i, 0), cy = vel(D3Q27, i, 1), cz = vel(D3Q27, i, 2);
+        const int w = (cx > 0 ? wxp : (cx < 0 ? wxm : 0)) + (cy > 0 ? wyp : (cy < 0 ? wym : 0)) +
+                      (cz > 0 ? wzp : (cz < 0 ? wzm : 0));
+        f[i] = P.src[i][c + w];
+      });
+      cum_forward<float>(f, s);
+      float raw[NIN];
+      closure_features<float>(s.Kn, s.drho, omega_s, raw);
+#pragma unroll
+      for (int i = 0; i < NIN; ++i) {
+        xin[i] = (raw[i] - nrm[i]) * nrm[NIN + i];
+        ok = ok && isfinite(xin[i]);
+      }
+      if (!ok)
+#pragma unroll
+        for (int i = 0; i < NIN; ++i) xin[i] = 0.f;
+    } else {
+#pragma unroll
+      for (int i = 0; i < NIN; ++i) xin[i] = 0.f;
+    }
+    xin[7] = 0.f;
+    float zz[4];
+    wmn::mlp_warp(xin, tab, st, zz);
+    if (active) {
+      Rates<float> k = keep;
+#pragma unroll
+      for (int o = 0; o < NOUT; ++o) {
+        const float sg = 1.0f / (1.0f + __expf(-zz[o]));
+        float om = 2.0f * sg;
+        om = om < 1e-3f ? 1e-3f : om;
+        om = om > 1.999f ? 1.999f : om;
+        ok = ok && isfinite(om);
+        k.om[2 + o] = 1.0f - om;
+      }
+      if (!ok)
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) k.om[2 + o] = 0.0f;  // rates 1
+      float Cs[3][3][3];
+      cum_backward<float>(s, k, Cs, f);
+      sfor<27>([&](auto I) { P.dst[CI(I)][c] = f[CI(I)]; });
+    }
+  }
+}
+
 // 4^3 block average of the canonical populations of a fine lattice
 template <class S, class T, int MODE>
 __global__ void __launch_bounds__(128)
@@ -576,17 +912,24 @@ __global__ void __launch_bounds__(128)
   for (int k = 0; k < NIN; ++k) feat[(int64_t)k * g.N + c] = raw[k];
 }
 
-// training forward: post-collision populations f* of every cell of a
-// canonical snapshot (the pull layout of the next step)
+// training forward, step k of the unrolled rollout: post-collision
+// populations f* of every cell, from the snapshot itself (SRC_PULL false, the
+// first step) or from the pull gather of the previous step's f* (the
+// pre-collision state of the next step).  Written in the pull layout of the
+// next step.
+template <bool SRC_PULL>
 __global__ void __launch_bounds__(128)
-    k_closure_fwd(const float* __restrict__ snap, Geo g, Rates<float> keep,
+    k_closure_fwd(const float* __restrict__ fsrc, Geo g, Rates<float> keep,
                   const float* __restrict__ params, float* __restrict__ fstar) {
   __shared__ float sp[NSMEM];
   load_params(sp, params);
   const int64_t c = (int64_t)blockIdx.x * 128 + threadIdx.x;
   if (c >= g.N) return;
+  int x, y, z;
+  cell_xyz(int(c), g, x, y, z);
+  const Nbr n = neighbours(x, y, z, g);
   float f[27];
-  sfor<27>([&](auto I) { f[CI(I)] = snap[(int64_t)CI(I) * g.N + c]; });
+  load_pops<D3Q27, float, float, SRC_PULL ? G_PULL : G_LOCAL>(fsrc, g, n, int(c), f);
   CumState<float> s;
   cum_forward<float>(f, s);
   float raw[NIN], xin[NIN], h1[NH], h2[NH], om[NOUT], dom[NOUT];
@@ -599,13 +942,13 @@ __global__ void __launch_bounds__(128)
   sfor<27>([&](auto I) { fstar[(int64_t)CI(I) * g.N + c] = f[CI(I)]; });
 }
 
-// loss of one step and the adjoint seed: per cell y of the streamed state,
-// r(y) = 2/N (u - u_target) / rho and u(y) (6 floats, SoA), plus per-block
-// partial sums of |u - u_target|^2
+// loss of one step and its adjoint seed: per cell y of the streamed state,
+// r(y) = 2 wk/N (u - u_target) / rho and u(y) (6 floats, SoA), plus per-block
+// partial sums of wk |u - u_target|^2 / N (wk: the step's weight, 1/K)
 constexpr int LOSS_THREADS = 256;
 __global__ void __launch_bounds__(LOSS_THREADS)
     k_closure_loss(const float* __restrict__ fstar, const float* __restrict__ target, Geo g,
-                   float* __restrict__ r6, double* __restrict__ part) {
+                   float* __restrict__ r6, double* __restrict__ part, double wk) {
   __shared__ double sh[LOSS_THREADS];
   double acc = 0.0;
   const double invN = 1.0 / double(g.N);
@@ -630,7 +973,7 @@ __global__ void __launch_bounds__(LOSS_THREADS)
     for (int d = 0; d < 3; ++d) {
       const double u = j[d] / rho, ut = jt[d] / rhot;
       acc += (u - ut) * (u - ut);
-      r6[(int64_t)d * g.N + c] = float(2.0 * invN * (u - ut) / rho);
+      r6[(int64_t)d * g.N + c] = float(2.0 * wk * invN * (u - ut) / rho);
       r6[(int64_t)(3 + d) * g.N + c] = float(u);
     }
   }
@@ -640,7 +983,7 @@ __global__ void __launch_bounds__(LOSS_THREADS)
     if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = sh[0] * invN;
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0] * invN * wk;
 }
 
 __global__ void k_fold_sum(const double* __restrict__ part, int n, int stride, int width,
@@ -653,17 +996,58 @@ __global__ void k_fold_sum(const double* __restrict__ part, int n, int stride, i
   out[k] = s;
 }
 
-// training backward.  64 threads per block; every thread takes one cell
-// per round, computes dL/domega through the tangents and the MLP backward,
-// stages its activations and deltas in shared memory, then each thread
-// accumulates the products of the parameters it owns over the round's 64
-// cells.  One partial row of NPARAM doubles per block.
+// dL/df_j of one cell through its collision: sum_i lam_i d f*_i / d f_j at
+// the cell's rates held fixed, plus sum_m lraw_m d raw_m / d f_j (the path
+// through the rates, lraw = dL/d raw from the network's input gradient).
+// One dual-number pass per j.
+__device__ __noinline__ void collision_vjp(const float (&f)[27], const Rates<float>& k,
+                                           float omega_s, const float (&lam)[27],
+                                           const float (&lraw)[NIN], float* out,
+                                           int64_t stride) {
+  Rates<Dual> kd;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) kd.om[q] = Dual(k.om[q], 0.f);
+#pragma unroll 1
+  for (int j = 0; j < 27; ++j) {
+    Dual fd[27];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) fd[i] = Dual(f[i], i == j ? 1.f : 0.f);
+    CumState<Dual> sd;
+    cum_forward<Dual>(fd, sd);
+    Dual rawd[NIN];
+    closure_features<Dual>(sd.Kn, sd.drho, Dual(omega_s, 0.f), rawd);
+    Dual Csd[3][3][3];
+    cum_backward<Dual>(sd, kd, Csd, fd);
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) acc += lam[i] * fd[i].d;
+#pragma unroll
+    for (int m = 0; m < NIN; ++m) acc += lraw[m] * rawd[m].d;
+    out[(int64_t)j * stride] = acc;
+  }
+}
+
+// training backward, step k of the unrolled rollout (the steps are taken
+// from the last back to the first).  64 threads per block; every thread
+// takes one cell x per round:
+//   f      = f(t+k)(x), the snapshot (SRC_PULL false) or the pull gather of
+//            the previous step's f*, and its collision with the network
+//   lam_i  = dL/df*_i(x) = lnext_i(x + xi_i) + the seed of the velocity loss
+//            of step k+1 at x + xi_i (lnext: dL/df(t+k+1), null for the
+//            last step)
+//   dL/domega through the tangents d f*/d omega_k, then the MLP backward;
+//   every thread accumulates the products of the parameters it owns over
+//   the round's 64 cells (activations and deltas staged in shared memory).
+//   lout (not null): dL/df(t+k)(x) for the step before (collision_vjp).
+// One partial row of NPARAM doubles per block, written or accumulated.
 constexpr int BWD_THREADS = 64;
 constexpr int BWD_PER_THREAD = (NPARAM + BWD_THREADS - 1) / BWD_THREADS;  // 23
+template <bool SRC_PULL>
 __global__ void __launch_bounds__(BWD_THREADS)
-    k_closure_bwd(const float* __restrict__ snap, const float* __restrict__ r6, Geo g,
+    k_closure_bwd(const float* __restrict__ fsrc, const float* __restrict__ r6,
+                  const float* __restrict__ lnext, float* __restrict__ lout, Geo g,
                   Rates<float> keep, const float* __restrict__ params,
-                  double* __restrict__ gpart) {
+                  double* __restrict__ gpart, int accumulate) {
   __shared__ float sp[NSMEM];
   __shared__ float s_x[BWD_THREADS][NIN + 1];
   __shared__ float s_h1[BWD_THREADS][NH + 1];
@@ -675,6 +1059,7 @@ __global__ void __launch_bounds__(BWD_THREADS)
   double acc[BWD_PER_THREAD];
   for (int k = 0; k < BWD_PER_THREAD; ++k) acc[k] = 0.0;
   const int tid = threadIdx.x;
+  const float omega_s = 1.0f - keep.om[0];
   const int64_t rounds = (g.N + (int64_t)gridDim.x * BWD_THREADS - 1) / ((int64_t)gridDim.x * BWD_THREADS);
   for (int64_t rd = 0; rd < rounds; ++rd) {
     const int64_t c = (rd * gridDim.x + blockIdx.x) * BWD_THREADS + tid;
@@ -683,26 +1068,26 @@ __global__ void __launch_bounds__(BWD_THREADS)
     for (int i = 0; i < NH; ++i) h1[i] = h2[i] = d1[i] = d2[i] = 0.f;
     for (int i = 0; i < NOUT; ++i) dz[i] = 0.f;
     if (c < g.N) {
+      int x, y, z;
+      cell_xyz(int(c), g, x, y, z);
+      const Nbr n = neighbours(x, y, z, g);
       float f[27];
-      sfor<27>([&](auto I) { f[CI(I)] = snap[(int64_t)CI(I) * g.N + c]; });
+      load_pops<D3Q27, float, float, SRC_PULL ? G_PULL : G_LOCAL>(fsrc, g, n, int(c), f);
       CumState<float> s;
       cum_forward<float>(f, s);
       float raw[NIN], om[NOUT], dom[NOUT];
-      closure_features<float>(s.Kn, s.drho, 1.0f - keep.om[0], raw);
+      closure_features<float>(s.Kn, s.drho, omega_s, raw);
       mlp_forward<float>(sp, raw, xin, h1, h2, om, dom);
       Rates<float> k = keep;
       for (int o = 0; o < NOUT; ++o) k.om[2 + o] = 1.0f - om[o];
       float Cs[3][3][3], post[27];
       cum_backward<float>(s, k, Cs, post);
-      // adjoint of streaming and of the velocity: lambda_i = dL/df*_i(x)
-      int x, y, z;
-      cell_xyz(int(c), g, x, y, z);
-      const Nbr n = neighbours(x, y, z, g);
+      // adjoint of streaming and of the velocity: lam_i = dL/df*_i(x)
       float lam[27];
       sfor<27>([&](auto I) {
         constexpr int i = CI(I);
         const int yc = cell_at(n, g, vel(D3Q27, i, 0), vel(D3Q27, i, 1), vel(D3Q27, i, 2));
-        float l = 0.f;
+        float l = lnext ? lnext[(int64_t)i * g.N + yc] : 0.f;
         for (int d = 0; d < 3; ++d)
           l += r6[(int64_t)d * g.N + yc] *
                (float(vel(D3Q27, i, d)) - r6[(int64_t)(3 + d) * g.N + yc]);
@@ -731,6 +1116,16 @@ __global__ void __launch_bounds__(BWD_THREADS)
         float a = 0.f;
         for (int j = 0; j < NH; ++j) a += sp[OW2 + j * NH + i] * d2[j];
         d1[i] = a * (1.f - h1[i] * h1[i]);
+      }
+      if (lout) {
+        // the network's input gradient: x = (raw - shift) * scale
+        float lraw[NIN];
+        for (int m = 0; m < NIN; ++m) {
+          float a = 0.f;
+          for (int r = 0; r < NH; ++r) a += sp[OW1 + r * NIN + m] * d1[r];
+          lraw[m] = a * sp[NPARAM + NIN + m];
+        }
+        collision_vjp(f, k, omega_s, lam, lraw, lout + c, g.N);
       }
     }
     for (int i = 0; i < NIN; ++i) s_x[tid][i] = xin[i];
@@ -768,7 +1163,9 @@ __global__ void __launch_bounds__(BWD_THREADS)
   }
   for (int kk = 0; kk < BWD_PER_THREAD; ++kk) {
     const int p = tid + kk * BWD_THREADS;
-    if (p < NPARAM) gpart[(int64_t)blockIdx.x * NPARAM + p] = acc[kk];
+    if (p >= NPARAM) continue;
+    double* dst = gpart + (int64_t)blockIdx.x * NPARAM + p;
+    *dst = accumulate ? *dst + acc[kk] : acc[kk];
   }
 }
 
@@ -808,9 +1205,33 @@ void launch_closure_step(const StepArgs& a, const void* closure) {
   } else {
     Rates<float> keep;
     for (int k = 0; k < 6; ++k) keep.om[k] = float(1.0 - a.rates[k]);
-#if LBM_CLOSURE_TC
+#if LBM_CLOSURE_NET == 2
     k_closure_pull_tc<<<grid, 128, 0, a.stream>>>((const float*)a.src, (float*)a.dst, a.g, keep,
                                                    (const float*)closure, a.status);
+#elif LBM_CLOSURE_NET == 1
+    static int resident = 0;  // CTAs per SM x SMs, once per process
+    if (!resident) {
+      int dev = 0, sms = 0, occ = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_closure_pull_mma, 128, 0) !=
+              cudaSuccess ||
+          occ < 1)
+        occ = 1;
+      resident = sms * occ;
+    }
+    const int tiles_x = (a.g.nx + 127) / 128;
+    const int ntiles = tiles_x * a.g.ny * a.g.nz;  // < 2^31: N < 2^31
+    const int blocks = ntiles < resident ? ntiles : resident;
+    PullPtrs<float> P;
+    const int64_t nx = a.g.nx, nxy = int64_t(a.g.nx) * a.g.ny;
+    for (int i = 0; i < 27; ++i) {
+      const int64_t delta = -(vel(D3Q27, i, 2) * nxy + vel(D3Q27, i, 1) * nx + vel(D3Q27, i, 0));
+      P.src[i] = (const float*)a.src + (int64_t(i) * a.g.N + delta);
+      P.dst[i] = (float*)a.dst + int64_t(i) * a.g.N;
+    }
+    k_closure_pull_mma<<<blocks, 128, 0, a.stream>>>(P, a.g, keep, (const float*)closure, tiles_x,
+                                                     ntiles);
 #else
     k_closure_pull<float, float><<<grid, 128, 0, a.stream>>>((const float*)a.src, (float*)a.dst,
                                                              a.g, keep, (const float*)closure);
@@ -851,10 +1272,12 @@ struct lbm_trainer {
   Geo g;
   double omega_s, omega_b;
   int cap, count;
+  int unroll;      // K: steps of the rollout loss
   float* snaps;
-  float* fstar;
-  float* r6;
-  double* lpart;
+  float* fstar;    // K post-collision fields, 27 N each
+  float* r6;       // K loss seeds, 6 N each
+  float* lam[2];   // dL/df of two consecutive steps (K > 1), 27 N each
+  double* lpart;   // K rows of lblocks loss partials
   int lblocks;
   double* gpart;
   int gblocks;
@@ -893,9 +1316,11 @@ int lbm_set_closure(lbm_ctx* c, const lbm_closure_weights* w) {
     hd[NPARAM + k] = w->shift[k];
     hd[NPARAM + NIN + k] = w->scale[k];
   }
-  // FP32: the float parameters, then the packed tensor-core B operands
+  // FP32: the float parameters, the lane table of the warp-level network,
+  // then the packed B operands of the tcgen05 network
   const size_t bytes = dbl ? lbm::NSMEM * sizeof(double)
                            : size_t(lbm::TC_BOFF_BYTES) + lbm::TC_BELEMS * sizeof(uint16_t);
+  static_assert(lbm::wmn::TAB_OFF_BYTES + lbm::wmn::TAB_BYTES <= lbm::TC_BOFF_BYTES, "layout");
   void* dev = nullptr;
   if (cudaMalloc(&dev, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -908,6 +1333,8 @@ int lbm_set_closure(lbm_ctx* c, const lbm_closure_weights* w) {
     std::vector<unsigned char> img(bytes, 0);
     std::vector<float> hf(hd.begin(), hd.end());
     std::memcpy(img.data(), hf.data(), hf.size() * sizeof(float));
+    lbm::pack_lane_table(hf.data(),
+                         reinterpret_cast<uint32_t*>(img.data() + lbm::wmn::TAB_OFF_BYTES));
     lbm::pack_tc_weights(hf.data(),
                          reinterpret_cast<uint16_t*>(img.data() + lbm::TC_BOFF_BYTES));
     rc = cuda_err(cudaMemcpy(dev, img.data(), bytes, cudaMemcpyHostToDevice));
@@ -928,8 +1355,8 @@ void lbm_trainer_destroy(lbm_trainer* t) {
   if (!t) return;
   if (t->stream) cudaStreamSynchronize(t->stream);
   else cudaDeviceSynchronize();
-  void* ptrs[] = {t->snaps, t->fstar, t->r6, t->lpart, t->gpart, t->grad, t->loss,
-                  t->master, t->rounded, t->m1, t->m2};
+  void* ptrs[] = {t->snaps, t->fstar, t->r6, t->lam[0], t->lam[1], t->lpart, t->gpart,
+                  t->grad, t->loss, t->master, t->rounded, t->m1, t->m2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete t;
@@ -960,6 +1387,7 @@ int lbm_trainer_create(lbm_trainer** out, const int64_t dims[3], double omega_s,
   t->omega_s = omega_s;
   t->omega_b = omega_b;
   t->cap = max_snapshots;
+  t->unroll = 1;
   t->stream = (cudaStream_t)stream;
   const int64_t lb = (N + lbm::LOSS_THREADS - 1) / lbm::LOSS_THREADS;
   t->lblocks = int(lb < 1184 ? lb : 1184);
@@ -995,6 +1423,39 @@ int lbm_trainer_create(lbm_trainer** out, const int64_t dims[3], double omega_s,
     return rc;
   }
   *out = t;
+  return LBM_OK;
+}
+
+int lbm_trainer_set_unroll(lbm_trainer* t, int K) {
+  if (!t || K < 1 || K > LBM_CLOSURE_MAX_UNROLL || K + 1 > t->cap) return LBM_ERR_INVALID;
+  if (K == t->unroll) return LBM_OK;
+  if (t->stream) cudaStreamSynchronize(t->stream);
+  else cudaDeviceSynchronize();
+  const size_t N = size_t(t->g.N);
+  float *fstar = nullptr, *r6 = nullptr, *lam0 = nullptr, *lam1 = nullptr;
+  double* lpart = nullptr;
+  bool ok = cudaMalloc((void**)&fstar, sizeof(float) * 27 * N * K) == cudaSuccess &&
+            cudaMalloc((void**)&r6, sizeof(float) * 6 * N * K) == cudaSuccess &&
+            cudaMalloc((void**)&lpart, sizeof(double) * size_t(t->lblocks) * K) == cudaSuccess;
+  if (ok && K > 1)
+    ok = cudaMalloc((void**)&lam0, sizeof(float) * 27 * N) == cudaSuccess &&
+         cudaMalloc((void**)&lam1, sizeof(float) * 27 * N) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    void* ptrs[] = {fstar, r6, lpart, lam0, lam1};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    return LBM_ERR_OOM;  // the trainer keeps its previous unroll
+  }
+  void* old[] = {t->fstar, t->r6, t->lpart, t->lam[0], t->lam[1]};
+  for (void* p : old)
+    if (p) cudaFree(p);
+  t->fstar = fstar;
+  t->r6 = r6;
+  t->lpart = lpart;
+  t->lam[0] = lam0;
+  t->lam[1] = lam1;
+  t->unroll = K;
   return LBM_OK;
 }
 
@@ -1118,23 +1579,45 @@ static int enqueue_loss_grad(lbm_trainer* t, int s) {
   keep.om[0] = float(1.0 - t->omega_s);
   keep.om[1] = float(1.0 - t->omega_b);
   for (int k = 2; k < 6; ++k) keep.om[k] = 0.f;
+  const int K = t->unroll;
   const size_t n = 27 * size_t(t->g.N);
   const float* snap = t->snaps + size_t(s) * n;
-  const float* target = snap + n;
   const int blocks = int((t->g.N + 127) / 128);
-  lbm::k_closure_fwd<<<blocks, 128, 0, t->stream>>>(snap, t->g, keep, t->rounded, t->fstar);
-  lbm::k_closure_loss<<<t->lblocks, lbm::LOSS_THREADS, 0, t->stream>>>(t->fstar, target, t->g,
-                                                                       t->r6, t->lpart);
-  lbm::k_fold_sum<<<1, 32, 0, t->stream>>>(t->lpart, t->lblocks, 1, 1, t->loss);
-  lbm::k_closure_bwd<<<t->gblocks, lbm::BWD_THREADS, 0, t->stream>>>(snap, t->r6, t->g, keep,
-                                                                     t->rounded, t->gpart);
+  auto fst = [&](int k) { return t->fstar + size_t(k) * n; };
+  auto r6k = [&](int k) { return t->r6 + size_t(k) * 6 * t->g.N; };
+  // forward: K learned-rate steps from snapshot s, the loss of each against
+  // snapshot s + k + 1 with weight 1/K
+  for (int k = 0; k < K; ++k) {
+    if (k == 0)
+      lbm::k_closure_fwd<false><<<blocks, 128, 0, t->stream>>>(snap, t->g, keep, t->rounded, fst(0));
+    else
+      lbm::k_closure_fwd<true><<<blocks, 128, 0, t->stream>>>(fst(k - 1), t->g, keep, t->rounded,
+                                                              fst(k));
+    lbm::k_closure_loss<<<t->lblocks, lbm::LOSS_THREADS, 0, t->stream>>>(
+        fst(k), snap + size_t(k + 1) * n, t->g, r6k(k), t->lpart + size_t(k) * t->lblocks,
+        1.0 / K);
+  }
+  lbm::k_fold_sum<<<1, 32, 0, t->stream>>>(t->lpart, t->lblocks * K, 1, 1, t->loss);
+  // backward: the steps from the last to the first; dL/df of the state a
+  // step starts from goes to the step before it
+  for (int k = K - 1; k >= 0; --k) {
+    const float* lnext = k == K - 1 ? nullptr : t->lam[(k + 1) & 1];
+    float* lout = k == 0 ? nullptr : t->lam[k & 1];
+    const int acc = k != K - 1;
+    if (k == 0)
+      lbm::k_closure_bwd<false><<<t->gblocks, lbm::BWD_THREADS, 0, t->stream>>>(
+          snap, r6k(0), lnext, lout, t->g, keep, t->rounded, t->gpart, acc);
+    else
+      lbm::k_closure_bwd<true><<<t->gblocks, lbm::BWD_THREADS, 0, t->stream>>>(
+          fst(k - 1), r6k(k), lnext, lout, t->g, keep, t->rounded, t->gpart, acc);
+  }
   lbm::k_fold_sum<<<(NPARAM + 127) / 128, 128, 0, t->stream>>>(t->gpart, t->gblocks, NPARAM,
                                                                 NPARAM, t->grad);
   return cuda_err(cudaGetLastError());
 }
 
 int lbm_trainer_loss_grad(lbm_trainer* t, int s, double* loss, double* grad) {
-  if (!t || s < 0 || s + 1 >= t->count) return LBM_ERR_INVALID;
+  if (!t || s < 0 || s + t->unroll >= t->count) return LBM_ERR_INVALID;
   int rc = enqueue_loss_grad(t, s);
   if (rc == LBM_OK && loss)
     rc = cuda_err(cudaMemcpyAsync(loss, t->loss, sizeof(double), cudaMemcpyDeviceToHost, t->stream));
@@ -1146,7 +1629,7 @@ int lbm_trainer_loss_grad(lbm_trainer* t, int s, double* loss, double* grad) {
 }
 
 int lbm_trainer_adam_step(lbm_trainer* t, int s, double lr, double* loss) {
-  if (!t || s < 0 || s + 1 >= t->count || !(lr > 0)) return LBM_ERR_INVALID;
+  if (!t || s < 0 || s + t->unroll >= t->count || !(lr > 0)) return LBM_ERR_INVALID;
   int rc = enqueue_loss_grad(t, s);
   if (rc != LBM_OK) return rc;
   t->adam_t++;

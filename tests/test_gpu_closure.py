@@ -71,19 +71,18 @@ def rel_linf(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
-# Input scales that make every normalised input O(1) for this flow without
-# amplifying rounding: the raw features are ~1e-2 (tr S), 1e-5 (I2 S), 1e-8
-# (det S), 1e-6 (I2 D), 1e-9 (det D), 1e-3 (|Pi|), 1e-3 (drho).
-FIXED_SCALE = np.array([1e2, 1e4, 1e6, 1e5, 1e7, 1e2, 1e2])
+# Fixed input scales that make every normalised input O(1) for this flow:
+# the conditioned features are all of degree 1 in Pi, ~3e-3 for those of S,
+# ~1e-3 for those of D and |Pi|, ~1e-3 for drho.
+FIXED_SCALE = np.array([1e2, 1e2, 1e2, 1e3, 1e3, 1e3, 1e2])
 
 
+# Data-derived scales (1/std of each feature over the lattice) are of the
+# same order as the fixed ones, since every conditioned feature has the
+# magnitude of Pi: both are held to the stencil's FP64 / FP32 tolerance.
 @pytest.mark.parametrize("norm,storage,tol", [
     ("fixed", L.STORE_F64, 1e-12), ("fixed", L.STORE_F32, 1e-5),
-    # Data-derived scales reach 1e11 (1/std of det D): the oracle's features
-    # come from absolute second moments (kappa ~ 1/3) whose FP64 rounding,
-    # ~1e-16 absolute, the scale turns into rate differences of ~1e-10 and
-    # f* differences of ~1e-11 relative; hence 1e-9 for FP64 in that case.
-    ("data", L.STORE_F64, 1e-9), ("data", L.STORE_F32, 1e-5)])
+    ("data", L.STORE_F64, 1e-12), ("data", L.STORE_F32, 1e-5)])
 def test_fused_learned_step_matches_oracle(norm, storage, tol):
     dims = (21, 7, 6)
     df = noisy_state(dims, 1)
@@ -108,8 +107,7 @@ def test_fused_learned_step_matches_oracle(norm, storage, tol):
             one = O.closure_step(base, dims, prev, params, sh32, sc32)
             assert rel_linf(got, one) < tol, n
             ref = O.closure_step(base, dims, ref, params, sh32, sc32)
-            if norm == "fixed":  # with 1e11 scales the multi-step run is ill-conditioned
-                assert rel_linf(got, ref) < tol, n
+            assert rel_linf(got, ref) < tol, n
             prev = got
         # disabling the closure returns to the plain regularised method
         lat.set_closure(None)
@@ -216,6 +214,53 @@ def test_loss_and_gradient_match_oracle_finite_differences():
     assert np.all(np.abs(g - fd) <= 2e-3 * gmax + 2e-3 * np.abs(fd)), np.c_[idx, g, fd]
 
 
+@pytest.mark.parametrize("K", [2, 3])
+def test_rollout_loss_and_gradient_match_oracle_finite_differences(K):
+    """K-step unrolled loss: the GPU's loss against the oracle's, and its
+    gradient (adjoint through the K collisions and streamings) against
+    central finite differences of the oracle's FP64 K-step loss."""
+    dims = (7, 6, 5)
+    states = [noisy_state(dims, 31 + k) for k in range(K + 1)]
+    shift, scale = normalisation(states[0], dims)
+    shift = np.float32(shift).astype(np.float64)
+    scale = np.float32(scale).astype(np.float64)
+    params = random_params(17, 0.5)
+    base = O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [OMEGA_S, 1.0, 0.0, 0.0, 0.0, 0.0])
+    with L.Trainer(dims, OMEGA_S, 1.0, K + 2) as tr:
+        for st in states:
+            tr.add_snapshot(st)
+        tr.set_params(params, shift, scale)
+        tr.set_unroll(K)
+        loss, grad = tr.loss_grad(0)
+        with pytest.raises(L.LBMError):
+            tr.loss_grad(1)  # window 1 .. 1 + K runs past the last snapshot
+        snaps = np.stack([tr.snapshot(k) for k in range(K + 1)])
+    ref_loss = O.closure_rollout_loss(base, dims, snaps, params, shift, scale)
+    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    rng = np.random.default_rng(5)
+    blocks = [(0, 224), (224, 256), (256, 1280), (1280, 1312), (1312, 1440), (1440, 1444)]
+    idx = [int(rng.integers(a, b)) for a, b in blocks for _ in range(3)]
+    idx += list(np.argsort(-np.abs(grad))[:6])
+    fd = []
+    for k in idx:
+        # the K-step loss is strongly curved along some first-layer weights
+        # (central differences with h = 1e-3, 1e-4, 1e-5 differ from the GPU
+        # gradient by 6e-1, 6e-3, 6e-5 of its largest component: the h^2
+        # truncation error), so the step is 1e-5; FP64 rounding of the
+        # difference stays below 1e-10 of the gradient
+        h = 1e-5
+        p1, p2 = params.copy(), params.copy()
+        p1[k] += h
+        p2[k] -= h
+        fd.append((O.closure_rollout_loss(base, dims, snaps, p1, shift, scale)
+                   - O.closure_rollout_loss(base, dims, snaps, p2, shift, scale)) / (2 * h))
+    fd = np.array(fd)
+    g = grad[idx]
+    gmax = np.abs(fd).max()
+    assert gmax > 0
+    assert np.all(np.abs(g - fd) <= 2e-3 * gmax + 2e-3 * np.abs(fd)), np.c_[idx, g, fd]
+
+
 def test_adam_lowers_the_loss_and_export_round_trips():
     dims = (10, 8, 6)
     s0, s1 = noisy_state(dims, 21), noisy_state(dims, 22)
@@ -236,13 +281,20 @@ def test_adam_lowers_the_loss_and_export_round_trips():
 
 
 def test_trained_network_gains_over_the_plain_method():
-    """Fine 64^3 plain cumulant run of the Fourier-mode flow restricted to
-    16^3 every 4 fine steps; train on the first pairs, then compare the
-    one-step velocity error on held-out pairs and a 4-step rollout with the
-    plain method (all higher-order rates 1)."""
+    """Fine 128^3 plain cumulant run of the Fourier-mode flow (nu = 2e-4)
+    restricted to 32^3 over 320 coarse steps; train on 8-step rollout
+    windows of the first 80 %, evaluate on the held-out last 20 %: the
+    8-step loss of the first held-out window and a-posteriori rollouts of 16
+    and 64 coarse steps from it, against the plain method (every higher rate
+    1) and the restricted fine solution.  Measured on B300: rollout errors
+    0.206 / 0.459 learned against 0.421 / 0.592 plain, held-out loss
+    4.6e-5 against 8.3e-5; the margins asserted are wider.  The untrained
+    network (zero output layer) is the plain method and fails them."""
     from paper_2211_02435_b300 import closure as C
-    res = C.train_and_evaluate(fine_edge=64, nsnap=24, ntrain=18, epochs=6, lr=3e-3,
-                               rollout=4, seed=5)
-    assert res["train_loss_final"] < res["train_loss_initial"]
-    assert res["heldout_loss_learned"] <= res["heldout_loss_plain"]
-    assert np.isfinite(res["rollout_err_learned"]) and np.isfinite(res["rollout_err_plain"])
+    res = C.train_and_evaluate(fine_edge=128, span=320, unroll=8, windows=24, epochs=8,
+                               lr=3e-3, rollout=64, short=16, seed=5)
+    assert res["train_loss_final"] < 0.8 * res["train_loss_initial"]
+    assert res["heldout_loss_learned"] < 0.8 * res["heldout_loss_plain"]
+    assert res["rollout16_err_learned"] < 0.8 * res["rollout16_err_plain"]
+    assert res["rollout64_err_learned"] < 0.9 * res["rollout64_err_plain"]
+    assert np.isfinite(res["rollout64_linf_learned"])
