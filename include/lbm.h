@@ -384,12 +384,25 @@ int lbm_set_shallow_water(lbm_ctx* ctx, double g);
  * The paper has no counterpart (its kernels are generated per platform).
  * A staged kernel whose bounded wait ran out makes the next synchronising
  * call (lbm_macroscopic / lbm_get_populations into host memory,
- * lbm_invariants, lbm_get_state) return LBM_ERR_TIMEOUT.
+ * lbm_invariants, lbm_get_state) return LBM_ERR_TIMEOUT (once: the report
+ * clears the condition; see lbm_set_wait_limit).
  * Errors: INVALID, UNSUPPORTED. */
 #define LBM_STEP_AUTO 0
 #define LBM_STEP_DIRECT 1
 #define LBM_STEP_STAGED 2
 int lbm_set_step_kernel(lbm_ctx* ctx, int kernel);
+
+/* Bound of every device wait of the context's kernels (the staged kernel's
+ * waits for its rows' bulk copies): `cycles` SM clock cycles, default
+ * LBM_WAIT_LIMIT_DEFAULT (2^31, about 1 s at 2 GHz); 0 gives up at the first
+ * unsuccessful test.  A wait that runs out abandons the rest of that step
+ * (the state is then undefined until lbm_set_populations / lbm_init_velocity
+ * / lbm_set_state), lets the copies already issued land (waiting with the
+ * default bound) and makes the next synchronising call return
+ * LBM_ERR_TIMEOUT once; the context stays usable.  The paper has no
+ * counterpart (failure detection of this library).  Errors: INVALID. */
+#define LBM_WAIT_LIMIT_DEFAULT 2147483648LL
+int lbm_set_wait_limit(lbm_ctx* ctx, int64_t cycles);
 
 /* Divergence watch of lbm_step: every `every` >= 1 steps (counted by the
  * context's step counter) the step call runs the FP64 invariants of f(n)

@@ -245,6 +245,7 @@ int lbm_create(lbm_ctx** out, const lbm_params* p) {
   c->g.N = N;
   c->eb = elem_bytes(p->storage);
   c->stream = (cudaStream_t)p->stream;
+  c->wait_limit = LBM_WAIT_LIMIT_DEFAULT;
   set_effective_rates(c, p->rates);
   const size_t bytes = size_t(c->q) * size_t(N) * size_t(c->eb);
   const int nbuf = p->streaming == LBM_PULL ? 2 : 1;
@@ -681,6 +682,12 @@ int lbm_set_divergence_check(lbm_ctx* c, int64_t every) {
   return LBM_OK;
 }
 
+int lbm_set_wait_limit(lbm_ctx* c, int64_t cycles) {
+  if (!c || cycles < 0) return LBM_ERR_INVALID;
+  c->wait_limit = cycles;
+  return LBM_OK;
+}
+
 int lbm_set_step_kernel(lbm_ctx* c, int kernel) {
   if (!c || kernel < LBM_STEP_AUTO || kernel > LBM_STEP_STAGED) return LBM_ERR_INVALID;
   if (kernel == LBM_STEP_STAGED && !staged_ok(c)) return LBM_ERR_UNSUPPORTED;
@@ -689,13 +696,16 @@ int lbm_set_step_kernel(lbm_ctx* c, int kernel) {
 }
 
 // Nonzero status word: a staged kernel's bounded wait ran out (synchronises).
+// The word is cleared once reported, so the context is usable again.
 static int read_status(lbm_ctx* c) {
   int st = 0;
   if (cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
           cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return LBM_ERR_CUDA;
-  return st ? LBM_ERR_TIMEOUT : LBM_OK;
+  if (!st) return LBM_OK;
+  if (cudaMemsetAsync(c->status, 0, sizeof(int), c->stream) != cudaSuccess) return LBM_ERR_CUDA;
+  return LBM_ERR_TIMEOUT;
 }
 
 // the step launch arguments of a context (every slab / the whole lattice)
@@ -716,6 +726,7 @@ static StepArgs step_args(const lbm_ctx* c) {
   }
   a.variant = use_staged(c) ? lbm::VARIANT_STAGED : lbm::VARIANT_DIRECT;
   a.status = c->status;
+  a.wait_limit = c->wait_limit;
   a.force_mode = c->force_mode;
   a.force_model = c->force_model;
   for (int d = 0; d < 3; ++d) a.force[d] = c->force[d];

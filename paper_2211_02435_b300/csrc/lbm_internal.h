@@ -54,6 +54,7 @@ struct StepArgs {
   int form;     // FORM_DEV / FORM_ABS_EQ (Eq. 2.6 arithmetic, FP64 storage) / FORM_DISC
   int variant;  // VARIANT_DIRECT / VARIANT_STAGED (pull only)
   int* status;  // device word set by a kernel whose bounded wait ran out
+  long long wait_limit;  // SM cycles a device wait may take (lbm_set_wait_limit)
   int force_mode;           // FORCE_NONE / FORCE_UNIFORM / FORCE_FIELD
   int force_model;          // 0 Guo, 1 He
   double force[3];          // uniform body force
@@ -174,6 +175,7 @@ struct lbm_ctx {
   void* closure;  // device closure parameters (lbm_closure.cu), NULL = off
   int* status;    // device word after the invariants scratch: nonzero = a bounded wait ran out
   int kernel;     // requested step kernel (LBM_STEP_*)
+  long long wait_limit;  // SM cycles a device wait may take before it gives up
   int force_mode;     // lbm::FORCE_*
   int force_model;    // LBM_FORCE_GUO / LBM_FORCE_HE
   double force[3];    // uniform body force (zeros when unset)

@@ -69,13 +69,17 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// wait for the phase with the given parity to complete; false after about
-// 2^31 SM cycles (~1 s) without completion
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// default limit of a device wait: 2^31 SM cycles (about 1 s)
+constexpr long long kWaitLimit = 1ll << 31;
+// wait for the phase with the given parity to complete; false once `limit`
+// SM cycles have passed without completion (0: at the first unsuccessful
+// test)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = kWaitLimit) {
   if (mbar_test(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_test(bar, parity)) {
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 >= limit) return false;
     __nanosleep(40);
   }
   return true;
@@ -94,9 +98,12 @@ constexpr int STG_NT = 256;  // threads per CTA
 
 // The row pipeline: calls body(rows_of_stage, r) for every row r of this
 // CTA, with rows_of_stage[i * nx + x] = plane i of row (y - xi_iy, z - xi_iz).
+// `limit` bounds each wait for a row's copies; the drain after a timeout
+// waits with the default limit, so every copy issued lands before the CTA
+// exits.
 template <int ST, class S, class Body>
 __device__ __forceinline__ void staged_rows(const RowPtrs<S>& P, const Geo& g, int stages,
-                                            int* status, Body&& body) {
+                                            int* status, long long limit, Body&& body) {
   constexpr int Q = q_of(ST);
   extern __shared__ __align__(128) unsigned char stg_raw[];
   __shared__ __align__(8) uint64_t bar[STG_MAX_STAGES];
@@ -133,7 +140,7 @@ __device__ __forceinline__ void staged_rows(const RowPtrs<S>& P, const Geo& g, i
   for (; k < K; ++k) {
     const int s = k % stages;
     const int r = b + k * G;
-    if (!tma::mbar_wait(&bar[s], uint32_t(k / stages) & 1u)) abort_all = 1;
+    if (!tma::mbar_wait(&bar[s], uint32_t(k / stages) & 1u, limit)) abort_all = 1;
     __syncthreads();
     if (abort_all) break;
     body(static_cast<const S*>(stage + int64_t(s) * Q * nx), r);
@@ -153,9 +160,9 @@ __device__ __forceinline__ void staged_rows(const RowPtrs<S>& P, const Geo& g, i
 template <int ST, class S, int SPACE, bool REG>
 __global__ void __launch_bounds__(STG_NT, 3) k_pull2_staged(const __grid_constant__ RowPtrs<S> P,
                                                           Geo g, Rates<P2> keep, int stages,
-                                                          int* status) {
+                                                          int* status, long long limit) {
   constexpr int Q = q_of(ST);
-  staged_rows<ST, S>(P, g, stages, status, [&](const S* row, int r) {
+  staged_rows<ST, S>(P, g, stages, status, limit, [&](const S* row, int r) {
     const int nx = g.nx;
     const int cbase = r * nx;
 #pragma unroll 1
@@ -189,9 +196,9 @@ __global__ void __launch_bounds__(STG_NT, 3) k_pull2_staged(const __grid_constan
 template <int ST, class S, class T, int SPACE, bool REG>
 __global__ void __launch_bounds__(STG_NT, 2) k_pull_staged(const __grid_constant__ RowPtrs<S> P,
                                                          Geo g, Rates<T> keep, int stages,
-                                                         int* status) {
+                                                         int* status, long long limit) {
   constexpr int Q = q_of(ST);
-  staged_rows<ST, S>(P, g, stages, status, [&](const S* row, int r) {
+  staged_rows<ST, S>(P, g, stages, status, limit, [&](const S* row, int r) {
     const int nx = g.nx;
     const int cbase = r * nx;
 #pragma unroll 1
@@ -255,7 +262,8 @@ void launch_staged(const StepArgs& a) {
     }
     Rates<P2> k2;
     for (int k = 0; k < 6; ++k) k2.om[k] = P2(1.0 - a.rates[k]);
-    kern<<<staged_grid(kern, smem, rows), STG_NT, smem, a.stream>>>(P, a.g, k2, stages, a.status);
+    kern<<<staged_grid(kern, smem, rows), STG_NT, smem, a.stream>>>(P, a.g, k2, stages, a.status,
+                                                                    a.wait_limit);
   } else {
     auto kern = k_pull_staged<ST, S, T, SPACE, REG>;
     static bool attr = false;
@@ -266,7 +274,7 @@ void launch_staged(const StepArgs& a) {
     Rates<T> keep;
     for (int k = 0; k < 6; ++k) keep.om[k] = T(1.0 - a.rates[k]);
     kern<<<staged_grid(kern, smem, rows), STG_NT, smem, a.stream>>>(P, a.g, keep, stages,
-                                                                    a.status);
+                                                                    a.status, a.wait_limit);
   }
 }
 

@@ -95,6 +95,7 @@ def lib():
         L.lbm_set_rates.argtypes = [vp, d]
         L.lbm_set_stream.argtypes = [vp, vp]
         L.lbm_set_step_kernel.argtypes = [vp, c_int]
+        L.lbm_set_wait_limit.argtypes = [vp, i64]
         L.lbm_set_force.argtypes = [vp, vp]
         L.lbm_set_force_field.argtypes = [vp, vp, c_int]
         L.lbm_set_force_model.argtypes = [vp, c_int]
@@ -130,6 +131,7 @@ def lib():
         L.lbm_trainer_set_params.argtypes = [vp, f32p, f32p, f32p]
         L.lbm_trainer_get_params.argtypes = [vp, f32p]
         L.lbm_trainer_loss_grad.argtypes = [vp, c_int, d, d]
+        L.lbm_trainer_set_unroll.argtypes = [vp, c_int]
         L.lbm_trainer_adam_step.argtypes = [vp, c_int, ctypes.c_double, d]
         L.lbm_trainer_export.argtypes = [vp, ctypes.POINTER(ClosureWeights)]
         L.lbm_trainer_destroy.argtypes = [vp]
@@ -361,6 +363,10 @@ class Lattice:
         """STEP_AUTO, STEP_DIRECT or STEP_STAGED (include/lbm.h)."""
         _check(lib().lbm_set_step_kernel(self._h, int(kernel)), "lbm_set_step_kernel")
 
+    def set_wait_limit(self, cycles):
+        """Bound (SM cycles) of the context's device waits (include/lbm.h)."""
+        _check(lib().lbm_set_wait_limit(self._h, int(cycles)), "lbm_set_wait_limit")
+
     def set_closure(self, weights):
         """Enable the learned rates (a ClosureWeights) or disable them (None)."""
         ptr = None if weights is None else ctypes.byref(weights)
@@ -562,6 +568,11 @@ class Trainer:
         p = np.empty(CLOSURE_NPARAM, dtype=np.float32)
         _check(lib().lbm_trainer_get_params(self._h, _fp(p)), "lbm_trainer_get_params")
         return p
+
+    def set_unroll(self, K):
+        """Steps of the rollout loss (1: one-step teacher forcing)."""
+        _check(lib().lbm_trainer_set_unroll(self._h, int(K)), "lbm_trainer_set_unroll")
+        self.unroll = int(K)
 
     def loss_grad(self, s):
         loss = np.zeros(1)

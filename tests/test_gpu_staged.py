@@ -124,3 +124,34 @@ def test_staged_rejects_what_it_cannot_run():
             with pytest.raises(L.LBMError) as e:
                 lat.set_step_kernel(3)
             assert e.value.code == -1
+
+
+@pytest.mark.parametrize("storage,tol", [(L.STORE_F32, 1e-5), (L.STORE_F16_DELTA, 4 * 2.0 ** -11)])
+def test_bounded_wait_that_runs_out_reports_timeout_and_the_context_recovers(storage, tol):
+    """Failure detection without a fault: with a wait bound of 0 cycles the
+    staged kernel's first wait for its rows' bulk copies gives up, the CTA
+    lets the copies already issued land and returns, and the next
+    synchronising call reports LBM_ERR_TIMEOUT once.  With the default bound
+    restored and the state set again, the same context steps to oracle
+    parity."""
+    rates = RATES_REG
+    dims = (64, 6, 5)
+    m, df0 = start(2, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, rates, dims, 71)
+    ref = O.step(m, dims, df0, 2)
+    with L.Lattice(2, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, storage, L.PULL, rates, dims) as lat:
+        lat.set_step_kernel(L.STEP_STAGED)
+        lat.set_populations(df0)
+        lat.set_wait_limit(0)
+        lat.step(1)
+        with pytest.raises(L.LBMError) as e:
+            lat.get_populations()
+        assert e.value.code == -8  # LBM_ERR_TIMEOUT
+        lat.set_wait_limit(2 ** 31)
+        lat.set_populations(df0)
+        lat.step(2)
+        got = lat.get_populations()  # reported once: no error now
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= tol * scale
+    with pytest.raises(L.LBMError):
+        with L.Lattice(2, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, storage, L.PULL, rates, dims) as lat:
+            lat.set_wait_limit(-1)
