@@ -70,19 +70,43 @@ def _table3():
     return out
 
 
+# Printed cells of Table 3 that this library does not reproduce to 1.5
+# decades, with the measured reason.  With every rate 1 each regularised
+# method collides to the same equilibrium, so on absolute storage every
+# method sits on the same floor (the FP64 quantisation of the stored f ~ w
+# sets it, ~8e-27 here for all methods); the paper's spread of that column
+# (1.7e-29 .. 1.9e-26) comes from the order of its generated arithmetic,
+# which it does not print.  For the same reason R-WO-MRT with the absolute
+# equilibrium on zero-centered storage lands on R-CM's level (4.0e-33)
+# rather than 4.4e-31: with rates 1 the weighted basis never enters the
+# regularised arithmetic.  These cells are held to 3 decades, and to the
+# method-independent floor that explains them.
+TABLE3_OFF = {"R-WO-MRT/absolute": 3.0, "R-CM/absolute": 3.0, "R-WO-MRT/zc_feq": 3.0}
+
+
 @pytest.mark.slow
 def test_tgv_plateau_table3_orders_of_magnitude():
-    """The full Table 3 case (L = 256, 200 000 steps) for SRT and R-K, the
-    two methods where the paper finds storage matters most: every plateau
-    the paper prints for them within 1.5 decades of ours; for R-WO-MRT the
-    zero-centered delta-equilibrium plateau as well."""
+    """The full Table 3 case (L = 256, 200 000 steps) for every method and
+    storage form the paper prints: each of the 10 printed plateaus within
+    1.5 decades of ours, except the three cells of TABLE3_OFF, held to 3
+    decades and to the explanation given there (the absolute-storage floor is
+    the same for every method; R-WO-MRT with f^eq equals R-CM with f^eq).
+    The paper's ordering holds in every row: zero-centered storage with
+    delta-equilibria lowest, absolute storage highest."""
     B.build()
     paper = _table3()
-    res = A.tgv_plateau(n=256, steps=200_000, every=50_000, methods=["SRT", "R-K", "R-WO-MRT"],
+    assert len(paper) == 10
+    res = A.tgv_plateau(n=256, steps=200_000, every=50_000,
+                        methods=["SRT", "R-WO-MRT", "R-CM", "R-K"],
                         forms=["absolute", "zc_feq", "zc_dfeq"])
-    checked = 0
-    for key, ours in ((k, v[-1]) for k, v in res["runs"].items()):
-        if key in paper and (not key.startswith("R-WO-MRT") or key.endswith("zc_dfeq")):
-            assert abs(np.log10(ours / paper[key])) < 1.5, (key, ours, paper[key])
-            checked += 1
-    assert checked == 5
+    ours = {k: v[-1] for k, v in res["runs"].items()}
+    for key, ref in paper.items():
+        band = TABLE3_OFF.get(key, 1.5)
+        assert key in ours, key
+        assert abs(np.log10(ours[key] / ref)) < band, (key, ours[key], ref)
+    floor = ours["SRT/absolute"]
+    for m in ("R-WO-MRT", "R-CM", "R-K"):
+        assert abs(np.log10(ours[f"{m}/absolute"] / floor)) < 0.5, (m, ours)
+    assert abs(np.log10(ours["R-WO-MRT/zc_feq"] / ours["R-CM/zc_feq"])) < 0.5, ours
+    for m in ("SRT", "R-WO-MRT", "R-CM"):
+        assert ours[f"{m}/absolute"] > 100 * ours[f"{m}/zc_dfeq"], (m, ours)
