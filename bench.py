@@ -116,24 +116,64 @@ def job_mlups(world, cells_per_rank, steps, seconds):
     return world * cells_per_rank * steps / seconds / 1e6
 
 
-def kernel_traffic_per_cell():
-    """DRAM bytes per cell update of the FP32 step kernel from the committed
-    ncu summary, or None when the kernel sources changed since the capture."""
+def profile_value(name, key, sources=("lbm_device.cuh", "lbm_kernels.cuh")):
+    """A figure `key = value` of the committed ncu summary profiles/<name>, or
+    None when the kernel sources it was taken from changed since (the summary
+    records the SHA-1 of those files as kernel_source_sha1)."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "profiles", "ncu_k_pull_d3q27_cumulant_f32_256.md")
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     txt = open(path).read()
-    m1 = re.search(r"traffic_bytes_per_cell = ([0-9.]+)", txt)
+    m1 = re.search(re.escape(key) + r" = ([0-9.eE+-]+)", txt)
     m2 = re.search(r"kernel_source_sha1 = ([0-9a-f]+)", txt)
     if not (m1 and m2):
         return None
     h = hashlib.sha1()
-    for f in ("lbm_device.cuh", "lbm_kernels.cuh"):
+    for f in sources:
         with open(os.path.join(ROOT, "paper_2211_02435_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return float(m1.group(1)) if h.hexdigest() == m2.group(1) else None
+
+
+def kernel_traffic_per_cell():
+    """DRAM bytes per cell update of the FP32 step kernel from the committed
+    ncu summary, or None when the kernel sources changed since the capture."""
+    return profile_value("ncu_k_pull_d3q27_cumulant_f32_256.md", "traffic_bytes_per_cell")
+
+
+def fp32_peak_tflops(sm_max_mhz):
+    """FP32 CUDA-core peak of this device: SMs x 128 FP32 lanes x 2 flop (one
+    fused multiply-add) x the maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return sms * 128 * 2 * (sm_max_mhz or 2032.0) * 1e6 / 1e12
+
+
+def alu_roof(profile, mlups, peak_tflops, sources):
+    """ALU roof of a kernel: FP32 flops per cell update (ncu instruction
+    counts, FFMA = 2, FFMA2 = 4, FADD / FMUL = 1, FADD2 / FMUL2 = 2) x cell
+    updates per second against the FP32 CUDA-core peak; and the FMA-pipe
+    lane-ops per cell (FADD2 / FMUL2 occupy two lanes like FFMA2) against the
+    pipe's lane rate, peak / 2."""
+    fpc = profile_value(profile, "fp32_flop_per_cell", sources)
+    if fpc is None:
+        return None
+    ach = fpc * mlups * 1e6 / 1e12
+    out = {"bound": "alu", "flop_per_cell": fpc, "achieved": ach, "peak": peak_tflops,
+           "unit": "TFLOP/s", "frac": ach / peak_tflops, "profile": profile}
+    ops = profile_value(profile, "fp32_lane_ops_per_cell", sources)
+    if ops is not None:
+        out["lane_ops_per_cell"] = ops
+        out["pipe_frac"] = ops * mlups * 1e6 / (peak_tflops * 1e12 / 2)
+    # instruction issue: 4 schedulers x 32 lanes per SM per clock, the same
+    # SMs x 128 x clock as the FP32 lane rate
+    ins = profile_value(profile, "thread_inst_per_cell", sources)
+    if ins is not None:
+        out["inst_per_cell"] = ins
+        out["issue_frac"] = ins * mlups * 1e6 / (peak_tflops * 1e12 / 2)
+    return out
 
 
 def make_fields(n):
@@ -264,19 +304,25 @@ def run_batched(args, L, torch, stream, peak):
 
 def run_learned(args, L, torch, stream):
     """Learned closure: fine 512^3 plain cumulant run (nu = 2e-4, seeded
-    Fourier-mode flow) restricted to 128^3 every 4 steps, GPU training of
-    the rate network, held-out one-step and rollout errors against the plain
-    method, and the fused learned-rate kernel's MLUPS against the plain
-    kernel's at 128^3."""
+    Fourier-mode flow) restricted to 128^3 every 4 fine steps over 1280
+    coarse steps, GPU training of the rate network on K-step rollout windows
+    of the first 80 %, held-out K-step loss and 64- / 256-step rollout errors
+    against the plain method from the first held-out snapshot, and the fused
+    learned-rate kernel's MLUPS against the plain kernel's at 128^3."""
     from paper_2211_02435_b300 import closure as C
-    res = C.train_and_evaluate(fine_edge=args.learned_fine, nsnap=160, ntrain=128, epochs=8,
-                               lr=3e-3, rollout=31, nu_fine=2e-4, seed=5, stream=stream)
+    sc = args.learned_fine / 512  # time scale of the flow relative to 512^3
+    res = C.train_and_evaluate(fine_edge=args.learned_fine, span=int(round(1280 * sc)),
+                               unroll=args.learned_unroll, windows=24,
+                               epochs=args.learned_epochs, lr=3e-3,
+                               rollout=int(round(256 * sc)), short=int(round(64 * sc)),
+                               nu_fine=2e-4, seed=5, stream=stream)
     w = res.pop("weights")
     n = args.learned_fine // 4
     omega_c = I.shear_viscosity_rate(2e-4 / 4)
     rho, u = I.fourier_modes((n, n, n), seed=5)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     rates = {}
+    steps = max(args.steps, 20)
     for name, weights in (("plain", None), ("learned", w)):
         with L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F32, L.PULL,
                        [omega_c] + [1.0] * 5, (n, n, n), stream=stream) as lat:
@@ -286,13 +332,63 @@ def run_learned(args, L, torch, stream):
             lat.step(args.warmup)
             torch.cuda.synchronize()
             e0.record(stream)
+            lat.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rates[name] = n ** 3 * steps / (e0.elapsed_time(e1) / 1e3) / 1e6
+    res[f"mlups_{n}_plain_kernel"] = rates["plain"]
+    res[f"mlups_{n}_learned_kernel"] = rates["learned"]
+    res["learned_vs_plain_mlups"] = rates["learned"] / rates["plain"]
+    return res
+
+
+def run_closure_timing(args):
+    """Throughput of the fused learned-rate step against the plain step
+    (D3Q27 cumulant, FP32, pull) at --size^3 on the Fourier-mode flow, with a
+    seeded random network (normalised on the initial state): one JSON line.
+    A small, training-free case for profiling the fused kernel."""
+    import torch
+    from paper_2211_02435_b300 import build as B
+    from paper_2211_02435_b300 import closure as C
+    from paper_2211_02435_b300 import lbm as L
+
+    B.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n = args.size
+    omega_c = I.shear_viscosity_rate(2e-4 / 4)
+    rho, u = I.fourier_modes((n, n, n), seed=5)
+    with L.Trainer((n, n, n), omega_c, 1.0, 2, stream=stream) as tr:
+        with L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F64, L.PULL,
+                       [omega_c] + [1.0] * 5, (n, n, n), stream=stream) as lat:
+            lat.init_velocity(rho.reshape(-1), u.reshape(-1))
+            lat.step(2)
+            tr.add_snapshot(lat.get_populations())
+        shift, scale = C.feature_normalisation(tr, [0])
+        p = C.init_params(7, 0.3)
+        p[1312:] = 0.3 * np.random.default_rng(8).standard_normal(132)
+        tr.set_params(p, shift, scale)
+        w = tr.export()
+    out = {"metric": "fused learned-rate step MLUPS vs the plain step", "unit": UNIT,
+           "cells": n ** 3, "steps": args.steps, "warmup": args.warmup}
+    for name, weights in (("plain", None), ("learned", w)):
+        with L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F32, L.PULL,
+                       [omega_c] + [1.0] * 5, (n, n, n), stream=stream) as lat:
+            if weights is not None:
+                lat.set_closure(weights)
+            lat.init_velocity(rho.reshape(-1), u.reshape(-1))
+            lat.step(args.warmup)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
             lat.step(args.steps)
             e1.record(stream)
             torch.cuda.synchronize()
-            rates[name] = n ** 3 * args.steps / (e0.elapsed_time(e1) / 1e3) / 1e6
-    res["mlups_128_plain_kernel"] = rates["plain"]
-    res["mlups_128_learned_kernel"] = rates["learned"]
-    return res
+            out[f"{name}_mlups"] = n ** 3 * args.steps / (e0.elapsed_time(e1) / 1e3) / 1e6
+    out["learned_vs_plain"] = out["learned_mlups"] / out["plain_mlups"]
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def run_cuda(args):
@@ -382,6 +478,19 @@ def run_cuda(args):
     lat32.macroscopic(None, u32)
     lat32.close()
     del lat32
+
+    # a separate sustained run of >= 1 s of steps, median of 5 windows
+    sustained = None
+    if not args.no_sustained and args.sustained_steps > 0:
+        lat, ms_s, win_s = time_form(main_store, args.sustained_steps, args.warmup,
+                                     streaming=main_stream, windows=5)
+        lat.close()
+        del lat
+        wm = sorted(N * k / (w / 1e3) / 1e6 for k, w in win_s)
+        sustained = {"steps": args.sustained_steps, "seconds": ms_s / 1e3, "windows": 5,
+                     "median_mlups": wm[2], "min_mlups": wm[0], "max_mlups": wm[-1],
+                     "median_frac": main_bpc * wm[2] * 1e6 / 1e9 / peak}
+
 
     forms = {}
     if not args.no_forms:
@@ -489,6 +598,20 @@ def run_cuda(args):
     if traffic is not None:
         traffic *= N
 
+    # ALU roofs of the kernels that may reach it (the packed FP16 step and
+    # the fused learned-rate step): FP32 flops per cell from ncu counts
+    fp32_peak = fp32_peak_tflops(clocks.get("sm_max_mhz"))
+    if "f16_delta" in forms:
+        forms["f16_delta"]["alu"] = alu_roof("alu_k_pull2_d3q27_cumulant_f16.md",
+                                             forms["f16_delta"]["mlups"], fp32_peak,
+                                             ("lbm_device.cuh", "lbm_kernels.cuh",
+                                              "lbm_packed.cuh"))
+    if learned is not None:
+        n_c = args.learned_fine // 4
+        learned["alu"] = alu_roof("alu_k_closure_pull_d3q27_128.md",
+                                  learned[f"mlups_{n_c}_learned_kernel"], fp32_peak,
+                                  ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_closure.cu"))
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -503,16 +626,64 @@ def run_cuda(args):
                                     + f"<D3Q27, {args.streaming}, {main_key} storage, cumulant, "
                                     + ("regularised>" if args.force == "none"
                                        else f"{args.force} force>")),
-                         "step_kernel": args.step_kernel},
-            "forms": forms, "batched": batched, "learned": learned, "clocks": clocks, "e2e": e2e,
-            "cpu_baseline": cpu,
-            "gpu_launches": args.steps}
+                         "step_kernel": args.step_kernel,
+                         "timed_windows_mlups": win_mlups},
+            "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": args.steps,
+            "sustained": sustained,
+            "forms": forms, "batched": batched, "learned": learned}
+    line["summary"] = summary(line, win_mlups)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def summary(line, win_mlups):
+    """The figures a reader needs, compact and last on the line."""
+    def r(x, nd=3):
+        return None if x is None else round(float(x), nd)
+
+    out = {"headline_mlups": r(line["value"], 0), "headline_frac": r(line["roofline"]["frac"]),
+           "headline_window_median_mlups": r(statistics.median(win_mlups), 0)}
+    if line.get("sustained"):
+        out["sustained_median_mlups"] = r(line["sustained"]["median_mlups"], 0)
+    f = line.get("forms") or {}
+    for k in ("f16_delta", "bf16_delta"):
+        if k in f:
+            alu = f[k].get("alu")
+            out[f"{k}_pull"] = {"mlups": r(f[k]["mlups"], 0), "frac": r(f[k]["roofline_frac"]),
+                                "u_rel_linf_vs_f64": r(f[k]["u_rel_linf_vs_f64"], 8),
+                                "alu_frac": r(alu["frac"]) if alu else None,
+                                "alu_pipe_frac": r(alu.get("pipe_frac")) if alu else None}
+    ip = {k.split("_")[-1]: r(v["roofline_frac"]) for k, v in f.items()
+          if k.startswith("f16_delta_") and "roofline_frac" in v}
+    if ip:
+        out["f16_delta_inplace_frac"] = ip
+    b = line.get("batched")
+    if b:
+        out["batched"] = {"mlups": r(b["mlups"], 0), "frac": r(b["roofline_frac"]),
+                          "tuning": [b["tuning"][k] for k in ("threads", "cells_per_thread",
+                                                             "blocks_per_sm")]}
+    le = line.get("learned")
+    if le:
+        o = {}
+        for key in le:
+            if key.startswith("rollout") and key.endswith("_err_learned"):
+                steps = key[len("rollout"):-len("_err_learned")]
+                o[f"rollout{steps}_l2"] = [r(le[key], 4), r(le[f"rollout{steps}_err_plain"], 4)]
+        o["heldout_loss"] = [le.get("heldout_loss_learned"), le.get("heldout_loss_plain")]
+        o["kernel_mlups"] = [r(v, 0) for k, v in le.items() if k.startswith("mlups_")][::-1]
+        o["alu_frac"] = r(le["alu"]["frac"]) if le.get("alu") else None
+        o["alu_pipe_frac"] = r(le["alu"].get("pipe_frac")) if le.get("alu") else None
+        o["issue_frac"] = r(le["alu"].get("issue_frac")) if le.get("alu") else None
+        out["learned"] = o
+    c = line.get("cpu_baseline")
+    if c:
+        out["oracle_mlups"] = {"cores": c["cores"], "all": r(c["value"], 3),
+                               "one": r(c["one_core"]["value"], 4)}
+    return out
 
 
 STEP_KERNELS = {"auto": 0, "direct": 1, "staged": 2}  # LBM_STEP_* of include/lbm.h
@@ -593,9 +764,16 @@ def main():
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="storage of the headline form (default FP32)")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-sustained", action="store_true")
+    ap.add_argument("--sustained-steps", type=int, default=250,
+                    help="steps of the separate >= 1 s sustained run (5 windows, median)")
+    ap.add_argument("--closure-timing", action="store_true",
+                    help="time the fused learned-rate step against the plain one at --size^3")
     ap.add_argument("--method-survey", action="store_true",
                     help="time the pull step of every stencil / space / storage instead")
     ap.add_argument("--learned-fine", type=int, default=512)
+    ap.add_argument("--learned-unroll", type=int, default=8)
+    ap.add_argument("--learned-epochs", type=int, default=4)
     ap.add_argument("--batch-n", type=int, default=4096)
     ap.add_argument("--step-kernel", choices=list(STEP_KERNELS), default="auto",
                     help="pull step kernel of the D3Q27 forms (include/lbm.h)")
@@ -608,6 +786,8 @@ def main():
         args.warmup = 3
     if args.method_survey:
         return run_method_survey(args)
+    if args.closure_timing:
+        return run_closure_timing(args)
     return run_reference(args) if args.impl == "reference" else run_cuda(args)
 
 

@@ -44,11 +44,26 @@ def _units():
     return units
 
 
+STAMP = LIB + ".sha1"
+
+
+def _sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for d in sorted(_deps()):
+        h.update(os.path.relpath(d, ROOT).encode())
+        with open(d, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    """The library exists and was linked from the sources as they are now
+    (content hash recorded next to it at link time)."""
+    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    with open(STAMP) as fh:
+        return fh.read().strip() == _sources_hash()
 
 
 def _flags_of(extra):
@@ -76,6 +91,7 @@ def _obj_current(src, out, extra):
 def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
+    stamp = _sources_hash()  # of the sources this build starts from
     os.makedirs(OBJ, exist_ok=True)
 
     def compile_one(u):
@@ -101,6 +117,8 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(stamp + "\n")
     return LIB
 
 
