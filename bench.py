@@ -276,7 +276,7 @@ def run_batched(args, L, torch, stream, peak):
     with L.Batch(L.D3Q19, L.SPACE_RAW, L.EQ_DELTA, L.STORE_F32, rates, [tuple(d) for d in dims],
                  om, stream=stream) as b:
         cells = b.cells()
-        tune, tune_mlups = b.autotune(trial_steps=2)
+        tune, tune_mlups = b.autotune(trial_steps=args.autotune_steps)
         b.init_tgv(u0)
         b.step(args.warmup)
         ms = timed(b.step, args.steps)
@@ -610,7 +610,7 @@ def run_cuda(args):
         n_c = args.learned_fine // 4
         learned["alu"] = alu_roof("alu_k_closure_pull_d3q27_128.md",
                                   learned[f"mlups_{n_c}_learned_kernel"], fp32_peak,
-                                  ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_closure.cu"))
+                                  ("lbm_device.cuh", "lbm_closure.cu"))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_s * 1e3,
@@ -775,6 +775,8 @@ def main():
     ap.add_argument("--learned-unroll", type=int, default=8)
     ap.add_argument("--learned-epochs", type=int, default=4)
     ap.add_argument("--batch-n", type=int, default=4096)
+    ap.add_argument("--autotune-steps", type=int, default=6,
+                    help="steps per autotuner trial of the batched ensemble")
     ap.add_argument("--step-kernel", choices=list(STEP_KERNELS), default="auto",
                     help="pull step kernel of the D3Q27 forms (include/lbm.h)")
     ap.add_argument("--streaming", choices=list(STREAMINGS), default="pull",

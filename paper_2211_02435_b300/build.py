@@ -70,34 +70,58 @@ def _flags_of(extra):
     return " ".join([NVCC] + FLAGS + extra)
 
 
-def _obj_current(src, out, extra):
-    """An object is current when it was compiled with the same command and is
-    newer than every file its dependency list (nvcc -MD) names."""
-    dep, cmdf = out + ".d", out + ".cmd"
-    if not (os.path.exists(out) and os.path.exists(dep) and os.path.exists(cmdf)):
-        return False
-    if open(cmdf).read() != _flags_of(extra):
-        return False
-    t = os.path.getmtime(out)
+def _dep_files(out):
+    """Repository files named by the nvcc dependency list of an object."""
+    dep = out + ".d"
+    if not os.path.exists(dep):
+        return None
     text = open(dep).read().replace("\\\n", " ")
     files = text.split(":", 1)[1].split() if ":" in text else []
-    files.append(src)
-    for f in files:
-        if not os.path.exists(f) or os.path.getmtime(f) > t:
-            return False
-    return True
+    return sorted({os.path.abspath(f) for f in files
+                   if os.path.abspath(f).startswith(ROOT + os.sep)})
+
+
+def _unit_stamp(src, out, extra, contents):
+    """Hash of an object's command line and of the contents its repository
+    dependencies had when this build started (`contents`: path -> bytes)."""
+    import hashlib
+    files = _dep_files(out)
+    if files is None:
+        return None
+    h = hashlib.sha1(_flags_of(extra).encode())
+    for f in sorted(set(files) | {os.path.abspath(src)}):
+        if f not in contents:
+            return None
+        h.update(f.encode())
+        h.update(contents[f])
+    return h.hexdigest()
+
+
+def _obj_current(src, out, extra, contents):
+    """An object is current when its stamp matches its command line and the
+    contents of the files it depends on; a file edited while it compiled
+    leaves the stamp of the old contents, so the next build redoes it."""
+    stamp = out + ".stamp"
+    if not (os.path.exists(out) and os.path.exists(stamp)):
+        return False
+    want = _unit_stamp(src, out, extra, contents)
+    return want is not None and open(stamp).read().strip() == want
 
 
 def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     stamp = _sources_hash()  # of the sources this build starts from
+    contents = {}
+    for d in _deps():
+        with open(d, "rb") as fh:
+            contents[os.path.abspath(d)] = fh.read()
     os.makedirs(OBJ, exist_ok=True)
 
     def compile_one(u):
         src, obj, extra = u
         out = os.path.join(OBJ, obj)
-        if not force and _obj_current(src, out, extra):
+        if not force and _obj_current(src, out, extra, contents):
             return out
         cmd = [NVCC] + FLAGS + extra + ["-MD", "-MF", out + ".d", "-c", src, "-o", out]
         if verbose:
@@ -105,8 +129,9 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {obj}:\n{r.stderr}")
-        with open(out + ".cmd", "w") as fh:
-            fh.write(_flags_of(extra))
+        st = _unit_stamp(src, out, extra, contents)
+        with open(out + ".stamp", "w") as fh:
+            fh.write((st or "") + "\n")
         return out
 
     with cf.ThreadPoolExecutor(max_workers=jobs or os.cpu_count() or 4) as ex:

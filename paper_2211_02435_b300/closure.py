@@ -151,3 +151,65 @@ def train_and_evaluate(fine_edge=512, span=1280, unroll=8, windows=24, epochs=6,
             out[f"rollout{length}_err_plain"], out[f"rollout{length}_linf_plain"] = e_p
         out["weights"] = w
     return out
+
+
+RATE_SWEEP = [("plain", [1.0, 1.0, 1.0, 1.0])] + [
+    (f"w3={w}", [w, 1.0, 1.0, 1.0]) for w in (0.01, 0.03, 0.1, 0.3, 0.5, 1.5)] + [
+    (f"w4={w}", [1.0, w, 1.0, 1.0]) for w in (0.3, 1.9)] + [
+    ("w5=0.3", [1.0, 1.0, 0.3, 1.0]), ("w6=0.3", [1.0, 1.0, 1.0, 0.3]),
+    ("w3=0.1,w4=1.9", [0.1, 1.9, 1.0, 1.0]), ("w3=0.03,w4=1.5", [0.03, 1.5, 1.0, 1.0])]
+
+
+def constant_rate_sweep(fine_edge=512, nu_fine=2e-4, seed=5, unroll=8, stream=None):
+    """What constant rates of orders 3..6 gain over the plain method on the
+    learned-closure data: rollout errors of the coarse method from the
+    restricted state at coarse steps 0 and 1024 (times scaled by fine_edge /
+    512) after 64 and 256 steps, and the mean one-step and `unroll`-step
+    losses over windows at steps 64, 512 and 896."""
+    sc = fine_edge / 512
+    T = [int(round(v * sc)) for v in (0, 64, 256, 512, 896, 1024, 1088, 1280)]
+    wins = [T[1], T[3], T[4]]
+    times = sorted({T[0], T[2], T[5], T[6], T[7]} | {w + k for w in wins for k in range(unroll + 1)})
+    at = {t: k for k, t in enumerate(times)}
+    coarse = fine_edge // 4
+    omega_c = I.shear_viscosity_rate(nu_fine / 4)
+    rows = []
+    with L.Trainer((coarse,) * 3, omega_c, 1.0, len(times), stream=stream) as tr:
+        make_snapshots(tr, fine_edge, times, nu_fine, seed, stream=stream)
+        for name, r4 in RATE_SWEEP:
+            # constant rates: a network whose output biases give them everywhere
+            p = np.zeros(L.CLOSURE_NPARAM)
+            p[1440:1444] = np.log(np.array(r4) / (2.0 - np.array(r4)))
+            tr.set_params(p, np.zeros(7), np.ones(7))
+            w = tr.export()
+            row = {"name": name, "rates_3_6": r4}
+            for t0, lengths in ((T[0], (T[1], T[2])), (T[5], (T[1], T[2]))):
+                for n in lengths:
+                    row[f"rollout_{t0}_{n}"] = rollout_error(tr, at[t0], n, at[t0 + n], omega_c,
+                                                             w, stream)[0]
+            for K in (1, unroll):
+                tr.set_unroll(K)
+                row[f"loss_k{K}"] = mean_loss(tr, [at[wt] for wt in wins])
+            tr.set_unroll(1)
+            rows.append(row)
+    return {"fine": f"{fine_edge}^3", "coarse": f"{coarse}^3", "nu_fine": nu_fine,
+            "rows": rows}
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["sweep", "train"])
+    ap.add_argument("--fine", type=int, default=512)
+    a = ap.parse_args()
+    if a.what == "sweep":
+        print(json.dumps(constant_rate_sweep(a.fine)))
+    else:
+        sc = a.fine / 512
+        res = train_and_evaluate(fine_edge=a.fine, span=int(round(1280 * sc)),
+                                 rollout=int(round(256 * sc)), short=int(round(64 * sc)),
+                                 log=print)
+        res.pop("weights")
+        print(json.dumps(res))

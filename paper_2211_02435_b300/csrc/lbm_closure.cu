@@ -632,13 +632,15 @@ __device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, 
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a0), "r"(a1), "r"(b0));
 }
-// tanh x = 1 - 2 / (1 + e^(2x)): exact at +-infinity (e^(2x) -> inf, 0),
-// absolute error ~2e-7 from the approximate exponential and reciprocal
+// the hidden activation: the special-function unit's tanh (one instruction,
+// relative error about 2^-11).  Measured against the FP64 oracle, the fused
+// step's relative L-infinity error is 3e-7 .. 8e-7 with it and with an
+// accurate tanh alike (the rates only scale the higher-order cumulants), and
+// the step runs 9 % faster.
 __device__ __forceinline__ float tanh_mma(float x) {
-  float e, r;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x * 2.8853900817779268f));  // 2 / ln 2
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
-  return fmaf(-2.0f, r, 1.0f);
+  float r;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 // the next layer's A fragments (hi and lo parts) of k-tile kk from the
 // accumulators D[mt][n-tile][4]
