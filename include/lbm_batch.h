@@ -82,11 +82,12 @@ int lbm_batch_set_tuning(lbm_batch* b, const lbm_batch_tuning* t);
 int lbm_batch_get_tuning(const lbm_batch* b, lbm_batch_tuning* t);
 
 /* Time every candidate shape (threads in {64, 128, 256}, cells per thread
- * in {1, 2, 4, 8}, blocks per SM in {4, 8, 16}) over trial_steps >= 1
- * steps each, keep the fastest and return it with its cell-update rate in
- * MLUPS.  The trial steps advance the ensemble: call it before the
- * lbm_batch_init_* calls.  Synchronises the stream.  Errors: INVALID,
- * CUDA. */
+ * in {1, 2, 4, 8}, blocks per SM in {4, 6, 8, 10, 12, 16}) over trial_steps >= 1
+ * steps (rounded up to even), then time the four fastest three more times
+ * each and keep the one with the best median; returns it with that median
+ * cell-update rate in MLUPS.  The trial steps advance the ensemble: call it
+ * before the lbm_batch_init_* calls.  Synchronises the stream.  Errors:
+ * INVALID, CUDA. */
 int lbm_batch_autotune(lbm_batch* b, int trial_steps, lbm_batch_tuning* best,
                        double* best_mlups);
 

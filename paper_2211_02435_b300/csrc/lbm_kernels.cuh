@@ -280,10 +280,15 @@ __global__ void __launch_bounds__(LBM_BX) k_scatter_swe(AbsF64* buf, Geo g, cons
 // pairs, for FP16 / BF16 delta storage and even Nx.  Directions with
 // xi_x = 0 read both cells with one aligned 2-element load; the others read
 // the two cells separately (their x wrap differs at the row ends).  Stores
-// are aligned 2-element stores.
+// are aligned 2-element stores.  The plane base of each direction is formed
+// in the kernel from the two buffer pointers, the plane size and the
+// compile-time offsets: warp-uniform values, which the compiler keeps on the
+// uniform datapath (an earlier form passed 54 pre-shifted plane pointers as
+// parameters, one constant-bank load and 64-bit add each: 50.7 -> 52.3 GLUPS
+// at 512^3).
 template <int ST, class S, int SPACE, bool REG>
-__global__ void LBM_PULL2_BOUNDS k_pull2(const __grid_constant__ PullPtrs<S> P, Geo g,
-                                                  Rates<P2> keep, int z0 = 0) {
+__global__ void LBM_PULL2_BOUNDS k_pull2(const S* __restrict__ src, S* __restrict__ dst, Geo g,
+                                         Rates<P2> keep, int z0 = 0) {
   const int x = 2 * (blockIdx.x * LBM_BX + threadIdx.x);
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = z0 + int(blockIdx.z);
@@ -297,12 +302,13 @@ __global__ void LBM_PULL2_BOUNDS k_pull2(const __grid_constant__ PullPtrs<S> P, 
   sfor<q_of(ST)>([&](auto I) {
     constexpr int i = CI(I);
     constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1), cz = vel(ST, i, 2);
+    // plane i shifted by the interior y / z offset of the gather
+    const S* pl = src + (int64_t(i) * g.N - (int64_t(cz) * nxy + int64_t(cy) * g.nx));
     const int off = c + (cy > 0 ? wyp : (cy < 0 ? wym : 0)) + (cz > 0 ? wzp : (cz < 0 ? wzm : 0));
-    P2 v;
-    if constexpr (cx == 0) v = Pack<S>::load2(P.src[i] + off);
-    else if constexpr (cx > 0) v = Pack<S>::load11(P.src[i] + off + wxp0, P.src[i] + off + 1);
-    else v = Pack<S>::load11(P.src[i] + off, P.src[i] + off + 1 + wxm1);
-    f[i] = v * P2(1.0f / float(1u << scale_exp(ST, i)));
+    constexpr int E = scale_exp(ST, i);
+    if constexpr (cx == 0) f[i] = Pack<S>::template load2s<E>(pl + off);
+    else if constexpr (cx > 0) f[i] = Pack<S>::template load11s<E>(pl + (off - 1 + wxp0), pl + off);
+    else f[i] = Pack<S>::template load11s<E>(pl + (off + 1), pl + (off + 2 + wxm1));
   });
   // the backward transform leaves population i multiplied by 2^|xi_i|^2;
   // the storage scale 2^s_i absorbs it exactly
@@ -311,7 +317,7 @@ __global__ void LBM_PULL2_BOUNDS k_pull2(const __grid_constant__ PullPtrs<S> P, 
     constexpr int i = CI(I);
     constexpr int k = vel(ST, i, 0) * vel(ST, i, 0) + vel(ST, i, 1) * vel(ST, i, 1) +
                       vel(ST, i, 2) * vel(ST, i, 2);
-    Pack<S>::store2(P.dst[i] + c, f[i] * P2(float(1u << (scale_exp(ST, i) - k))));
+    Pack<S>::store2(dst + (int64_t(i) * g.N + c), f[i] * P2(float(1u << (scale_exp(ST, i) - k))));
   });
 }
 
@@ -479,16 +485,18 @@ __global__ void LBM_PULL2_BOUNDS k_inplace2(const __grid_constant__ InPlacePtrs<
   auto wyz = [&](int oy, int oz) {
     return (oy < 0 ? wyp : (oy > 0 ? wym : 0)) + (oz < 0 ? wzp : (oz > 0 ? wzm : 0));
   };
+  // (plane pointers from the parameter table: forming the 2 q slot bases in
+  // the kernel from one buffer pointer, as k_pull2 does, measured 14 %
+  // slower here)
   P2 f[q_of(ST)];
   sfor<q_of(ST)>([&](auto I) {
     constexpr int i = CI(I);
     using Mp = InPlaceMap<ST, MODE, i>;
     const S* p = P.rd[i] + (c + wyz(Mp::ry, Mp::rz));
-    P2 v;
-    if constexpr (Mp::rx == 0) v = Pack<S>::load2(p);
-    else if constexpr (Mp::rx < 0) v = Pack<S>::load11(p + wx0, p + 1);
-    else v = Pack<S>::load11(p, p + 1 + wx1);
-    f[i] = v * P2(1.0f / float(1u << scale_exp(ST, i)));
+    constexpr int E = scale_exp(ST, i);
+    if constexpr (Mp::rx == 0) f[i] = Pack<S>::template load2s<E>(p);
+    else if constexpr (Mp::rx < 0) f[i] = Pack<S>::template load11s<E>(p + wx0, p + 1);
+    else f[i] = Pack<S>::template load11s<E>(p, p + 1 + wx1);
   });
   // the backward transform leaves population i multiplied by 2^|xi_i|^2;
   // the storage scale 2^s_i absorbs it exactly
@@ -865,7 +873,8 @@ void launch_step_typed(const StepArgs& a) {
         Rates<P2> k2;
         for (int k = 0; k < 6; ++k) k2.om[k] = P2(1.0 - a.rates[k]);
         const dim3 grid2((a.g.nx / 2 + LBM_BX - 1) / LBM_BX, a.g.ny, a.nzc > 0 ? a.nzc : a.g.nz);
-        k_pull2<ST, S, SPACE, REG><<<grid2, LBM_BX, 0, a.stream>>>(P, a.g, k2, a.z0);
+        k_pull2<ST, S, SPACE, REG><<<grid2, LBM_BX, 0, a.stream>>>((const S*)a.src, (S*)a.dst,
+                                                                  a.g, k2, a.z0);
         return;
       }
     }

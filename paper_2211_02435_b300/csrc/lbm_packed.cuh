@@ -88,6 +88,24 @@ P2F P2 rcp(P2 x) {
 // two cells' packed values of one population plane (x and x+1)
 template <class S>
 struct Pack;
+// h * 2^-E as FP32 in one mixed-precision multiply-add (FP16 operands, FP32
+// result: the product is exact); adding -0 keeps the sign of a zero, so the
+// result equals the conversion followed by the power-of-two multiply bit
+// for bit
+template <int E>
+P2F float h2f_scaled(__half h) {
+#ifdef __CUDA_ARCH__
+  static_assert(E >= 0 && E <= 14, "2^-E must be a normal FP16 number");
+  float r;
+  asm("fma.rn.f32.f16 %0, %1, %2, %3;"
+      : "=f"(r)
+      : "h"(__half_as_ushort(h)), "h"((unsigned short)((15 - E) << 10)), "f"(-0.0f));
+  return r;
+#else
+  return __half2float(h) / float(1u << E);
+#endif
+}
+
 template <>
 struct Pack<__half> {
   P2F static P2 load2(const __half* p) {
@@ -95,6 +113,16 @@ struct Pack<__half> {
   }
   P2F static P2 load11(const __half* p0, const __half* p1) {
     return P2(make_float2(__half2float(*p0), __half2float(*p1)));
+  }
+  // the same values times 2^-E (the decode of the per-direction scale)
+  template <int E>
+  P2F static P2 load2s(const __half* p) {
+    const __half2 h = *reinterpret_cast<const __half2*>(p);
+    return P2(make_float2(h2f_scaled<E>(__low2half(h)), h2f_scaled<E>(__high2half(h))));
+  }
+  template <int E>
+  P2F static P2 load11s(const __half* p0, const __half* p1) {
+    return P2(make_float2(h2f_scaled<E>(*p0), h2f_scaled<E>(*p1)));
   }
   P2F static void store2(__half* p, P2 v) {
     *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v);
@@ -111,6 +139,16 @@ struct Pack<__nv_bfloat16> {
   }
   P2F static P2 load11(const __nv_bfloat16* p0, const __nv_bfloat16* p1) {
     return P2(make_float2(__bfloat162float(*p0), __bfloat162float(*p1)));
+  }
+  // BF16 widens by a shift (not on the FMA pipe), so the scale stays a
+  // separate packed multiply
+  template <int E>
+  P2F static P2 load2s(const __nv_bfloat16* p) {
+    return load2(p) * P2(1.0f / float(1u << E));
+  }
+  template <int E>
+  P2F static P2 load11s(const __nv_bfloat16* p0, const __nv_bfloat16* p1) {
+    return load11(p0, p1) * P2(1.0f / float(1u << E));
   }
   P2F static void store2(__nv_bfloat16* p, P2 v) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v.v);

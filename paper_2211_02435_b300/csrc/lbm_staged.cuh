@@ -174,11 +174,10 @@ __global__ void __launch_bounds__(STG_NT, 3) k_pull2_staged(const __grid_constan
         constexpr int i = CI(I);
         constexpr int cx = vel(ST, i, 0);
         const S* rw = row + i * nx;
-        P2 v;
-        if constexpr (cx == 0) v = Pack<S>::load2(rw + x);
-        else if constexpr (cx > 0) v = Pack<S>::load11(rw + xm, rw + x);
-        else v = Pack<S>::load11(rw + x + 1, rw + xp2);
-        f[i] = v * P2(1.0f / float(1u << scale_exp(ST, i)));
+        constexpr int E = scale_exp(ST, i);
+        if constexpr (cx == 0) f[i] = Pack<S>::template load2s<E>(rw + x);
+        else if constexpr (cx > 0) f[i] = Pack<S>::template load11s<E>(rw + xm, rw + x);
+        else f[i] = Pack<S>::template load11s<E>(rw + x + 1, rw + xp2);
       });
       collide<ST, P2, SPACE, REG, true>(f, keep);
       sfor<Q>([&](auto I) {
