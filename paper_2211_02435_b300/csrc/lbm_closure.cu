@@ -598,13 +598,13 @@ __global__ void __launch_bounds__(128)
 // the 7 inputs and the 4 outputs pass through shared memory.
 namespace wmn {
 // per-lane table, word w of lane l at [w * 32 + l]
-constexpr int L1_B = 0;       // layer 1, n-tiles 0..3: B (k 2t, 2t+1; n 8j + g)
+constexpr int L1_B = 0;       // layer 1, n-tiles 0..3: B (k 2t, 2t+1; n 8j + g);
+                              // input 7 is the constant 1 and its weight the bias
 constexpr int L2_B = 4;       // layer 2, (k-tile kk, n-tile j): 2 words at 4 + 2 (4 kk + j)
 constexpr int L3_B = 20;      // layer 3, k-tile kk: 2 words at 20 + 2 kk
-constexpr int L1_BIAS = 24;   // layer 1 bias of columns 8j + 2t + e at 24 + 2j + e
-constexpr int L2_BIAS = 32;   // layer 2, same layout
-constexpr int L3_BIAS = 40;   // layer 3 bias of columns 2t + e (0 for t >= 2)
-constexpr int WORDS = 42;
+constexpr int L2_BIAS = 24;   // layer 2 bias of columns 8j + 2t + e at 24 + 2j + e
+constexpr int L3_BIAS = 32;   // layer 3 bias of columns 2t + e (0 for t >= 2)
+constexpr int WORDS = 34;
 // byte offset of the table in the device parameter image (after the floats)
 constexpr int TAB_OFF_BYTES = ((NSMEM * 4 + 127) / 128) * 128;
 constexpr int TAB_BYTES = WORDS * 32 * 4;
@@ -653,8 +653,9 @@ __device__ __forceinline__ void next_a(const float (&D)[4][4], int kk, uint32_t 
 }
 
 // The network of the warp's 32 cells: x this lane's normalised inputs (x[7]
-// = 0), tab the lane table (shared memory), st 256 words of per-warp shared
-// staging; z receives this lane's 4 outputs.  All 32 lanes must call it.
+// = 1, the input that carries layer 1's bias), tab the lane table (shared
+// memory), st 256 words of per-warp shared staging; z receives this lane's 4
+// outputs.  All 32 lanes must call it.
 __device__ __forceinline__ void mlp_warp(const float (&x)[8], const uint32_t* __restrict__ tab,
                                          uint32_t* st, float (&z)[4]) {
   const int lane = threadIdx.x & 31, t = lane & 3, g = lane >> 2;
@@ -678,9 +679,7 @@ __device__ __forceinline__ void mlp_warp(const float (&x)[8], const uint32_t* __
     const uint32_t l0 = st[8 * r0 + 4 + t], l1 = st[8 * r1 + 4 + t];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const float b0 = __uint_as_float(T[32 * (L1_BIAS + 2 * j)]);
-      const float b1 = __uint_as_float(T[32 * (L1_BIAS + 2 * j + 1)]);
-      D[mt][j][0] = b0, D[mt][j][1] = b1, D[mt][j][2] = b0, D[mt][j][3] = b1;
+      D[mt][j][0] = D[mt][j][1] = D[mt][j][2] = D[mt][j][3] = 0.f;
       const uint32_t B = T[32 * (L1_B + j)];
       mma_k8(D[mt][j], h0, h1, B);
       mma_k8(D[mt][j], l0, l1, B);
@@ -769,7 +768,8 @@ inline void pack_lane_table(const float* P, uint32_t* tab) {
     std::memcpy(&u, &v, 4);
     return u;
   };
-  auto W1 = [&](int n, int k) { return k < NIN ? P[OW1 + n * NIN + k] : 0.f; };
+  // input column 7 is the constant 1: its weights are layer 1's biases
+  auto W1 = [&](int n, int k) { return k < NIN ? P[OW1 + n * NIN + k] : P[OB1 + n]; };
   auto W2 = [&](int n, int k) { return P[OW2 + n * NH + k]; };
   auto W3 = [&](int n, int k) { return n < NOUT ? P[OW3 + n * NH + k] : 0.f; };
   for (int l = 0; l < 32; ++l) {
@@ -788,10 +788,7 @@ inline void pack_lane_table(const float* P, uint32_t* tab) {
       at(wmn::L3_B + 2 * kk + 1) = pair(W3(g, k + 8), W3(g, k + 9));
     }
     for (int j = 0; j < 4; ++j)
-      for (int e = 0; e < 2; ++e) {
-        at(wmn::L1_BIAS + 2 * j + e) = fbits(P[OB1 + 8 * j + 2 * t + e]);
-        at(wmn::L2_BIAS + 2 * j + e) = fbits(P[OB2 + 8 * j + 2 * t + e]);
-      }
+      for (int e = 0; e < 2; ++e) at(wmn::L2_BIAS + 2 * j + e) = fbits(P[OB2 + 8 * j + 2 * t + e]);
     for (int e = 0; e < 2; ++e)
       at(wmn::L3_BIAS + e) = fbits(2 * t + e < NOUT ? P[OB3 + 2 * t + e] : 0.f);
   }
@@ -854,14 +851,14 @@ __global__ void LBM_CLOSURE_BOUNDS
 #pragma unroll
       for (int i = 0; i < NIN; ++i) xin[i] = 0.f;
     }
-    xin[7] = 0.f;
+    xin[7] = 1.f;  // the bias input
     float zz[4];
     wmn::mlp_warp(xin, tab, st, zz);
     if (active) {
       Rates<float> k = keep;
 #pragma unroll
       for (int o = 0; o < NOUT; ++o) {
-        const float sg = 1.0f / (1.0f + __expf(-zz[o]));
+        const float sg = __fdividef(1.0f, 1.0f + __expf(-zz[o]));
         float om = 2.0f * sg;
         om = om < 1e-3f ? 1e-3f : om;
         om = om > 1.999f ? 1.999f : om;
