@@ -42,3 +42,46 @@ def test_cuda_arm_fails_loudly_without_a_device():
                   "--no-learned", timeout=120)
     assert r.returncode != 0
     assert not r.stdout.strip().startswith("{")
+
+
+def _bench_module():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench
+
+
+def test_committed_ncu_summaries_match_the_kernel_sources():
+    """The figures the bench line reads from profiles/ (DRAM traffic per cell
+    of the FP32 step, ALU-roof counts of the FP16 and learned steps) were
+    taken from the kernel sources as committed: each summary records the
+    hash of its sources and is dropped (null in the line) when they differ."""
+    bench = _bench_module()
+    assert bench.kernel_traffic_per_cell() is not None
+    pull2 = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_packed.cuh")
+    closure = ("lbm_device.cuh", "lbm_closure.cu")
+    for name, src in (("alu_k_pull2_d3q27_cumulant_f16.md", pull2),
+                      ("alu_k_closure_pull_d3q27_128.md", closure)):
+        for key in ("fp32_flop_per_cell", "fp32_lane_ops_per_cell", "thread_inst_per_cell"):
+            assert bench.profile_value(name, key, src) is not None, (name, key)
+
+
+def test_alu_roof_and_summary_arithmetic():
+    bench = _bench_module()
+    src = ("lbm_device.cuh", "lbm_closure.cu")
+    roof = bench.alu_roof("alu_k_closure_pull_d3q27_128.md", 10000.0, 80.0, src)
+    fpc = roof["flop_per_cell"]
+    assert abs(roof["achieved"] - fpc * 1e4 * 1e6 / 1e12) < 1e-9
+    assert abs(roof["frac"] - roof["achieved"] / 80.0) < 1e-12
+    # lane-ops and instructions against the lane / issue rate, half the flop peak
+    assert abs(roof["pipe_frac"] - roof["lane_ops_per_cell"] * 1e10 / 40e12) < 1e-12
+    assert abs(roof["issue_frac"] - roof["inst_per_cell"] * 1e10 / 40e12) < 1e-12
+    line = {"value": 31000.0, "roofline": {"frac": 1.05},
+            "forms": {"f16_delta": {"mlups": 52000.0, "roofline_frac": 0.87,
+                                    "u_rel_linf_vs_f64": 7e-4, "alu": roof},
+                      "f16_delta_aa": {"mlups": 1.0, "roofline_frac": 0.8}},
+            "batched": None, "learned": None, "cpu_baseline": None, "sustained": None}
+    s = bench.summary(line, [30000.0, 31000.0, 32000.0])
+    assert s["headline_window_median_mlups"] == 31000.0
+    assert s["f16_delta_pull"]["alu_frac"] == round(roof["frac"], 3)
+    assert s["f16_delta_inplace_frac"] == {"aa": 0.8}
+    assert len(json.dumps(s)) < 1500
