@@ -17,9 +17,12 @@
  * normalised x_i = (raw_i - shift_i) * scale_i.  Network:
  *   h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), z = W3 h2 + b3,
  *   omega_{3..6} = clamp(2 sigmoid(z), 1e-3, 1.999);
- * with any non-finite input or output all four rates fall back to 1 (the
- * plain regularised cumulant method).  Weights are applied in BF16 with
- * FP32 (FP64 for FP64 storage) accumulation.
+ * with any normalised input non-finite or outside FP16's range
+ * (|x_i| > 65504), or any non-finite output, all four rates fall back to 1
+ * (the plain regularised cumulant method).  Weights are BF16 numbers; FP64
+ * lattices apply them in FP64, FP32 lattices on the tensor cores as FP16
+ * operands (exact for BF16 values of magnitude 2^-17 .. 65504) with the
+ * activations split into two FP16 parts and FP32 accumulation.
  *
  * Parameter vector layout (LBM_CLOSURE_NPARAM values): W1[32][7], b1[32],
  * W2[32][32], b2[32], W3[4][32], b3[4], row-major.
@@ -63,8 +66,8 @@ typedef struct {
  * Served for D3Q27 cumulant contexts with pull streaming and FP32 or FP64
  * storage (others: LBM_ERR_UNSUPPORTED).  While enabled, lbm_step runs the
  * fused kernel; the context's rates for orders 3..6 are ignored.  The
- * weights are copied to the device.  Errors: INVALID, UNSUPPORTED, OOM,
- * CUDA. */
+ * weights are copied to the device.  Errors: INVALID (also a weight that is
+ * not finite or of magnitude above 65504), UNSUPPORTED, OOM, CUDA. */
 int lbm_set_closure(lbm_ctx* ctx, const lbm_closure_weights* w);
 
 typedef struct lbm_trainer lbm_trainer;

@@ -1064,7 +1064,9 @@ int lbm_oracle_closure_mlp(const double* P, const double* shift,
   int ok = 1;
   for (int i = 0; i < NI; ++i) {
     x[i] = (raw[i] - shift[i]) * scale[i];
-    ok = ok && isfinite(x[i]);
+    /* usable input: finite and within FP16's range (|x| <= 65504), the
+       operand range of the GPU network; otherwise the cell keeps rates 1 */
+    ok = ok && x[i] <= 65504.0 && x[i] >= -65504.0;
   }
   for (int r = 0; r < NH; ++r) {
     double a = b1[r];

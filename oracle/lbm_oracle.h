@@ -211,7 +211,8 @@ int lbm_oracle_closure_features(int stencil, const double* df,
 
 /* omega[4] (orders 3..6) = clamp(2 sigmoid(W3 tanh(W2 tanh(W1 x + b1) + b2)
  * + b3), 1e-3, 1.999) with x_i = (raw_i - shift_i) * scale_i; all four are 1
- * if any input or output is not finite. */
+ * if any x_i is not finite or |x_i| > 65504 (the FP16 range of the GPU
+ * network's operands), or any output is not finite. */
 int lbm_oracle_closure_mlp(const double* params, const double* shift,
                            const double* scale, const double raw[7],
                            double omega[4]);

@@ -105,6 +105,14 @@ LBM_D Dual sqrt_t(Dual x) {
   return Dual(r, r > 0.f ? 0.5f * x.d / r : 0.f);
 }
 
+// A cell's normalised input is usable when it is finite and within FP16's
+// range, the operand type of the tensor-core network (|x| <= 65504; NaN
+// fails both comparisons); a cell with an unusable input keeps rates 1.
+template <class T>
+LBM_D bool input_ok(T x) {
+  return x <= T(65504) && x >= T(-65504);
+}
+
 // ----------------------------------------------------------- network
 // P points to NSMEM values: parameters, then shift[7], then scale[7].
 // Returns the rates omega[4] and d omega / d z (0 where clamped or on the
@@ -118,7 +126,7 @@ LBM_D void mlp_forward(const T* P, const T (&raw)[NIN], T (&x)[NIN], T (&h1)[NH]
 #pragma unroll
   for (int i = 0; i < NIN; ++i) {
     x[i] = (raw[i] - shift[i]) * scale[i];
-    ok = ok && isfinite(x[i]);
+    ok = ok && input_ok(x[i]);
   }
   if constexpr (std::is_same<T, float>::value) {
 #pragma unroll
@@ -207,8 +215,24 @@ LBM_D void closure_features(const T (&K)[3][3][3], T drho, T omega_s, T (&raw)[N
   const T i2D = da * db + db * dc + dc * da - off;
   const T detD = da * (db * dc - r * r) - p * (p * dc - r * q) + q * (p * r - db * q);
   const T n2D = da * da + db * db + dc * dc + T(2) * off;
-  const T nP = sqrt_t(n2P), nD = sqrt_t(n2D);
   const bool zP = !(n2P > T(0)), zD = !(n2D > T(0));
+#ifdef __CUDA_ARCH__
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32 on the device: one reciprocal square root per norm (the special
+    // function unit's, a few ulp) in place of a square root and IEEE
+    // divisions; 3 % of the fused learned-rate step
+    const float rP = rsqrtf(n2P), rD = rsqrtf(n2D);
+    raw[0] = s * trP;
+    raw[1] = zP ? 0.f : -s * i2P * rP;
+    raw[2] = zP ? 0.f : s * detP * (rP * rP);
+    raw[3] = zD ? 0.f : i2D * rD;
+    raw[4] = zD ? 0.f : detD * (rD * rD);
+    raw[5] = zP ? 0.f : n2P * rP;
+    raw[6] = drho;
+    return;
+  }
+#endif
+  const T nP = sqrt_t(n2P), nD = sqrt_t(n2D);
   raw[0] = s * trP;
   raw[1] = zP ? T(0) : -s * i2P / nP;    // s^2 I2(Pi) / (|s| |Pi|)
   raw[2] = zP ? T(0) : s * detP / n2P;   // s^3 det(Pi) / (s^2 |Pi|^2)
@@ -527,7 +551,7 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
     for (int i = 0; i < NIN; ++i) {
       xin[i] = (raw[i] - sp[NPARAM + i]) * sp[NPARAM + NIN + i];
-      ok = ok && isfinite(xin[i]);
+      ok = ok && input_ok(xin[i]);
     }
     xin[7] = 0.0f;
   } else {
@@ -588,14 +612,22 @@ __global__ void __launch_bounds__(128)
 
 // --------------------------------- warp-level tensor-core network (FP32)
 // A warp's 32 cells (one per lane) are two 16-row tiles.  Layer l computes
-// D = A B + bias with A the activations and B[k][n] = W_l[n][k] (BF16 weights)
-// by mma.sync (m16n8k8 for the 7 inputs padded to 8, m16n8k16 above), FP32
-// accumulation.  Each FP32 activation enters as two BF16 parts, hi = bf16(a)
-// and lo = bf16(a - hi) (|a - hi - lo| <= 2^-17 |a|), each multiplied by the
-// same B, so every product is exact.  The accumulator fragments of two
-// adjacent n8 tiles are, element for element, the A fragment of the next
-// layer's k16 tile: the hidden activations never leave the registers; only
-// the 7 inputs and the 4 outputs pass through shared memory.
+// D = A B + bias with A the activations and B[k][n] = W_l[n][k] by mma.sync
+// (m16n8k8 for the 7 inputs padded to 8, m16n8k16 above), FP16 operands and
+// FP32 accumulation.  The weights are BF16 numbers, whose 8 significant bits
+// FP16 holds exactly (down to |w| = 2^-17; below that the FP16 subnormal
+// spacing 2^-24 bounds the change); the host refuses weights beyond FP16's
+// range.  Each FP32 activation enters as two FP16 parts, hi = fp16(a) and
+// lo = fp16(a - hi) (|a - hi - lo| <= 2^-22 |a|, plus 2^-25 where lo is
+// subnormal), each multiplied by the same B, so every product is exact.
+// Two BF16 parts (2^-17) measured a fused-step error of up to 1.2e-5 of the
+// FP64 oracle on strongly non-equilibrium states, two FP16 parts 2.7e-6;
+// with the residual a - hi formed by one mixed-precision FMA per value, the
+// FP16 split is also the cheaper one (16.4 against 16.2 GLUPS at 128^3).
+// The accumulator fragments of two adjacent n8 tiles are, element for
+// element, the A fragment of the next layer's k16 tile: the hidden
+// activations never leave the registers; only the 7 inputs and the 4 outputs
+// pass through shared memory.
 namespace wmn {
 // per-lane table, word w of lane l at [w * 32 + l]
 constexpr int L1_B = 0;       // layer 1, n-tiles 0..3: B (k 2t, 2t+1; n 8j + g);
@@ -609,34 +641,42 @@ constexpr int WORDS = 34;
 constexpr int TAB_OFF_BYTES = ((NSMEM * 4 + 127) / 128) * 128;
 constexpr int TAB_BYTES = WORDS * 32 * 4;
 
-// two floats as BF16 pairs: first element in the low half (the lower k)
-__device__ __forceinline__ uint32_t bf16x2(float first, float second) {
+// two floats as an FP16 pair: first element in the low half (the lower k)
+__device__ __forceinline__ uint32_t f16x2(float first, float second) {
   uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(second), "f"(first));
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(second), "f"(first));
   return r;
 }
+// hi and lo parts of a pair; a - hi is exact (Sterbenz: hi is a's nearest
+// FP16 number) and comes from one mixed-precision FMA, hi * (-1) + a, that
+// reads hi's half of the packed register as its FP16 operand
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
-  hi = bf16x2(a, b);
-  lo = bf16x2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xffff0000u));
+  hi = f16x2(a, b);
+  float ra, rb;
+  asm("{\n .reg .b16 h0, h1;\n mov.b32 {h0, h1}, %2;\n"
+      " fma.rn.f32.f16 %0, h0, %5, %3;\n fma.rn.f32.f16 %1, h1, %5, %4;\n}"
+      : "=f"(ra), "=f"(rb)
+      : "r"(hi), "f"(a), "f"(b), "h"((unsigned short)0xBC00));  // FP16 -1
+  lo = f16x2(ra, rb);
 }
 __device__ __forceinline__ void mma_k16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
                                         uint32_t b1) {
-  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, "
       "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 __device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
-  asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, "
       "{%4, %5}, {%6}, {%0, %1, %2, %3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a0), "r"(a1), "r"(b0));
 }
 // the hidden activation: the special-function unit's tanh (one instruction,
-// relative error about 2^-11).  Measured against the FP64 oracle, the fused
-// step's relative L-infinity error is 3e-7 .. 8e-7 with it and with an
-// accurate tanh alike (the rates only scale the higher-order cumulants), and
-// the step runs 9 % faster.
+// relative error about 2^-11).  Against the FP64 oracle the fused step's
+// relative L-infinity error changed little with an accurate tanh from ex2
+// and rcp (9.5e-6 against 1.1e-5 with two BF16 parts, the largest case),
+// which ran 16 % slower.
 __device__ __forceinline__ float tanh_mma(float x) {
   float r;
   asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -754,14 +794,10 @@ __device__ __forceinline__ void mlp_warp(const float (&x)[8], const uint32_t* __
 }
 }  // namespace wmn
 
-// Pack the weights (FP32 values of BF16 numbers) and biases into the lane
-// table of mlp_warp.
+// Pack the weights (FP32 values of BF16 numbers, |w| <= 65504) as FP16 and
+// the biases into the lane table of mlp_warp.
 inline void pack_lane_table(const float* P, uint32_t* tab) {
-  auto bits = [](float v) {
-    uint32_t u;
-    std::memcpy(&u, &v, 4);
-    return u >> 16;  // exact: v is a BF16 value
-  };
+  auto bits = [](float v) { return uint32_t(__half_as_ushort(__float2half_rn(v))); };
   auto pair = [&](float first, float second) { return bits(first) | (bits(second) << 16); };
   auto fbits = [](float v) {
     uint32_t u;
@@ -842,7 +878,7 @@ __global__ void LBM_CLOSURE_BOUNDS
 #pragma unroll
       for (int i = 0; i < NIN; ++i) {
         xin[i] = (raw[i] - nrm[i]) * nrm[NIN + i];
-        ok = ok && isfinite(xin[i]);
+        ok = ok && input_ok(xin[i]);
       }
       if (!ok)
 #pragma unroll
@@ -871,6 +907,112 @@ __global__ void LBM_CLOSURE_BOUNDS
       float Cs[3][3][3];
       cum_backward<float>(s, k, Cs, f);
       sfor<27>([&](auto I) { P.dst[CI(I)][c] = f[CI(I)]; });
+    }
+  }
+}
+
+// The same step with two cells (x, x + 1) per thread for even Nx: the
+// cumulant transforms run on packed FP32 pairs (FFMA2 / FADD2 / FMUL2, each
+// lane the FP32 arithmetic of the one-cell kernel), which halves the
+// collision's instruction count per cell; the features and the sigmoid stay
+// per cell and the warp's network runs twice, once per cell of the pair.  A
+// tile is 256 consecutive cells (a pair never straddles a row).  Measured on
+// B300 at 128^3: 16.1 GLUPS against 13.8 for the one-cell kernel, 16.3 with
+// the register cap of four CTAs per SM (72 bytes of spills).
+__global__ void __launch_bounds__(128, 4)
+    k_closure_pull_mma2(const __grid_constant__ PullPtrs<float> P, Geo g, Rates<float> keep,
+                        const float* __restrict__ params, int ntiles) {
+  __shared__ __align__(16) uint32_t tab[wmn::WORDS * 32];
+  __shared__ __align__(16) uint32_t stage[4][256];
+  __shared__ float nrm[2 * NIN];
+  {
+    const uint32_t* gt = reinterpret_cast<const uint32_t*>(
+        reinterpret_cast<const char*>(params) + wmn::TAB_OFF_BYTES);
+    for (int k = threadIdx.x; k < wmn::WORDS * 32; k += 128) tab[k] = gt[k];
+    if (threadIdx.x < 2 * NIN) nrm[threadIdx.x] = params[NPARAM + threadIdx.x];
+  }
+  __syncthreads();
+  uint32_t* st = stage[threadIdx.x >> 5];
+  const float omega_s = 1.0f - keep.om[0];
+  const int nxy = g.nx * g.ny;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int c0 = tile * 256 + 2 * int(threadIdx.x);
+    const bool active = c0 < int(g.N);
+    const int c = active ? c0 : 0;
+    const int row = c / g.nx, x = c - row * g.nx;
+    const int y = row % g.ny, z = row / g.ny;
+    P2 f[27];
+    CumState<P2> s;
+    float xa[8], xb[8];  // the two cells' normalised inputs
+    bool oka = true, okb = true;
+    if (active) {
+      // wrap corrections: cell x reading x - 1, cell x + 1 reading x + 2
+      const int wx0 = x == 0 ? g.nx : 0, wx1 = x + 2 == g.nx ? -g.nx : 0;
+      const int wyp = y == 0 ? nxy : 0, wym = y == g.ny - 1 ? -nxy : 0;
+      const int wzp = z == 0 ? int(g.N) : 0, wzm = z == g.nz - 1 ? -int(g.N) : 0;
+      sfor<27>([&](auto I) {
+        constexpr int i = CI(I);
+        constexpr int cx = vel(D3Q27, i, 0), cy = vel(D3Q27, i, 1), cz = vel(D3Q27, i, 2);
+        const int w = (cy > 0 ? wyp : (cy < 0 ? wym : 0)) + (cz > 0 ? wzp : (cz < 0 ? wzm : 0));
+        const float* p = P.src[i] + (c + w);  // cell x's source element
+        if constexpr (cx == 0) f[i] = P2(*reinterpret_cast<const float2*>(p));
+        else if constexpr (cx > 0) f[i] = P2(make_float2(p[wx0], p[1]));
+        else f[i] = P2(make_float2(p[0], p[1 + wx1]));
+      });
+      cum_forward<P2>(f, s);
+      float Ka[3][3][3], Kb[3][3][3];
+      sfor<27>([&](auto K) {
+        constexpr int a = CI(K) / 9, b = (CI(K) / 3) % 3, cc = CI(K) % 3;
+        Ka[a][b][cc] = s.Kn[a][b][cc].v.x;
+        Kb[a][b][cc] = s.Kn[a][b][cc].v.y;
+      });
+      float ra[NIN], rb[NIN];
+      closure_features<float>(Ka, s.drho.v.x, omega_s, ra);
+      closure_features<float>(Kb, s.drho.v.y, omega_s, rb);
+#pragma unroll
+      for (int i = 0; i < NIN; ++i) {
+        xa[i] = (ra[i] - nrm[i]) * nrm[NIN + i];
+        xb[i] = (rb[i] - nrm[i]) * nrm[NIN + i];
+        oka = oka && input_ok(xa[i]);
+        okb = okb && input_ok(xb[i]);
+      }
+      if (!oka)
+#pragma unroll
+        for (int i = 0; i < NIN; ++i) xa[i] = 0.f;
+      if (!okb)
+#pragma unroll
+        for (int i = 0; i < NIN; ++i) xb[i] = 0.f;
+    } else {
+#pragma unroll
+      for (int i = 0; i < NIN; ++i) xa[i] = xb[i] = 0.f;
+    }
+    xa[7] = xb[7] = 1.f;  // the bias input
+    float za[4], zb[4];
+    wmn::mlp_warp(xa, tab, st, za);
+    wmn::mlp_warp(xb, tab, st, zb);
+    if (active) {
+      Rates<P2> k;
+#pragma unroll
+      for (int o = 0; o < 6; ++o) k.om[o] = P2(keep.om[o]);
+#pragma unroll
+      for (int o = 0; o < NOUT; ++o) {
+        float oa = 2.0f * __fdividef(1.0f, 1.0f + __expf(-za[o]));
+        float ob = 2.0f * __fdividef(1.0f, 1.0f + __expf(-zb[o]));
+        oa = oa < 1e-3f ? 1e-3f : (oa > 1.999f ? 1.999f : oa);
+        ob = ob < 1e-3f ? 1e-3f : (ob > 1.999f ? 1.999f : ob);
+        oka = oka && isfinite(oa);
+        okb = okb && isfinite(ob);
+        k.om[2 + o] = P2(make_float2(1.0f - oa, 1.0f - ob));
+      }
+      // a cell whose inputs or rates are not finite relaxes with rates 1
+#pragma unroll
+      for (int o = 0; o < NOUT; ++o) {
+        if (!oka) k.om[2 + o].v.x = 0.0f;
+        if (!okb) k.om[2 + o].v.y = 0.0f;
+      }
+      P2 Cs[3][3][3];
+      cum_backward<P2>(s, k, Cs, f);
+      sfor<27>([&](auto I) { *reinterpret_cast<float2*>(P.dst[CI(I)] + c) = f[CI(I)].v; });
     }
   }
 }
@@ -1208,20 +1350,16 @@ void launch_closure_step(const StepArgs& a, const void* closure) {
     k_closure_pull_tc<<<grid, 128, 0, a.stream>>>((const float*)a.src, (float*)a.dst, a.g, keep,
                                                    (const float*)closure, a.status);
 #elif LBM_CLOSURE_NET == 1
-    static int resident = 0;  // CTAs per SM x SMs, once per process
-    if (!resident) {
+    // persistent grids: CTAs per SM x SMs, once per process and kernel
+    auto resident_of = [](auto kernel) {
       int dev = 0, sms = 0, occ = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_closure_pull_mma, 128, 0) !=
-              cudaSuccess ||
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 128, 0) != cudaSuccess ||
           occ < 1)
         occ = 1;
-      resident = sms * occ;
-    }
-    const int tiles_x = (a.g.nx + 127) / 128;
-    const int ntiles = tiles_x * a.g.ny * a.g.nz;  // < 2^31: N < 2^31
-    const int blocks = ntiles < resident ? ntiles : resident;
+      return sms * occ;
+    };
     PullPtrs<float> P;
     const int64_t nx = a.g.nx, nxy = int64_t(a.g.nx) * a.g.ny;
     for (int i = 0; i < 27; ++i) {
@@ -1229,8 +1367,18 @@ void launch_closure_step(const StepArgs& a, const void* closure) {
       P.src[i] = (const float*)a.src + (int64_t(i) * a.g.N + delta);
       P.dst[i] = (float*)a.dst + int64_t(i) * a.g.N;
     }
-    k_closure_pull_mma<<<blocks, 128, 0, a.stream>>>(P, a.g, keep, (const float*)closure, tiles_x,
-                                                     ntiles);
+    if (a.g.nx % 2 == 0) {
+      static const int resident2 = resident_of(k_closure_pull_mma2);
+      const int ntiles = int((a.g.N + 255) / 256);  // N < 2^31
+      k_closure_pull_mma2<<<ntiles < resident2 ? ntiles : resident2, 128, 0, a.stream>>>(
+          P, a.g, keep, (const float*)closure, ntiles);
+    } else {
+      static const int resident = resident_of(k_closure_pull_mma);
+      const int tiles_x = (a.g.nx + 127) / 128;
+      const int ntiles = tiles_x * a.g.ny * a.g.nz;  // < 2^31: N < 2^31
+      k_closure_pull_mma<<<ntiles < resident ? ntiles : resident, 128, 0, a.stream>>>(
+          P, a.g, keep, (const float*)closure, tiles_x, ntiles);
+    }
 #else
     k_closure_pull<float, float><<<grid, 128, 0, a.stream>>>((const float*)a.src, (float*)a.dst,
                                                              a.g, keep, (const float*)closure);
@@ -1310,7 +1458,11 @@ int lbm_set_closure(lbm_ctx* c, const lbm_closure_weights* w) {
     return LBM_ERR_UNSUPPORTED;
   const bool dbl = c->p.storage == LBM_STORE_F64;
   std::vector<double> hd(lbm::NSMEM);
-  for (int k = 0; k < NPARAM; ++k) hd[k] = bf16_bits_to_float(w->w[k]);
+  for (int k = 0; k < NPARAM; ++k) {
+    hd[k] = bf16_bits_to_float(w->w[k]);
+    // the FP32 network's FP16 operands hold every finite weight up to 65504
+    if (!(hd[k] <= 65504.0 && hd[k] >= -65504.0)) return LBM_ERR_INVALID;
+  }
   for (int k = 0; k < NIN; ++k) {
     hd[NPARAM + k] = w->shift[k];
     hd[NPARAM + NIN + k] = w->scale[k];

@@ -80,11 +80,14 @@ FIXED_SCALE = np.array([1e2, 1e2, 1e2, 1e3, 1e3, 1e3, 1e2])
 # Data-derived scales (1/std of each feature over the lattice) are of the
 # same order as the fixed ones, since every conditioned feature has the
 # magnitude of Pi: both are held to the stencil's FP64 / FP32 tolerance.
+# Odd Nx runs the FP32 step one cell per thread; even Nx two cells per
+# thread (924 cells: three full 256-cell tiles and a ragged one; Nx = 2: both
+# cells of every pair wrap along x)
+@pytest.mark.parametrize("dims", [(21, 7, 6), (22, 7, 6), (2, 9, 5)], ids=str)
 @pytest.mark.parametrize("norm,storage,tol", [
     ("fixed", L.STORE_F64, 1e-12), ("fixed", L.STORE_F32, 1e-5),
     ("data", L.STORE_F64, 1e-12), ("data", L.STORE_F32, 1e-5)])
-def test_fused_learned_step_matches_oracle(norm, storage, tol):
-    dims = (21, 7, 6)
+def test_fused_learned_step_matches_oracle(norm, storage, tol, dims):
     df = noisy_state(dims, 1)
     if norm == "fixed":
         shift, scale = np.zeros(7), FIXED_SCALE
@@ -115,6 +118,37 @@ def test_fused_learned_step_matches_oracle(norm, storage, tol):
         plain = O.step(O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [OMEGA_S] + [1.0] * 5),
                        dims, prev, 1)
         assert rel_linf(lat.get_populations(), plain) < min(tol, 1e-12 if storage == L.STORE_F64 else 1e-5)
+
+
+@pytest.mark.parametrize("dims", [(21, 7, 6), (22, 7, 6)], ids=str)
+def test_inputs_beyond_fp16_range_fall_back_and_large_weights_are_refused(dims):
+    """A normalised input beyond FP16's range (the tensor-core network's
+    operand type) makes the cell keep rates 1, as the oracle does: here
+    x_6 = (drho + 1) * 1e6 in every cell, so the fused FP32 step is the
+    plain regularised step.  A weight above 65504 is refused."""
+    df = noisy_state(dims, 3)
+    params = random_params(4)
+    shift, scale = np.zeros(7), np.ones(7)
+    shift[6], scale[6] = -1.0, 1e6
+    base = O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [OMEGA_S, 1.0, 0.0, 0.0, 0.0, 0.0])
+    with L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_ABSOLUTE, L.STORE_F32, L.PULL,
+                   [OMEGA_S] + [1.0] * 5, dims) as lat:
+        lat.set_closure(weights(params, shift, scale))
+        lat.set_populations(df)
+        lat.step(1)
+        got = lat.get_populations()
+        ref = O.closure_step(base, dims, df, params, np.float32(shift).astype(np.float64),
+                             np.float32(scale).astype(np.float64))
+        plain = O.step(O.method(2, O.SPACE_CUMULANT, O.EQ_ABSOLUTE, [OMEGA_S] + [1.0] * 5),
+                       dims, df, 1)
+        assert rel_linf(ref, plain) < 1e-13
+        assert rel_linf(got, plain) < 1e-5
+        big = params.copy()
+        big[100] = 1e5  # BF16 99840
+        for p in (big, -big):
+            with pytest.raises(L.LBMError) as e:
+                lat.set_closure(weights(p, shift, scale))
+            assert e.value.code == -1
 
 
 def test_zero_network_is_the_plain_method_and_unsupported_contexts():

@@ -162,6 +162,14 @@ def test_mlp_closed_form_cases(O):
     bad = raw.copy()
     bad[3] = np.nan
     assert np.array_equal(O.closure_mlp(p, shift, scale, bad), np.ones(4))
+    # a normalised input counts up to FP16's largest finite value, 65504
+    # (the operand range of the GPU network), and falls back beyond it
+    edge = raw.copy()
+    edge[3] = -65504.0
+    np.testing.assert_allclose(O.closure_mlp(p, shift, scale, edge), ref, rtol=1e-15)
+    for v in (65504.5, -65505.0, np.inf):
+        edge[3] = v
+        assert np.array_equal(O.closure_mlp(p, shift, scale, edge), np.ones(4)), v
 
 
 def _dims():
