@@ -602,7 +602,7 @@ def run_cuda(args):
     # the fused learned-rate step): FP32 flops per cell from ncu counts
     fp32_peak = fp32_peak_tflops(clocks.get("sm_max_mhz"))
     if "f16_delta" in forms:
-        forms["f16_delta"]["alu"] = alu_roof("alu_k_pull2_d3q27_cumulant_f16.md",
+        forms["f16_delta"]["alu"] = alu_roof("alu_k_pull4_d3q27_cumulant_f16.md",
                                              forms["f16_delta"]["mlups"], fp32_peak,
                                              ("lbm_device.cuh", "lbm_kernels.cuh",
                                               "lbm_packed.cuh"))

@@ -39,6 +39,17 @@ namespace lbm {
 #else
 #define LBM_PULL2_BOUNDS __launch_bounds__(LBM_BX)
 #endif
+// the same for the four-cells-per-thread kernels (k_pull4, k_inplace4):
+// left to the compiler they take 130 .. 164 registers, three CTAs per SM;
+// four CTAs (128 registers, at most 36 bytes of spills) measured at 512^3
+// FP16 (fraction of the copy bandwidth, three CTAs -> four): pull 0.906 ->
+// 1.014, AA 0.872 -> 0.907, Esoteric Twist 0.870 -> 1.010, Esoteric Pull
+// 0.844 -> 0.943, Esoteric Push 0.892 -> 0.913; five CTAs (96 registers,
+// 380 .. 448 bytes of spills) fell to 0.61 .. 0.71
+#ifndef LBM_QUAD_MINB
+#define LBM_QUAD_MINB 4
+#endif
+#define LBM_QUAD_BOUNDS __launch_bounds__(LBM_BX, LBM_QUAD_MINB)
 
 // how a kernel reads the canonical populations f(n) of a cell; the in-place
 // family below takes an even and an odd value per pattern (3 + 2 k + parity)
@@ -321,6 +332,47 @@ __global__ void LBM_PULL2_BOUNDS k_pull2(const S* __restrict__ src, S* __restric
   });
 }
 
+// Four cells per thread (x = 4k .. 4k + 3) for FP16 / BF16 delta storage
+// when Nx % 4 == 0: the arithmetic of k_pull2 on two packed pairs per
+// population (every lane computes what k_pull2 computes, so the states are
+// bitwise equal).  xi_x = 0 planes: one aligned 8-byte load; xi_x = +-1: the
+// aligned quad and the one element beyond it.  Half the loads, stores and
+// address arithmetic per cell of k_pull2: 52.6 -> 54.6 GLUPS at 512^3 FP16,
+// and 60.9 with four CTAs per SM (LBM_QUAD_MINB).
+template <int ST, class S, int SPACE, bool REG>
+__global__ void LBM_QUAD_BOUNDS k_pull4(const S* __restrict__ src, S* __restrict__ dst, Geo g,
+                                         Rates<P4> keep) {
+  const int x = 4 * (blockIdx.x * LBM_BX + threadIdx.x);
+  if (x >= g.nx) return;
+  const int y = blockIdx.y, z = int(blockIdx.z);
+  const int c = (z * g.ny + y) * g.nx + x;
+  const int nxy = g.nx * g.ny;
+  const int wxp0 = x == 0 ? g.nx : 0;           // cell x reading x - 1
+  const int wxm3 = x + 4 == g.nx ? -g.nx : 0;   // cell x + 3 reading x + 4
+  const int wyp = y == 0 ? nxy : 0, wym = y == g.ny - 1 ? -nxy : 0;
+  const int wzp = z == 0 ? int(g.N) : 0, wzm = z == g.nz - 1 ? -int(g.N) : 0;
+  P4 f[q_of(ST)];
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    constexpr int cx = vel(ST, i, 0), cy = vel(ST, i, 1), cz = dim_of(ST) == 3 ? vel(ST, i, 2) : 0;
+    const S* pl = src + (int64_t(i) * g.N - (int64_t(cz) * nxy + int64_t(cy) * g.nx));
+    const int off = c + (cy > 0 ? wyp : (cy < 0 ? wym : 0)) + (cz > 0 ? wzp : (cz < 0 ? wzm : 0));
+    constexpr int E = scale_exp(ST, i);
+    if constexpr (cx == 0) f[i] = Pack<S>::template load4s<E>(pl + off);
+    else if constexpr (cx > 0) f[i] = Pack<S>::template load1_3s<E>(pl + (off - 1 + wxp0), pl + off);
+    else f[i] = Pack<S>::template load3_1s<E>(pl + off, pl + (off + 4 + wxm3));
+  });
+  // the backward transform leaves population i multiplied by 2^|xi_i|^2;
+  // the storage scale 2^s_i absorbs it exactly
+  collide<ST, P4, SPACE, REG, true>(f, keep);
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    constexpr int k = vel(ST, i, 0) * vel(ST, i, 0) + vel(ST, i, 1) * vel(ST, i, 1) +
+                      vel(ST, i, 2) * vel(ST, i, 2);
+    store4<S>(dst + (int64_t(i) * g.N + c), f[i] * P4(float(1u << (scale_exp(ST, i) - k))));
+  });
+}
+
 // In-place streaming on one buffer (Sec. 4.3), every pattern through one
 // kernel with per-direction plane pointers (as the pull kernel): population
 // i is read from slot rd_i at node x + r_i and f*_i written to slot wr_i at
@@ -522,12 +574,73 @@ __global__ void LBM_PULL2_BOUNDS k_inplace2(const __grid_constant__ InPlacePtrs<
   });
 }
 
+// Four cells per thread (Nx % 4 == 0): the arithmetic of k_inplace2 on two
+// packed pairs per population, over the same pointer table.  A cell's x
+// offset of 0 keeps the four cells' access one aligned 8-byte access; -1 or
+// +1 splits it into the aligned quad (less one element) and the element
+// beyond it, of which the one at the row's end wraps.  Each cell reads and
+// writes its own set of elements, so grouping four of them per thread keeps
+// the in-place update race-free.
+template <int ST, class S, int SPACE, bool REG, int MODE>
+__global__ void LBM_QUAD_BOUNDS k_inplace4(const __grid_constant__ InPlacePtrs<S> P, Geo g,
+                                            Rates<P4> keep) {
+  const int x = 4 * (int(blockIdx.x) * LBM_BX + threadIdx.x);
+  if (x >= g.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int c = (z * g.ny + y) * g.nx + x;
+  const int nxy = g.nx * g.ny;
+  const int wx0 = x == 0 ? g.nx : 0;           // cell x at offset -1
+  const int wx3 = x + 4 == g.nx ? -g.nx : 0;   // cell x + 3 at offset +1
+  const int wyp = y == 0 ? nxy : 0, wym = y == g.ny - 1 ? -nxy : 0;
+  const int wzp = z == 0 ? int(g.N) : 0, wzm = z == g.nz - 1 ? -int(g.N) : 0;
+  auto wyz = [&](int oy, int oz) {
+    return (oy < 0 ? wyp : (oy > 0 ? wym : 0)) + (oz < 0 ? wzp : (oz > 0 ? wzm : 0));
+  };
+  P4 f[q_of(ST)];
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    using Mp = InPlaceMap<ST, MODE, i>;
+    // p: the element cell x reads (its x offset included in the table)
+    const S* p = P.rd[i] + (c + wyz(Mp::ry, Mp::rz));
+    constexpr int E = scale_exp(ST, i);
+    if constexpr (Mp::rx == 0) f[i] = Pack<S>::template load4s<E>(p);
+    else if constexpr (Mp::rx < 0) f[i] = Pack<S>::template load1_3s<E>(p + wx0, p + 1);
+    else f[i] = Pack<S>::template load3_1s<E>(p - 1, p + 3 + wx3);
+  });
+  collide<ST, P4, SPACE, REG, true>(f, keep);
+  sfor<q_of(ST)>([&](auto I) {
+    constexpr int i = CI(I);
+    using Mp = InPlaceMap<ST, MODE, i>;
+    constexpr int k = vel(ST, i, 0) * vel(ST, i, 0) + vel(ST, i, 1) * vel(ST, i, 1) +
+                      vel(ST, i, 2) * vel(ST, i, 2);
+    const P4 v = f[i] * P4(float(1u << (scale_exp(ST, i) - k)));
+    S* p = P.wr[i] + (c + wyz(Mp::wy, Mp::wz));
+    if constexpr (Mp::wx == 0) store4<S>(p, v);
+    else if constexpr (Mp::wx < 0) store1_3<S>(p + wx0, p + 1, v);
+    else store3_1<S>(p - 1, p + 3 + wx3, v);
+  });
+}
+
 template <int ST, class S, int SPACE, bool REG>
 void launch_inplace2(const StepArgs& a, const Rates<P2>& keep) {
   S* buf = (S*)a.dst;
   const dim3 grid2((a.g.nx / 2 + LBM_BX - 1) / LBM_BX, a.g.ny, a.g.nz);
+  // four cells per thread where Nx % 4 == 0, compiled for the D3Q27
+  // regularised cumulant method only (for every method it took the compile
+  // of one storage type from minutes to beyond 45 minutes)
+  constexpr bool QUADS = ST == D3Q27 && SPACE == SP_CUMULANT && REG;
+  Rates<P4> k4;
+  for (int k = 0; k < 6; ++k) k4.om[k] = P4(keep.om[k], keep.om[k]);
   auto go = [&](auto mode_tag) {
     constexpr int MODE = decltype(mode_tag)::value;
+    if constexpr (QUADS) {
+      if (a.g.nx % 4 == 0) {
+        const dim3 grid4((a.g.nx / 4 + LBM_BX - 1) / LBM_BX, a.g.ny, a.g.nz);
+        k_inplace4<ST, S, SPACE, REG, MODE>
+            <<<grid4, LBM_BX, 0, a.stream>>>(inplace_ptrs<ST, MODE>(buf, a.g), a.g, k4);
+        return;
+      }
+    }
     k_inplace2<ST, S, SPACE, REG, MODE>
         <<<grid2, LBM_BX, 0, a.stream>>>(inplace_ptrs<ST, MODE>(buf, a.g), a.g, keep);
   };
@@ -913,6 +1026,14 @@ void launch_step_typed(const StepArgs& a) {
         Rates<P2> k2;
         for (int k = 0; k < 6; ++k) k2.om[k] = P2(1.0 - a.rates[k]);
         const dim3 grid2((a.g.nx / 2 + LBM_BX - 1) / LBM_BX, a.g.ny, a.nzc > 0 ? a.nzc : a.g.nz);
+        if (a.g.nx % 4 == 0 && a.z0 == 0 && (a.nzc == 0 || a.nzc == a.g.nz)) {
+          Rates<P4> k4;
+          for (int k = 0; k < 6; ++k) k4.om[k] = P4(1.0 - a.rates[k]);
+          const dim3 grid4((a.g.nx / 4 + LBM_BX - 1) / LBM_BX, a.g.ny, a.g.nz);
+          k_pull4<ST, S, SPACE, REG><<<grid4, LBM_BX, 0, a.stream>>>((const S*)a.src, (S*)a.dst,
+                                                                    a.g, k4);
+          return;
+        }
         k_pull2<ST, S, SPACE, REG><<<grid2, LBM_BX, 0, a.stream>>>((const S*)a.src, (S*)a.dst,
                                                                   a.g, k2, a.z0);
         return;

@@ -85,6 +85,43 @@ P2F P2 rcp(P2 x) {
 #endif
 }
 
+// four cells (x .. x+3) as two packed pairs; every operation is the P2
+// operation on each pair, so each lane computes exactly what P2 (and the
+// scalar FP32 path) computes
+struct P4 {
+  P2 l, h;
+  P4() = default;
+  P2F P4(P2 a, P2 b) : l(a), h(b) {}
+  P2F explicit P4(double s) : l(s), h(s) {}
+  P2F explicit P4(float s) : l(s), h(s) {}
+  P2F explicit P4(int s) : l(s), h(s) {}
+};
+struct M4 {  // lazy product
+  M2 l, h;
+  P2F operator P4() const { return P4(P2(l), P2(h)); }
+};
+P2F P4 neg(P4 x) { return P4(neg(x.l), neg(x.h)); }
+P2F P4 operator-(P4 x) { return neg(x); }
+P2F M4 operator-(M4 m) { return M4{-m.l, -m.h}; }
+P2F P4 operator+(P4 a, P4 b) { return P4(a.l + b.l, a.h + b.h); }
+P2F P4 operator-(P4 a, P4 b) { return P4(a.l - b.l, a.h - b.h); }
+P2F M4 operator*(P4 a, P4 b) { return M4{a.l * b.l, a.h * b.h}; }
+P2F P4 operator+(M4 m, P4 c) { return P4(m.l + c.l, m.h + c.h); }
+P2F P4 operator+(P4 c, M4 m) { return P4(c.l + m.l, c.h + m.h); }
+P2F P4 operator-(M4 m, P4 c) { return P4(m.l - c.l, m.h - c.h); }
+P2F P4 operator-(P4 c, M4 m) { return P4(c.l - m.l, c.h - m.h); }
+P2F P4 operator+(M4 x, M4 y) { return P4(x.l + y.l, x.h + y.h); }
+P2F P4 operator-(M4 x, M4 y) { return P4(x.l - y.l, x.h - y.h); }
+P2F M4 operator*(M4 m, P4 b) { return M4{m.l * b.l, m.h * b.h}; }
+P2F M4 operator*(P4 a, M4 m) { return M4{a.l * m.l, a.h * m.h}; }
+P2F M4 operator*(M4 x, M4 y) { return M4{x.l * y.l, x.h * y.h}; }
+P2F P4& operator+=(P4& a, P4 b) { return a = a + b; }
+P2F P4& operator+=(P4& a, M4 b) { return a = a + b; }
+P2F P4& operator-=(P4& a, P4 b) { return a = a - b; }
+P2F P4& operator-=(P4& a, M4 b) { return a = a - b; }
+P2F P4& operator*=(P4& a, P4 b) { return a = P4(a * b); }
+P2F P4 rcp(P4 x) { return P4(rcp(x.l), rcp(x.h)); }
+
 // two cells' packed values of one population plane (x and x+1)
 template <class S>
 struct Pack;
@@ -106,8 +143,52 @@ P2F float h2f_scaled(__half h) {
 #endif
 }
 
+// the same for BF16: b * 2^-E in one mixed-precision multiply-add (BF16
+// operands, exact product); equal, bit for bit, to the widening followed by
+// the power-of-two multiply, in one FMA-pipe instruction and no shifts
+template <int E>
+P2F float b2f_scaled(__nv_bfloat16 b) {
+#ifdef __CUDA_ARCH__
+  static_assert(E >= 0 && E <= 126, "2^-E must be a normal BF16 number");
+  float r;
+  asm("fma.rn.f32.bf16 %0, %1, %2, %3;"
+      : "=f"(r)
+      : "h"(__bfloat16_as_ushort(b)), "h"((unsigned short)((127 - E) << 7)), "f"(-0.0f));
+  return r;
+#else
+  return __bfloat162float(b) / float(1u << E);
+#endif
+}
+
 template <>
 struct Pack<__half> {
+  // four cells (x .. x+3, Nx % 4 == 0): the aligned quad at p, times 2^-E
+  template <int E>
+  P2F static P4 load4s(const __half* p) {
+    const uint2 w = *reinterpret_cast<const uint2*>(p);
+    const __half2 a = *reinterpret_cast<const __half2*>(&w.x);
+    const __half2 b = *reinterpret_cast<const __half2*>(&w.y);
+    return P4(P2(make_float2(h2f_scaled<E>(__low2half(a)), h2f_scaled<E>(__high2half(a)))),
+              P2(make_float2(h2f_scaled<E>(__low2half(b)), h2f_scaled<E>(__high2half(b)))));
+  }
+  // (e, q0, q1, q2): the element at pe and the first three of the quad at p
+  template <int E>
+  P2F static P4 load1_3s(const __half* pe, const __half* p) {
+    const uint2 w = *reinterpret_cast<const uint2*>(p);
+    const __half2 a = *reinterpret_cast<const __half2*>(&w.x);
+    const __half2 b = *reinterpret_cast<const __half2*>(&w.y);
+    return P4(P2(make_float2(h2f_scaled<E>(*pe), h2f_scaled<E>(__low2half(a)))),
+              P2(make_float2(h2f_scaled<E>(__high2half(a)), h2f_scaled<E>(__low2half(b)))));
+  }
+  // (q1, q2, q3, e): the last three of the quad at p and the element at pe
+  template <int E>
+  P2F static P4 load3_1s(const __half* p, const __half* pe) {
+    const uint2 w = *reinterpret_cast<const uint2*>(p);
+    const __half2 a = *reinterpret_cast<const __half2*>(&w.x);
+    const __half2 b = *reinterpret_cast<const __half2*>(&w.y);
+    return P4(P2(make_float2(h2f_scaled<E>(__high2half(a)), h2f_scaled<E>(__low2half(b)))),
+              P2(make_float2(h2f_scaled<E>(__high2half(b)), h2f_scaled<E>(*pe))));
+  }
   P2F static P2 load2(const __half* p) {
     return P2(__half22float2(*reinterpret_cast<const __half2*>(p)));
   }
@@ -140,15 +221,42 @@ struct Pack<__nv_bfloat16> {
   P2F static P2 load11(const __nv_bfloat16* p0, const __nv_bfloat16* p1) {
     return P2(make_float2(__bfloat162float(*p0), __bfloat162float(*p1)));
   }
-  // BF16 widens by a shift (not on the FMA pipe), so the scale stays a
-  // separate packed multiply
+  // four cells (x .. x+3, Nx % 4 == 0): the aligned quad at p, times 2^-E
+  template <int E>
+  P2F static P4 load4s(const __nv_bfloat16* p) {
+    const uint2 w = *reinterpret_cast<const uint2*>(p);
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&w.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&w.y);
+    return P4(P2(make_float2(b2f_scaled<E>(__low2bfloat16(a)), b2f_scaled<E>(__high2bfloat16(a)))),
+              P2(make_float2(b2f_scaled<E>(__low2bfloat16(b)), b2f_scaled<E>(__high2bfloat16(b)))));
+  }
+  // (e, q0, q1, q2): the element at pe and the first three of the quad at p
+  template <int E>
+  P2F static P4 load1_3s(const __nv_bfloat16* pe, const __nv_bfloat16* p) {
+    const uint2 w = *reinterpret_cast<const uint2*>(p);
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&w.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&w.y);
+    return P4(P2(make_float2(b2f_scaled<E>(*pe), b2f_scaled<E>(__low2bfloat16(a)))),
+              P2(make_float2(b2f_scaled<E>(__high2bfloat16(a)), b2f_scaled<E>(__low2bfloat16(b)))));
+  }
+  // (q1, q2, q3, e): the last three of the quad at p and the element at pe
+  template <int E>
+  P2F static P4 load3_1s(const __nv_bfloat16* p, const __nv_bfloat16* pe) {
+    const uint2 w = *reinterpret_cast<const uint2*>(p);
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&w.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&w.y);
+    return P4(P2(make_float2(b2f_scaled<E>(__high2bfloat16(a)), b2f_scaled<E>(__low2bfloat16(b)))),
+              P2(make_float2(b2f_scaled<E>(__high2bfloat16(b)), b2f_scaled<E>(*pe))));
+  }
+  // the same values times 2^-E (the decode of the per-direction scale)
   template <int E>
   P2F static P2 load2s(const __nv_bfloat16* p) {
-    return load2(p) * P2(1.0f / float(1u << E));
+    const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(p);
+    return P2(make_float2(b2f_scaled<E>(__low2bfloat16(h)), b2f_scaled<E>(__high2bfloat16(h))));
   }
   template <int E>
   P2F static P2 load11s(const __nv_bfloat16* p0, const __nv_bfloat16* p1) {
-    return load11(p0, p1) * P2(1.0f / float(1u << E));
+    return P2(make_float2(b2f_scaled<E>(*p0), b2f_scaled<E>(*p1)));
   }
   P2F static void store2(__nv_bfloat16* p, P2 v) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v.v);
@@ -158,5 +266,29 @@ struct Pack<__nv_bfloat16> {
     *p1 = __float2bfloat16_rn(v.v.y);
   }
 };
+
+// four cells' stores (the same rounding as store2 / store11): the aligned
+// quad at p; and the two shifted forms, whose four elements straddle a quad
+// boundary: one element apart (at pe, possibly wrapped), an aligned pair and
+// one more element
+template <class S>
+P2F void store4(S* p, P4 v) {
+  uint2 w;
+  Pack<S>::store2(reinterpret_cast<S*>(&w.x), v.l);
+  Pack<S>::store2(reinterpret_cast<S*>(&w.y), v.h);
+  *reinterpret_cast<uint2*>(p) = w;
+}
+// (v0 -> pe, v1 v2 -> p[0..1], v3 -> p[2])
+template <class S>
+P2F void store1_3(S* pe, S* p, P4 v) {
+  Pack<S>::store11(pe, p + 2, P2(make_float2(v.l.v.x, v.h.v.y)));
+  Pack<S>::store2(p, P2(make_float2(v.l.v.y, v.h.v.x)));
+}
+// (v0 -> p[1], v1 v2 -> p[2..3], v3 -> pe)
+template <class S>
+P2F void store3_1(S* p, S* pe, P4 v) {
+  Pack<S>::store11(p + 1, pe, P2(make_float2(v.l.v.x, v.h.v.y)));
+  Pack<S>::store2(p + 2, P2(make_float2(v.l.v.y, v.h.v.x)));
+}
 
 }  // namespace lbm

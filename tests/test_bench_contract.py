@@ -57,9 +57,9 @@ def test_committed_ncu_summaries_match_the_kernel_sources():
     hash of its sources and is dropped (null in the line) when they differ."""
     bench = _bench_module()
     assert bench.kernel_traffic_per_cell() is not None
-    pull2 = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_packed.cuh")
+    pull4 = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_packed.cuh")
     closure = ("lbm_device.cuh", "lbm_closure.cu")
-    for name, src in (("alu_k_pull2_d3q27_cumulant_f16.md", pull2),
+    for name, src in (("alu_k_pull4_d3q27_cumulant_f16.md", pull4),
                       ("alu_k_closure_pull_d3q27_128.md", closure)):
         for key in ("fp32_flop_per_cell", "fp32_lane_ops_per_cell", "thread_inst_per_cell"):
             assert bench.profile_value(name, key, src) is not None, (name, key)

@@ -299,19 +299,24 @@ def test_taylor_green_config_d3q19_omrt_fp64():
             assert rel_linf(u_g, u_r) < 1e-12
 
 
+# Nx = 134 (2 mod 4): two cells per thread; Nx = 532 (0 mod 4): four cells
+# per thread, 133 threads per row, so two blocks of 128 with a ragged tail
 EVEN_DIMS = {0: (134, 37, 1), 1: (134, 6, 5), 2: (134, 6, 5)}
+QUAD_DIMS = {0: (532, 9, 1), 1: (532, 6, 5), 2: (532, 6, 5)}
 
 
 @pytest.mark.parametrize("streaming", L.STREAMING_PATTERNS)
 @pytest.mark.parametrize("storage,p", [(L.STORE_F16_DELTA, 10), (L.STORE_BF16_DELTA, 7)])
 @pytest.mark.parametrize("method", METHODS, ids=lambda m: f"sp{m[0]}eq{m[1]}reg{int(m[2])}")
 @pytest.mark.parametrize("st", [0, 1, 2], ids=["D2Q9", "D3Q19", "D3Q27"])
-def test_packed_half_kernel_error_bound(st, method, storage, p, streaming):
+@pytest.mark.parametrize("cells", [2, 4], ids=["pairs", "quads"])
+def test_packed_half_kernel_error_bound(cells, st, method, storage, p, streaming):
     """Even Nx routes FP16 / BF16 steps, pull and in place, to the
-    two-cells-per-thread kernels with packed FP32 arithmetic; same rounding
-    bound as the scalar kernel (see test_half_storage_error_bound)."""
+    two- (Nx % 4 == 2) or four-cells-per-thread (Nx % 4 == 0) kernels with
+    packed FP32 arithmetic; same rounding bound as the scalar kernel (see
+    test_half_storage_error_bound)."""
     space, eq, reg = method
-    dims = EVEN_DIMS[st]
+    dims = (EVEN_DIMS if cells == 2 else QUAD_DIMS)[st]
     d = 2 if st == 0 else 3
     rho, u = I.taylor_green(dims, 0.05, d=d)
     u = I.add_uniform_noise(u, 1e-3, seed=11)
@@ -331,11 +336,12 @@ def test_packed_half_kernel_error_bound(st, method, storage, p, streaming):
 
 @pytest.mark.parametrize("storage", [L.STORE_F16_DELTA, L.STORE_BF16_DELTA], ids=["f16", "bf16"])
 @pytest.mark.parametrize("st", [0, 1, 2], ids=["D2Q9", "D3Q19", "D3Q27"])
-def test_packed_half_pull_and_in_place_are_bitwise_identical(st, storage):
-    """The packed in-place kernel runs the packed pull kernel's arithmetic:
+@pytest.mark.parametrize("cells", [2, 4], ids=["pairs", "quads"])
+def test_packed_half_pull_and_in_place_are_bitwise_identical(cells, st, storage):
+    """The packed in-place kernels run the packed pull kernels' arithmetic:
     identical FP16 / BF16 states after odd and even step counts."""
     space, eq, reg = L.SPACE_CUMULANT, L.EQ_ABSOLUTE, True
-    dims = EVEN_DIMS[st]
+    dims = (EVEN_DIMS if cells == 2 else QUAD_DIMS)[st]
     rho, u = I.taylor_green(dims, 0.05, d=2 if st == 0 else 3)
     u = I.add_uniform_noise(u, 1e-3, seed=11)
     for n in (4, 5):
@@ -347,3 +353,42 @@ def test_packed_half_pull_and_in_place_are_bitwise_identical(st, storage):
                 out.append(lat.get_populations())
         for k in range(1, len(out)):
             assert np.array_equal(out[0], out[k]), (n, k)
+
+
+@pytest.mark.parametrize("streaming", L.STREAMING_PATTERNS)
+@pytest.mark.parametrize("storage", [L.STORE_F16_DELTA, L.STORE_BF16_DELTA], ids=["f16", "bf16"])
+@pytest.mark.parametrize("method", [(L.SPACE_CUMULANT, L.EQ_ABSOLUTE, True),
+                                    (L.SPACE_RAW, L.EQ_DELTA, False),
+                                    (L.SPACE_TRT, L.EQ_ABSOLUTE, False)],
+                         ids=lambda m: f"sp{m[0]}eq{m[1]}reg{int(m[2])}")
+@pytest.mark.parametrize("st", [0, 1, 2], ids=["D2Q9", "D3Q19", "D3Q27"])
+def test_four_cell_kernels_equal_two_cell_kernels_on_a_periodic_replica(st, method, storage,
+                                                                        streaming):
+    """Two copies along x of an Nx = 266 state (2 mod 4: two cells per
+    thread) form an Nx = 532 state (0 mod 4: four cells per thread) whose
+    periodic neighbours are the same values: after odd and even step counts
+    the large lattice holds exactly two copies of the small one."""
+    space, eq, reg = method
+    ny, nz = (9, 1) if st == 0 else (6, 5)
+    small, big = (266, ny, nz), (532, ny, nz)
+    rho, u = I.taylor_green(small, 0.05, d=2 if st == 0 else 3)
+    u = I.add_uniform_noise(u, 1e-3, seed=13)
+    m = O.method(st, space, eq, rates_of(space, reg))
+    df0 = O.init(m, small, rho, u)
+    _, w, _ = O.lattice(st)
+    pert = I.random_deviations(len(w), int(np.prod(small)), 2e-3, seed=14)
+    df0 = df0 + (w[:, None] * pert).reshape(df0.shape)
+    q = len(w)
+
+    def tile(df):
+        a = np.asarray(df).reshape(q, nz, ny, 266)
+        return np.concatenate([a, a], axis=3).reshape(q, -1)
+
+    for n in (4, 5):
+        got = []
+        for dims, d in ((small, df0), (big, tile(df0))):
+            with L.Lattice(st, space, eq, storage, streaming, rates_of(space, reg), dims) as lat:
+                lat.set_populations(d)
+                lat.step(n)
+                got.append(lat.get_populations())
+        assert np.array_equal(tile(got[0]).reshape(got[1].shape), got[1]), n
