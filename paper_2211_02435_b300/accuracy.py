@@ -8,6 +8,13 @@
   Fourier flow (max |u| = 0.08), FP16 / BF16 delta storage and FP32 storage
   against FP64 storage, velocity and density-deviation errors (relative L-inf
   and L2) at fixed intervals.
+* ``storage_encoding``: what one FP16 encode of a state costs, with the
+  library's per-direction power-of-two scale and without it (the deviations
+  stored as they are): D3Q27 central-moment (R-) states after 100 FP64 steps
+  of flows from max |u| = 0.08 down to 1e-4; relative L2 error of the
+  decoded populations and of the velocity and density deviation computed
+  from them, and the share of deviations that fall below FP16's smallest
+  normal number (2^-14) unscaled.
 * ``tgv_plateau``: the round-off plateau of the decaying Taylor-Green vortex
   (Sec. 5.1, Eq. 5.1/5.2, Table 3): D3Q27, L x L x 1 (the flow is
   z-invariant), u0 = 0.25, nu = 1/6 (every rate 1), FP64; the relative
@@ -106,6 +113,46 @@ def half_storage(n=512, nu=1e-3, steps=5000, every=1000, seed=3, stream=None):
                       f"(seed {seed}), nu={nu}", "steps": steps, "rows": rows}
 
 
+def storage_encoding(n=128, nu=1e-3, steps=100, stream=None):
+    rates = [I.shear_viscosity_rate(nu)] + [1.0] * 5
+    dims = (n, n, n)
+    cases = [("fourier", 0.08)] + [("taylor_green", u0) for u0 in (1e-2, 1e-3, 1e-4)]
+    rows = []
+    for kind, u0 in cases:
+        if kind == "fourier":
+            rho, u = I.fourier_modes(dims, n_modes=8, umax=u0, seed=3)
+        else:
+            rho, u = I.taylor_green(dims, u0)
+        with L.Lattice(L.D3Q27, L.SPACE_CENTRAL, L.EQ_ABSOLUTE, L.STORE_F64, L.PULL, rates, dims,
+                       stream=stream) as ref:
+            ref.init_velocity(rho.reshape(-1), u.reshape(-1))
+            ref.step(steps)
+            df = ref.get_populations()
+            r64, u64 = ref.macroscopic()
+            # unscaled: each deviation rounded to the nearest FP16 number as it is
+            plain = df.astype(np.float16).astype(np.float64)
+            ref.set_populations(plain)
+            r_p, u_p = ref.macroscopic()
+        with L.Lattice(L.D3Q27, L.SPACE_CENTRAL, L.EQ_ABSOLUTE, L.STORE_F16_DELTA, L.PULL, rates,
+                       dims, stream=stream) as lat:
+            lat.set_populations(df)
+            scaled = lat.get_populations()
+            r_s, u_s = lat.macroscopic()
+        del rho, u
+        norm = np.sqrt((df ** 2).sum())
+        nz = df != 0
+        row = {"flow": kind, "u0": u0,
+               "unscaled_subnormal_share": float((np.abs(df[nz]) < 2.0 ** -14).mean()),
+               "scaled": {"pop_rel_l2": float(np.sqrt(((scaled - df) ** 2).sum()) / norm),
+                          **_errors(u_s, u64, r_s, r64)},
+               "unscaled": {"pop_rel_l2": float(np.sqrt(((plain - df) ** 2).sum()) / norm),
+                            **_errors(u_p, u64, r_p, r64)}}
+        rows.append(row)
+        del df, plain, scaled
+    return {"config": f"D3Q27 central moments R-, {n}^3, {steps} FP64 steps, nu={nu}",
+            "rows": rows}
+
+
 PLATEAU_METHODS = (("SRT", L.SPACE_POPULATIONS), ("R-WO-MRT", L.SPACE_RAW_WEIGHTED),
                    ("R-O-MRT", L.SPACE_RAW), ("R-CM", L.SPACE_CENTRAL),
                    ("R-K", L.SPACE_CUMULANT))
@@ -166,7 +213,8 @@ def main():
     import argparse
     import json
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("study", choices=["fp32_vs_fp64", "half_storage", "tgv_plateau"])
+    ap.add_argument("study", choices=["fp32_vs_fp64", "half_storage", "storage_encoding",
+                                      "tgv_plateau"])
     ap.add_argument("--n", type=int)
     ap.add_argument("--steps", type=int)
     ap.add_argument("--every", type=int)
@@ -176,6 +224,8 @@ def main():
     kw = {k: v for k, v in (("n", a.n), ("steps", a.steps), ("every", a.every)) if v}
     if a.study == "tgv_plateau":
         res = tgv_plateau(**kw)
+    elif a.study == "storage_encoding":
+        res = storage_encoding(nu=a.nu, **{k: v for k, v in kw.items() if k != "every"})
     else:
         fn = fp32_vs_fp64 if a.study == "fp32_vs_fp64" else half_storage
         res = fn(nu=a.nu, **kw)

@@ -45,11 +45,20 @@ namespace lbm {
 // FP16 (fraction of the copy bandwidth, three CTAs -> four): pull 0.906 ->
 // 1.014, AA 0.872 -> 0.907, Esoteric Twist 0.870 -> 1.010, Esoteric Pull
 // 0.844 -> 0.943, Esoteric Push 0.892 -> 0.913; five CTAs (96 registers,
-// 380 .. 448 bytes of spills) fell to 0.61 .. 0.71
+// 380 .. 448 bytes of spills) fell to 0.61 .. 0.71.  The general-rate
+// instances (every forward transform kept) need 160 .. 250 registers; at
+// four CTAs they spill up to 480 bytes and run better at three (fraction of
+// the copy bandwidth, FP16 D3Q27, four -> three CTAs): TRT 0.789 -> 0.866,
+// raw moments 0.828 -> 0.883, cumulants 0.577 -> 0.685, central moments
+// 0.825 -> 0.823; SRT (104 bytes of spills) keeps four, 0.944 -> 0.909.
 #ifndef LBM_QUAD_MINB
 #define LBM_QUAD_MINB 4
 #endif
-#define LBM_QUAD_BOUNDS __launch_bounds__(LBM_BX, LBM_QUAD_MINB)
+#ifndef LBM_QUAD_MINB_GENERAL
+#define LBM_QUAD_MINB_GENERAL 3
+#endif
+#define LBM_QUAD_BOUNDS \
+  __launch_bounds__(LBM_BX, (REG || SPACE == SP_SRT) ? LBM_QUAD_MINB : LBM_QUAD_MINB_GENERAL)
 
 // how a kernel reads the canonical populations f(n) of a cell; the in-place
 // family below takes an even and an odd value per pattern (3 + 2 k + parity)
