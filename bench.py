@@ -598,14 +598,15 @@ def run_cuda(args):
     if traffic is not None:
         traffic *= N
 
-    # ALU roofs of the kernels that may reach it (the packed FP16 step and
+    # ALU roofs of the kernels that may reach it (the packed FP16 and BF16 steps and
     # the fused learned-rate step): FP32 flops per cell from ncu counts
     fp32_peak = fp32_peak_tflops(clocks.get("sm_max_mhz"))
-    if "f16_delta" in forms:
-        forms["f16_delta"]["alu"] = alu_roof("alu_k_pull4_d3q27_cumulant_f16.md",
-                                             forms["f16_delta"]["mlups"], fp32_peak,
-                                             ("lbm_device.cuh", "lbm_kernels.cuh",
-                                              "lbm_packed.cuh"))
+    for form, prof in (("f16_delta", "alu_k_pull4_d3q27_cumulant_f16.md"),
+                       ("bf16_delta", "alu_k_pull4_d3q27_cumulant_bf16.md")):
+        if form in forms:
+            forms[form]["alu"] = alu_roof(prof, forms[form]["mlups"], fp32_peak,
+                                          ("lbm_device.cuh", "lbm_kernels.cuh",
+                                           "lbm_packed.cuh"))
     if learned is not None:
         n_c = args.learned_fine // 4
         learned["alu"] = alu_roof("alu_k_closure_pull_d3q27_128.md",

@@ -52,7 +52,7 @@ def _bench_module():
 
 def test_committed_ncu_summaries_match_the_kernel_sources():
     """The figures the bench line reads from profiles/ (DRAM traffic per cell
-    of the FP32 step, ALU-roof counts of the FP16 and learned steps) were
+    of the FP32 step, ALU-roof counts of the FP16, BF16 and learned steps) were
     taken from the kernel sources as committed: each summary records the
     hash of its sources and is dropped (null in the line) when they differ."""
     bench = _bench_module()
@@ -60,6 +60,7 @@ def test_committed_ncu_summaries_match_the_kernel_sources():
     pull4 = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_packed.cuh")
     closure = ("lbm_device.cuh", "lbm_closure.cu")
     for name, src in (("alu_k_pull4_d3q27_cumulant_f16.md", pull4),
+                      ("alu_k_pull4_d3q27_cumulant_bf16.md", pull4),
                       ("alu_k_closure_pull_d3q27_128.md", closure)):
         for key in ("fp32_flop_per_cell", "fp32_lane_ops_per_cell", "thread_inst_per_cell"):
             assert bench.profile_value(name, key, src) is not None, (name, key)
