@@ -172,6 +172,16 @@ int lbm_batch_create(lbm_batch** out, const lbm_params* p, int n, const int64_t*
     return LBM_ERR_UNSUPPORTED;
   for (int k = 0; k < 6; ++k)
     if (!(p->rates[k] > 0.0 && p->rates[k] <= 2.0)) return LBM_ERR_INVALID;
+  if (p->space == LBM_SPACE_POPULATIONS && shear_rates) return LBM_ERR_INVALID;
+  // every instance's box and shear rate, before any device work
+  for (int k = 0; k < n; ++k) {
+    const int64_t nx = dims[3 * k], ny = dims[3 * k + 1], nz = dims[3 * k + 2];
+    const double om = shear_rates ? shear_rates[k] : p->rates[0];
+    if (nx < 1 || ny < 1 || nz < 1 || nx >= (int64_t(1) << 31) || ny > 65535 || nz > 65535 ||
+        !lbm::index_fits(nx, ny, nz) || (p->stencil == LBM_D2Q9 && nz != 1) ||
+        !(om > 0.0 && om <= 2.0))
+      return LBM_ERR_INVALID;
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     cudaGetLastError();
@@ -196,12 +206,6 @@ int lbm_batch_create(lbm_batch** out, const lbm_params* p, int n, const int64_t*
   for (int k = 0; k < n; ++k) {
     const int64_t nx = dims[3 * k], ny = dims[3 * k + 1], nz = dims[3 * k + 2];
     const double om = shear_rates ? shear_rates[k] : p->rates[0];
-    if (nx < 1 || ny < 1 || nz < 1 || ny > 65535 || nz > 65535 || nx * ny * nz >= (int64_t(1) << 31) ||
-        (p->stencil == LBM_D2Q9 && nz != 1) || !(om > 0.0 && om <= 2.0) ||
-        (p->space == LBM_SPACE_POPULATIONS && shear_rates)) {
-      delete b;
-      return LBM_ERR_INVALID;
-    }
     BInst& I = b->inst[k];
     I.nx = int(nx);
     I.ny = int(ny);

@@ -113,6 +113,40 @@ def test_noalloc_rejects_wrapping_sizes_before_any_launch(lib, dims):
     assert rc == -1
 
 
+@pytest.mark.parametrize("dims,fits", [
+    ((65536, 32767, 1), False),   # N < 2^31, but N + Nx*Ny is not
+    ((1024, 1024, 2047), False),  # N + Nx*Ny = 2^31
+    ((1024, 1024, 2046), True),   # the largest Nz for a 1024^2 plane
+    ((1 << 31, 1, 1), False),
+])
+def test_create_bounds_the_kernels_cell_indices(lib, dims, fits):
+    # the step kernels form cell index + periodic wrap in 32-bit integers, so
+    # a lattice is refused unless N + Nx*Ny + 2*Nx + 4096 < 2^31; the check
+    # runs before any device work (FP64 storage: an accepted size fails
+    # later, for want of a device here or of 900 GB of memory on a B300)
+    h = ctypes.c_void_p()
+    rc = lib.lbm_create(ctypes.byref(h), ctypes.byref(_params(dims=dims, storage=L.STORE_F64)))
+    if fits:
+        assert rc in (-5, -4), rc
+    else:
+        assert rc == -1
+    assert not h.value
+
+
+@pytest.mark.parametrize("box", [
+    (65536, 32767, 1),            # one instance past the 32-bit index bound
+    ((1 << 40) + 1, 1, 1),        # Nx alone past 2^31 (its product must not wrap)
+    (1, 1 << 40, 1 << 30),
+    (8, 8, 0),
+])
+def test_batch_create_bounds_every_instance_before_device_work(lib, box):
+    h = ctypes.c_void_p()
+    dims = (ctypes.c_int64 * 6)(8, 8, 8, *box)
+    p = _params(stencil=L.D3Q19, space=L.SPACE_RAW, rates=[1.5] + [1.0] * 5)
+    assert lib.lbm_batch_create(ctypes.byref(h), ctypes.byref(p), 2, dims, None) == -1
+    assert not h.value
+
+
 def test_python_binding_raises_on_error(lib):
     with pytest.raises(L.LBMError) as e:
         L.Lattice(L.D3Q27, L.SPACE_CUMULANT, L.EQ_DELTA, L.STORE_F32, L.PULL, [1.9], (8, 8, 8))
