@@ -106,3 +106,19 @@ def test_batched_ensemble_of_tiny_boxes(storage, tol):
             m = O.method(O.D3Q19, L.SPACE_RAW, O.EQ_DELTA, [om[k]] + rates[1:])
             ref = O.step(m, box, O.init(m, box, *fields[k]), 5)
             assert rel_linf(b.get_populations(k), ref) < tol, (k, box)
+
+
+@pytest.mark.parametrize("streaming", L.STREAMING_PATTERNS)
+def test_zero_steps_leave_the_state_and_negative_counts_are_refused(streaming):
+    dims = (6, 2, 3)
+    space, eq, rates = METHODS[0]
+    m, df0 = initial(L.D3Q27, space, eq, rates, dims, seed=5)
+    with L.Lattice(L.D3Q27, space, eq, L.STORE_F32, streaming, rates, dims) as lat:
+        lat.set_populations(df0)
+        lat.step(1)  # an odd AA parity: the read-out gathers
+        before, t0 = lat.get_populations(), lat.time()
+        lat.step(0)
+        assert np.array_equal(lat.get_populations(), before)
+        assert L.lib().lbm_step(lat._h, -1) == -1
+        assert np.array_equal(lat.get_populations(), before)
+        assert lat.time() == t0
