@@ -198,9 +198,10 @@ typedef struct {
   int streaming;    /* lbm_streaming                                     */
   double rates[6];  /* see LBM_RATE_*; each in (0, 2]                     */
   int64_t dims[3];  /* Nx, Ny, Nz (Nz = 1 for D2Q9); each >= 1, Ny, Nz <=
-                       65535, Nx*Ny*Nz + Nx*Ny + 2*Nx + 4096 < 2^31 (the
-                       kernels' 32-bit cell indices with their periodic
-                       wrap corrections); else LBM_ERR_INVALID           */
+                       65535, Nx*Ny*Nz + Nx*Ny + 2*Nx + 4096 < 2^31 on
+                       D3Q19 / D3Q27 and Nx*Ny + 2*Nx + 4096 < 2^31 on
+                       D2Q9 (the kernels' 32-bit cell indices with their
+                       periodic wrap corrections); else LBM_ERR_INVALID  */
   int boundary;     /* LBM_PERIODIC                                      */
   void* stream;     /* cudaStream_t for every enqueue; NULL = default     */
   int arithmetic;   /* lbm_arithmetic (0 = deviations throughout)         */

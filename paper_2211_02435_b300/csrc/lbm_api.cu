@@ -224,7 +224,8 @@ int lbm_create(lbm_ctx** out, const lbm_params* p) {
   if (p->dims[1] > 65535 || p->dims[2] > 65535) return LBM_ERR_INVALID;
   if (p->dims[0] >= (int64_t(1) << 31) || p->dims[1] * p->dims[0] >= (int64_t(1) << 31))
     return LBM_ERR_INVALID;
-  if (!lbm::index_fits(p->dims[0], p->dims[1], p->dims[2])) return LBM_ERR_INVALID;
+  if (!lbm::index_fits(p->dims[0], p->dims[1], p->dims[2], p->stencil == LBM_D2Q9 ? 2 : 3))
+    return LBM_ERR_INVALID;
   const int64_t N = p->dims[0] * p->dims[1] * p->dims[2];
   if (!valid_rates(p->rates)) return LBM_ERR_INVALID;
   int ndev = 0;

@@ -178,7 +178,8 @@ int lbm_batch_create(lbm_batch** out, const lbm_params* p, int n, const int64_t*
     const int64_t nx = dims[3 * k], ny = dims[3 * k + 1], nz = dims[3 * k + 2];
     const double om = shear_rates ? shear_rates[k] : p->rates[0];
     if (nx < 1 || ny < 1 || nz < 1 || nx >= (int64_t(1) << 31) || ny > 65535 || nz > 65535 ||
-        !lbm::index_fits(nx, ny, nz) || (p->stencil == LBM_D2Q9 && nz != 1) ||
+        !lbm::index_fits(nx, ny, nz, p->stencil == LBM_D2Q9 ? 2 : 3) ||
+        (p->stencil == LBM_D2Q9 && nz != 1) ||
         !(om > 0.0 && om <= 2.0))
       return LBM_ERR_INVALID;
   }

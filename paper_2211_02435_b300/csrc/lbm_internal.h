@@ -16,13 +16,16 @@ struct Geo {
 };
 
 // The step kernels index cells with 32-bit integers: a gather forms c + w
-// with c < N and a periodic wrap correction w of at most N + Nx*Ny + Nx, the
-// packed FP16 / BF16 accesses reach a few elements beyond that, and the
-// tiles of the persistent and batched kernels run up to 2048 cells past N.
-// A lattice is accepted when all of these stay below 2^31.  The caller has
-// already checked 1 <= Nx < 2^31 and Ny, Nz <= 65535, so no product wraps.
-inline bool index_fits(int64_t nx, int64_t ny, int64_t nz) {
-  return nx * ny * nz + nx * ny + 2 * nx + 4096 < (int64_t(1) << 31);
+// with c < N and a periodic wrap correction w.  On a 3-D stencil the z wrap
+// (+N) applies in plane 0, c < Nx*Ny, and the y wrap (+Nx*Ny) in row 0 of a
+// plane, so c + w stays below N + Nx*Ny + 2*Nx; a 2-D stencil has no z wrap
+// and stays below N + 2*Nx.  The packed FP16 / BF16 accesses reach a few
+// elements further and the tiles of the persistent and batched kernels run
+// up to 2048 cells past N.  A lattice is accepted when all of these stay
+// below 2^31.  The caller has already checked 1 <= Nx < 2^31 and Ny, Nz <=
+// 65535, so no product wraps.
+inline bool index_fits(int64_t nx, int64_t ny, int64_t nz, int dim) {
+  return nx * ny * nz + (dim == 3 ? nx * ny : 0) + 2 * nx + 4096 < (int64_t(1) << 31);
 }
 
 enum { STORE_F64 = 0, STORE_F32 = 1, STORE_F16 = 2, STORE_BF16 = 3, STORE_F64_ABS = 4 };

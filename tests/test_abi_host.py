@@ -113,19 +113,24 @@ def test_noalloc_rejects_wrapping_sizes_before_any_launch(lib, dims):
     assert rc == -1
 
 
-@pytest.mark.parametrize("dims,fits", [
-    ((65536, 32767, 1), False),   # N < 2^31, but N + Nx*Ny is not
-    ((1024, 1024, 2047), False),  # N + Nx*Ny = 2^31
-    ((1024, 1024, 2046), True),   # the largest Nz for a 1024^2 plane
-    ((1 << 31, 1, 1), False),
+@pytest.mark.parametrize("st,dims,fits", [
+    (L.D3Q27, (65536, 32767, 1), False),   # N < 2^31, but N + Nx*Ny is not
+    (L.D3Q27, (1024, 1024, 2047), False),  # N + Nx*Ny = 2^31
+    (L.D3Q27, (1024, 1024, 2046), True),   # the largest Nz for a 1024^2 plane
+    (L.D3Q19, (46000, 46000, 1), False),   # one plane: the z wrap doubles the index
+    (L.D2Q9, (46000, 46000, 1), True),     # no z wrap on D2Q9: N + 2*Nx + 4096 < 2^31
+    (L.D2Q9, (46340, 46340, 1), False),
+    (L.D3Q27, (1 << 31, 1, 1), False),
 ])
-def test_create_bounds_the_kernels_cell_indices(lib, dims, fits):
+def test_create_bounds_the_kernels_cell_indices(lib, st, dims, fits):
     # the step kernels form cell index + periodic wrap in 32-bit integers, so
-    # a lattice is refused unless N + Nx*Ny + 2*Nx + 4096 < 2^31; the check
-    # runs before any device work (FP64 storage: an accepted size fails
-    # later, for want of a device here or of 900 GB of memory on a B300)
+    # a lattice is refused unless N + Nx*Ny + 2*Nx + 4096 < 2^31 (D2Q9: N +
+    # 2*Nx + 4096); the check runs before any device work (FP64 storage: an
+    # accepted size fails later, for want of a device here or of the 300 GB
+    # and more it would take on a B300)
     h = ctypes.c_void_p()
-    rc = lib.lbm_create(ctypes.byref(h), ctypes.byref(_params(dims=dims, storage=L.STORE_F64)))
+    rc = lib.lbm_create(ctypes.byref(h),
+                        ctypes.byref(_params(stencil=st, dims=dims, storage=L.STORE_F64)))
     if fits:
         assert rc in (-5, -4), rc
     else:
