@@ -583,19 +583,31 @@ __global__ void LBM_PULL2_BOUNDS k_inplace2(const __grid_constant__ InPlacePtrs<
   });
 }
 
+// Block order of the four-cell in-place kernel (bit m: mode m in reverse).
+// Measured at 512^3 FP16 (fraction of the copy bandwidth, forward ->
+// reversed): AA 0.916 -> 0.927 with both parities reversed (0.925 even
+// only, 0.919 odd only); Esoteric Push 0.937 -> 0.903 / 0.901 / 0.870 for
+// its first / second / both parities, so only the AA modes run in reverse.
+#ifndef LBM_INPLACE4_REV_MASK
+#define LBM_INPLACE4_REV_MASK ((1 << MODE_AA_EVEN) | (1 << MODE_AA_ODD))
+#endif
+
 // Four cells per thread (Nx % 4 == 0): the arithmetic of k_inplace2 on two
 // packed pairs per population, over the same pointer table.  A cell's x
 // offset of 0 keeps the four cells' access one aligned 8-byte access; -1 or
 // +1 splits it into the aligned quad (less one element) and the element
 // beyond it, of which the one at the row's end wraps.  Each cell reads and
 // writes its own set of elements, so grouping four of them per thread keeps
-// the in-place update race-free.
+// the in-place update race-free (in either block order).
 template <int ST, class S, int SPACE, bool REG, int MODE>
 __global__ void LBM_QUAD_BOUNDS k_inplace4(const __grid_constant__ InPlacePtrs<S> P, Geo g,
                                             Rates<P4> keep) {
-  const int x = 4 * (int(blockIdx.x) * LBM_BX + threadIdx.x);
+  constexpr bool REV = (LBM_INPLACE4_REV_MASK >> MODE) & 1;
+  const int bx = REV ? int(gridDim.x) - 1 - int(blockIdx.x) : int(blockIdx.x);
+  const int x = 4 * (bx * LBM_BX + threadIdx.x);
   if (x >= g.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = REV ? g.ny - 1 - int(blockIdx.y) : int(blockIdx.y);
+  const int z = REV ? g.nz - 1 - int(blockIdx.z) : int(blockIdx.z);
   const int c = (z * g.ny + y) * g.nx + x;
   const int nxy = g.nx * g.ny;
   const int wx0 = x == 0 ? g.nx : 0;           // cell x at offset -1
