@@ -918,7 +918,7 @@ __global__ void LBM_CLOSURE_BOUNDS
 // per cell and the warp's network runs twice, once per cell of the pair.  A
 // tile is 256 consecutive cells (a pair never straddles a row).  Measured on
 // B300 at 128^3: 16.1 GLUPS against 13.8 for the one-cell kernel, 16.3 with
-// the register cap of four CTAs per SM (72 bytes of spills).
+// the register cap of four CTAs per SM (84 bytes of spills).
 __global__ void __launch_bounds__(128, 4)
     k_closure_pull_mma2(const __grid_constant__ PullPtrs<float> P, Geo g, Rates<float> keep,
                         const float* __restrict__ params, int ntiles) {
