@@ -510,8 +510,11 @@ def run_cuda(args):
 
         forms["f32"] = {"mlups": N * args.steps / (ms32 / 1e3) / 1e6,
                         "roofline_frac": achieved / peak, "u_rel_linf_vs_f64": uerr(u32)}
+        # each form is timed under its own clock sampler: the forms run one
+        # after the other, and a form late in the run can meet the power cap
         for name, st in (("f16_delta", L.STORE_F16_DELTA), ("bf16_delta", L.STORE_BF16_DELTA)):
-            lat, ms = time_form(st, args.steps, args.warmup)
+            with ClockSampler(local) as ck:
+                lat, ms = time_form(st, args.steps, args.warmup)
             uu = np.empty(3 * N)
             lat.macroscopic(None, uu)
             lat.close()
@@ -520,21 +523,24 @@ def run_cuda(args):
             forms[name] = {"mlups": N * args.steps / (ms / 1e3) / 1e6,
                            "achieved_gbs": ach, "roofline_frac": ach / peak,
                            "u_rel_linf_vs_f64": uerr(uu),
-                           "vs_f32_mlups": (N * args.steps / (ms / 1e3)) / (N * args.steps / (ms32 / 1e3))}
+                           "vs_f32_mlups": (N * args.steps / (ms / 1e3)) / (N * args.steps / (ms32 / 1e3)),
+                           "clocks": ck.summary()}
             del uu
         # in-place patterns (one buffer), FP32 and FP16 delta, even number of steps
         st_ip = 2 * (args.steps // 2)
         for key, store in (("f32", L.STORE_F32), ("f16_delta", L.STORE_F16_DELTA)):
             for name in ("aa", "et", "epull", "epush"):
-                lat, ms = time_form(store, st_ip, args.warmup + args.warmup % 2,
-                                    streaming=STREAMINGS[name])
+                with ClockSampler(local) as ck:
+                    lat, ms = time_form(store, st_ip, args.warmup + args.warmup % 2,
+                                        streaming=STREAMINGS[name])
                 lat.close()
                 del lat
                 ach = BYTES_PER_CELL[key] * N / (ms / 1e3 / st_ip) / 1e9
                 forms[f"{key}_{name}"] = {
                     "mlups": N * st_ip / (ms / 1e3) / 1e6, "achieved_gbs": ach,
                     "roofline_frac": ach / peak, "buffers": 1,
-                    "note": "same per-cell arithmetic as pull (bitwise equal states)"}
+                    "note": "same per-cell arithmetic as pull (bitwise equal states)",
+                    "clocks": ck.summary()}
         # body force (Guo): uniform, and a per-cell field (+12 B/cell of reads)
         for name, force, bpc in (
                 ("f32_force_uniform", np.array([1e-6, 0.0, 0.0]), BYTES_PER_CELL["f32"]),
@@ -662,6 +668,10 @@ def summary(line, win_mlups):
           if k.startswith("f16_delta_") and "roofline_frac" in v}
     if ip:
         out["f16_delta_inplace_frac"] = ip
+        mhz = {k.split("_")[-1]: (v.get("clocks") or {}).get("sm_mhz") for k, v in f.items()
+               if k.startswith("f16_delta_") and "roofline_frac" in v}
+        if any(m is not None for m in mhz.values()):
+            out["f16_delta_inplace_sm_mhz"] = mhz
     b = line.get("batched")
     if b:
         out["batched"] = {"mlups": r(b["mlups"], 0), "frac": r(b["roofline_frac"]),

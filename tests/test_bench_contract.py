@@ -79,10 +79,15 @@ def test_alu_roof_and_summary_arithmetic():
     line = {"value": 31000.0, "roofline": {"frac": 1.05},
             "forms": {"f16_delta": {"mlups": 52000.0, "roofline_frac": 0.87,
                                     "u_rel_linf_vs_f64": 7e-4, "alu": roof},
-                      "f16_delta_aa": {"mlups": 1.0, "roofline_frac": 0.8}},
+                      "f16_delta_aa": {"mlups": 1.0, "roofline_frac": 0.8,
+                                       "clocks": {"sm_mhz": 1845.0, "reasons": ["sw_power_cap"]}},
+                      "f16_delta_et": {"mlups": 1.0, "roofline_frac": 0.99,
+                                       "clocks": {"sm_mhz": 2032.0, "reasons": []}}},
             "batched": None, "learned": None, "cpu_baseline": None, "sustained": None}
     s = bench.summary(line, [30000.0, 31000.0, 32000.0])
     assert s["headline_window_median_mlups"] == 31000.0
     assert s["f16_delta_pull"]["alu_frac"] == round(roof["frac"], 3)
-    assert s["f16_delta_inplace_frac"] == {"aa": 0.8}
+    assert s["f16_delta_inplace_frac"] == {"aa": 0.8, "et": 0.99}
+    # the SM clock each in-place form ran at (sampled over its timing)
+    assert s["f16_delta_inplace_sm_mhz"] == {"aa": 1845.0, "et": 2032.0}
     assert len(json.dumps(s)) < 1500
